@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the Static PageRank hot path on one GB300 (replicas on N GPUs).
+
+Workload (default `rmat24`): the 2^24-vertex R-MAT graph, 2^28 samples with
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), seed 1, duplicates removed, one
+self-loop per vertex; FP64 Static PageRank, alpha = 0.85, uniform 1/n start,
+L-inf tolerance 1e-10, at most 500 sweeps. One step = one full solve
+(initialisation, in-degree partition, sweeps to tolerance), graph resident.
+
+Prints one JSON line (rank 0). `value` is GTEPS = sweeps x |E| / time to
+tolerance, summed over ranks (each rank solves its own replica: weak scaling).
+`--impl reference` times the CPU oracle instead on a bounded sample of sweeps.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS & time-to-tol 1e-10: static vs DF-P, FP32-refined vs FP64, on 1 GB300"
+
+WORKLOADS = {
+    # name: (kind, params, description)
+    "rmat24": ("rmat", (24, 1 << 28), "R-MAT 2^24 vertices, 2^28 samples (a,b,c,d)=(.57,.19,.19,.05) seed 1, "
+                                      "dedup + self-loops; Static FP64, alpha 0.85, tol 1e-10 L-inf"),
+    "grid4096": ("grid", (4096, 0.05), "4096x4096 bidirectional 4-neighbour grid, 5% edges dropped, seed 1, "
+                                       "self-loops; Static FP64, alpha 0.85, tol 1e-10 L-inf"),
+    "rmat16": ("rmat", (16, 1 << 20), "R-MAT 2^16 vertices, 2^20 samples seed 1, dedup + self-loops; "
+                                      "Static FP64, alpha 0.85, tol 1e-10 L-inf"),
+}
+
+
+def make_edges(name):
+    import synth
+    kind, prm, _ = WORKLOADS[name]
+    if kind == "rmat":
+        return synth.rmat(prm[0], prm[1], seed=1)
+    return synth.grid(prm[0], prm[1], seed=1)
+
+
+def algorithmic_bytes_per_sweep(n, m):
+    """Compulsory bytes of one FP64 Static sweep: in-CSR indices 4m, offsets 4(n+1),
+    the gathered vector and the degree read once each (12n), the new ranks written (8n)."""
+    return 4 * m + 24 * n
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per sweep from the committed ncu summary, valid only while the
+    sweep sources are unchanged (sha256 recorded beside the number)."""
+    path = os.path.join(ROOT, "profiles", "sweep_rmat24_traffic.txt")
+    try:
+        rec = {}
+        with open(path) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 2:
+                    rec[parts[0]] = parts[1]
+        h = hashlib.sha256()
+        for fn in ("sweep.cu", "common.cuh", "internal.cuh"):
+            with open(os.path.join(ROOT, "paper_2404_08299_gb300", "csrc", fn), "rb") as f:
+                h.update(f.read())
+        if rec.get("source_sha256") == h.hexdigest():
+            return float(rec["dram_bytes_per_sweep"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for k, nm in enumerate(names):
+                    if p[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n, src, dst, m, target_s):
+    """The FP64 oracle (as it stands) on the host cores: a bounded sample of sweeps
+    of the same Static iteration on the same graph."""
+    import oracle
+    oracle.build()
+    t0 = time.time()
+    og = oracle.graph(n, src, dst)
+    t_build = time.time() - t0
+    t0 = time.time()
+    oracle.pagerank_static(og, tol=0.0, max_iter=1)
+    t1 = time.time() - t0
+    k = max(1, min(200, int(target_s / max(t1, 1e-6))))
+    t0 = time.time()
+    oracle.pagerank_static(og, tol=0.0, max_iter=k)
+    t = time.time() - t0
+    return {"value": k * m / t / 1e9, "unit": "GTEPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d FP64 Static sweeps of the full graph (oracle CSR build %.1fs untimed)" % (k, t_build),
+            "seconds": round(t, 3)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n, src, dst = make_edges(args.workload)
+    import oracle
+    oracle.build()
+    og = oracle.graph(n, src, dst)
+    m = og.m
+    sweeps = args.ref_sweeps
+    for _ in range(args.warmup):
+        oracle.pagerank_static(og, tol=0.0, max_iter=sweeps)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.time()
+        oracle.pagerank_static(og, tol=0.0, max_iter=sweeps)
+        ts.append(time.time() - t0)
+    T = sum(ts)
+    val = args.steps * sweeps * m / T / 1e9
+    kind, prm, desc = WORKLOADS[args.workload]
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GTEPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": T / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": n, "m": m,
+                       "step": "%d oracle sweeps (bounded sample of the solve)" % sweeps},
+            "cpu_baseline": {"value": val, "unit": "GTEPS", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d FP64 Static sweeps per step" % sweeps},
+            "e2e": {"value": val, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--accumulate", default="exact", choices=["exact", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sweeps", type=int, default=2)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import paper_2404_08299_gb300 as prdf
+    from paper_2404_08299_gb300 import build as pbuild
+    import synth
+
+    if rank == 0:
+        pbuild.build()
+        synth.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        dist.barrier()
+
+    n, src, dst = make_edges(args.workload)
+    m0 = len(src)
+    acc = prdf.PRDF_ACC_EXACT if args.accumulate == "exact" else prdf.PRDF_ACC_FP64
+
+    # pinned host inputs (also used by the end-to-end leg)
+    h_src = torch.from_numpy(src).pin_memory()
+    h_dst = torch.from_numpy(dst).pin_memory()
+    d_src = h_src.cuda(non_blocking=True)
+    d_dst = h_dst.cuda(non_blocking=True)
+    g = prdf.Graph(n, d_src, d_dst)
+    n_, m = g.size()
+    del d_src, d_dst
+    torch.cuda.synchronize()
+
+    # warm-up solves
+    for _ in range(args.warmup):
+        g.pagerank_static(accumulate=acc)
+    torch.cuda.synchronize()
+
+    # timed region: K full solves, device-timed with CUDA events on the launching stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sts = []
+    for _ in range(args.steps):
+        R, st = g.pagerank_static(accumulate=acc, time_sweeps=1)
+        sts.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    iters = sts[-1].iterations
+    ms_step = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    edges_per_step = sum(s.iterations for s in sts) / len(sts) * m
+    value = world * edges_per_step / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the rank sweep
+    sweep_ms = sum(s.ms_sweep for s in sts) / sum(s.iterations for s in sts)
+    B = algorithmic_bytes_per_sweep(n, m)
+    achieved = B / (sweep_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = recorded_traffic()
+
+    # end to end through the public API with host buffers: H2D edge list, graph build, solve, D2H ranks
+    h_R = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        s_d = h_src.cuda(non_blocking=True)
+        d_d = h_dst.cuda(non_blocking=True)
+        g2 = prdf.Graph(n, s_d, d_d)
+        R2, st2 = g2.pagerank_static(accumulate=acc)
+        h_R.copy_(R2, non_blocking=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e_ms.append(a0.elapsed_time(a1))
+        del g2, s_d, d_d, R2
+    e2e_step = sum(e2e_ms) / len(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+    e2e_val = world * st2.iterations * m / (e2e_step * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n, src, dst, m, args.cpu_seconds)
+
+    if rank == 0:
+        kind, prm, desc = WORKLOADS[args.workload]
+        line = {
+            "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": n, "m": m, "samples": m0,
+                       "accumulate": args.accumulate, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (in-CSR %.2f GB, rank vector %.0f MB)" % (
+                           (4 * m + 8 * (n + 1)) / 1e9, 8 * n / 1e6)},
+            "time_to_tol_ms": ms_step, "iterations": iters, "converged": bool(sts[-1].converged),
+            "final_delta": sts[-1].final_delta, "paper_style_geps": m / (ms_step * 1e-3) / 1e9,
+            "ms_partition": statistics.median(s.ms_partition for s in sts),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "rank sweep (k_sweep_group<1,8,32> + k_sweep_block), one launch = one sweep",
+                         "bytes_per_sweep": B, "ms_per_sweep": sweep_ms, "peak_source": peak_kind},
+            "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 8 * m0, "d2h_bytes_per_step": 8 * n,
+                    "ms_per_step": e2e_step},
+            "gpu_launches": int(sum(s.kernel_launches for s in sts)),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

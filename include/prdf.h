@@ -1,0 +1,214 @@
+/*
+ * prdf -- Static and Dynamic Frontier with Pruning (DF-P) PageRank on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of libprdf.so. The operations follow the statement of the problem in
+ * Sahu, "Efficient GPU Implementation of Static and Incrementally Expanding
+ * DF-P PageRank for Dynamic Graphs" (arXiv 2404.08299):
+ *   - PageRank, Eq. 1 (Section 3.1), with a self-loop on every vertex;
+ *   - Static PageRank, Alg. static (Section 4.1-4.2);
+ *   - DF / DF-P PageRank, Alg. frontier with the closed-loop update Eq. 2
+ *     (Section 4.3, 4.5);
+ *   - degree partitioning, Alg. partition (Appendix A.2);
+ *   - affected-vertex marking, Alg. affected (Appendix A.3);
+ *   - batch updates Delta^{t-} = E^{t-1} \ E^t, Delta^{t+} = E^t \ E^{t-1}
+ *     (Section 3.3).
+ * Extensions beyond the paper: FP32 sweeps refined in FP64, K-column
+ * weighted personalised PageRank, and its adjoint (gradients).
+ *
+ * Conventions for every entry point
+ *   - Array arguments are DEVICE pointers (for example torch tensors'
+ *     data_ptr) unless the name ends in _host. Work is issued on the
+ *     cudaStream_t passed as `stream` (NULL = legacy default stream) and the
+ *     call returns after the results are complete on that stream unless the
+ *     comment says otherwise.
+ *   - Vertex ids are int32 in [0, n); edge offsets are int64; ranks are
+ *     double (FP64) unless stated; flags are uint8 (Section 5.1.2).
+ *   - The caller owns every array it passes. A prdf_graph owns its device
+ *     CSR of G and G', degree arrays, partitions and scratch; it is freed by
+ *     prdf_graph_destroy.
+ *   - Return value: PRDF_OK (0) or a negative PRDF_E* code; nothing is
+ *     written to outputs on PRDF_EINVAL. prdf_last_error() gives a message
+ *     for the calling thread's last failure. No entry point traps or asserts
+ *     on the device. Reaching max_iter is not an error: stats->converged = 0.
+ *   - Not reentrant on one graph: calls on the same prdf_graph must not
+ *     overlap (they share its scratch).
+ */
+#ifndef PRDF_H
+#define PRDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PRDF_OK 0
+#define PRDF_EINVAL (-1)   /* bad argument: id >= n, size < 0, alpha not in (0,1), tol <= 0, K <= 0, ... */
+#define PRDF_ENOMEM (-2)   /* device allocation failed */
+#define PRDF_ECUDA (-3)    /* a CUDA runtime call or kernel failed */
+#define PRDF_ETIMEOUT (-4) /* a bounded device-side wait ran out */
+#define PRDF_ESTATE (-5)   /* call out of order (e.g. weights needed but graph unweighted) */
+
+/* which CSR */
+#define PRDF_OUT 0 /* G:  row u lists out-neighbours of u (targets) */
+#define PRDF_IN 1  /* G': row v lists in-neighbours of v (sources)  */
+
+/* precision of the rank iteration */
+#define PRDF_FP64 0        /* FP64 ranks and sweeps (Section 5.1.2) */
+#define PRDF_FP32_REFINE 1 /* FP32 ranks + compensated sums, then FP64 refinement sweeps */
+
+/* accumulation of in-neighbour sums in FP64 sweeps */
+#define PRDF_ACC_EXACT 0 /* exact fixed-point sum of the FP64 terms, rounded once */
+#define PRDF_ACC_FP64 1  /* plain FP64 additions */
+
+/* graph creation flags */
+#define PRDF_ADD_SELF_LOOPS 1u /* give every vertex exactly one self-loop (Section 3.1) */
+
+typedef struct prdf_graph prdf_graph;
+
+typedef struct {
+  double alpha;        /* damping factor, default 0.85 (Section 5.1.2) */
+  double tol;          /* L-inf iteration tolerance tau, default 1e-10 */
+  double tau_f;        /* DF frontier tolerance, default 1e-6 */
+  double tau_p;        /* DF-P prune tolerance, default 1e-6 */
+  int max_iter;        /* MAX_ITERATIONS, default 500 */
+  int precision;       /* PRDF_FP64 (default) or PRDF_FP32_REFINE */
+  double tol_fp32_rel; /* FP32 stage stops when ||dR||_inf <= tol_fp32_rel * ||R||_inf; default 1e-6 */
+  int accumulate;      /* PRDF_ACC_EXACT (default) or PRDF_ACC_FP64 */
+  int prune;           /* DF-P (1, default) or DF (0), for prdf_pagerank_dfp */
+  int check_every;     /* sweeps launched between host convergence checks, default 8 */
+  int time_sweeps;     /* 1: time every rank sweep with CUDA events (stats->ms_sweep), default 0 */
+  void* stream;        /* cudaStream_t for all work; NULL = legacy default stream */
+} prdf_params;
+
+typedef struct {
+  int iterations;           /* sweeps run, including the final one (all stages) */
+  int converged;            /* 1 if the final L-inf change was <= tol */
+  double final_delta;       /* L-inf change of the final sweep */
+  int iterations_fp32;      /* sweeps of the FP32 stage (PRDF_FP32_REFINE) */
+  int sweeps_launched;      /* sweeps issued, including those that exited at once after convergence */
+  float ms_total;           /* device time of the whole call (CUDA events) */
+  float ms_partition;       /* initialisation + partitioning */
+  float ms_mark;            /* initial marking (DF/DF-P) */
+  float ms_iterate;         /* sweeps + residual + frontier expansion (incl. host convergence checks) */
+  float ms_sweep;           /* device time of the first `iterations` rank sweeps (needs time_sweeps) */
+  long long edges_processed;/* in-edges gathered over all sweeps (Static) */
+  long long affected_initial; /* |deltaV| before the first sweep (DF/DF-P) */
+  long long kernel_launches;  /* kernels launched by the call */
+} prdf_stats;
+
+/* Fill *p with the defaults above. */
+void prdf_params_default(prdf_params* p);
+
+/* Message for the calling thread's last failing call ("" if none). */
+const char* prdf_last_error(void);
+const char* prdf_strerror(int code);
+
+/* ---------------------------------------------------------------- graph -- */
+
+/*
+ * Build G (out-CSR) and G' (in-CSR) on the device from an edge list
+ * (Section 4.1, 4.3: the CSR of G^t and of its transpose G^t').
+ * src, dst: int32[m0] device arrays, ids in [0, n). Duplicate edges are
+ * merged; with PRDF_ADD_SELF_LOOPS every vertex gets exactly one self-loop
+ * (Section 3.1, 5.1.3). Rows are sorted by ascending neighbour id.
+ * w: optional float32[m0] positive edge weights (NULL = unweighted); the
+ * weight of merged duplicates is their maximum, an added self-loop gets 1.0.
+ * n >= 1, 0 <= m0 < 2^32. Returns PRDF_EINVAL for ids out of range.
+ */
+int prdf_graph_create(int32_t n, const int32_t* src, const int32_t* dst, const float* w, int64_t m0,
+                      unsigned flags, void* stream, prdf_graph** out);
+void prdf_graph_destroy(prdf_graph* g);
+
+/* n and the number of (unique, self-loop-including) edges m. Host outputs. */
+int prdf_graph_size(const prdf_graph* g, int32_t* n_host, int64_t* m_host);
+
+/*
+ * Copy one CSR out: off int64[n+1], adj int32[m] (device). w (float32[m],
+ * nullable) receives the edge weights in the same slot order (weighted
+ * graphs only).
+ */
+int prdf_graph_export_csr(const prdf_graph* g, int which, int64_t* off, int32_t* adj, float* w, void* stream);
+
+/*
+ * Apply a batch update with set semantics (Section 3.3):
+ * E^t = (E^{t-1} \ D) u I, self-loops never deleted (Section 5.1.3).
+ * del_src/del_dst: int32[n_del], ins_src/ins_dst: int32[n_ins] (device).
+ * Rebuilds G and G' in place. del_eff (uint8[n_del], nullable) gets 1 where
+ * the deletion is in Delta^{t-} = E^{t-1} \ E^t; ins_eff (uint8[n_ins],
+ * nullable) gets 1 where the insertion is in Delta^{t+} = E^t \ E^{t-1}.
+ * Weighted graphs take new edges' weights from ins_w (float32[n_ins]), which
+ * is then required.
+ */
+int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, int64_t n_del,
+                           const int32_t* ins_src, const int32_t* ins_dst, const float* ins_w, int64_t n_ins,
+                           uint8_t* del_eff, uint8_t* ins_eff, void* stream);
+
+/*
+ * Degree thresholds between the vertex classes of one CSR's kernels
+ * (Alg. partition generalised to n_thr+1 classes). Class 0 holds
+ * degree <= thr[0], class c holds thr[c-1] < degree <= thr[c], the last class
+ * degree > thr[n_thr-1]. For PRDF_IN the classes are the thread-, warp- and
+ * block-per-vertex rank kernels (n_thr = 2); for PRDF_OUT the thread-, warp-
+ * and block-per-vertex marking kernels (n_thr = 2). thr_host: host int64[n_thr],
+ * strictly increasing, thr[0] >= 0.
+ */
+int prdf_graph_set_thresholds(prdf_graph* g, int which, int n_thr, const int64_t* thr_host);
+
+/*
+ * Alg. partition: stable partition of vertex ids by the degree of one CSR
+ * into the classes above; P int32[n] (device) receives the ids, class by
+ * class, each class in ascending id order; counts_host (host int64[n_thr+1])
+ * receives the class sizes (N_P = counts_host[0] for the paper's two classes).
+ */
+int prdf_partition(prdf_graph* g, int which, int32_t* P, int64_t* counts_host, void* stream);
+
+/* ------------------------------------------------------------- frontier -- */
+
+/*
+ * Alg. affected, initialAffected: for each deletion i with del_mask[i] != 0
+ * (all if del_mask is NULL) set dN[del_src[i]] = 1 and dV[del_dst[i]] = 1; for
+ * each insertion i with ins_mask[i] != 0 set dN[ins_src[i]] = 1. dV, dN:
+ * uint8[n] device arrays, OR-ed into (not cleared).
+ */
+int prdf_initial_affected(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask,
+                          int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins,
+                          uint8_t* dV, uint8_t* dN, void* stream);
+
+/*
+ * Alg. affected, expandAffected: dV[w] = 1 for every w in G.out(u) with
+ * dN[u] != 0, by the thread/warp/block-per-vertex kernels over the out-degree
+ * partition. dV, dN: uint8[n] device; dV is OR-ed into.
+ */
+int prdf_expand_affected(prdf_graph* g, const uint8_t* dN, uint8_t* dV, void* stream);
+
+/* ---------------------------------------------------------------- ranks -- */
+
+/*
+ * Static PageRank, Alg. static with Eq. 1: R = 1/n (or R0 if not NULL, which
+ * is Naive-dynamic, Alg. naive), partition G' by in-degree, then synchronous
+ * pull sweeps until ||R_new - R||_inf <= p->tol or p->max_iter sweeps.
+ * ranks: double[n] device output. R0: double[n] device or NULL.
+ * stats may be NULL.
+ */
+int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, double* ranks, prdf_stats* stats);
+
+/*
+ * DF-P (p->prune = 1) or DF (p->prune = 0) PageRank, Alg. frontier with
+ * Alg. update and Alg. affected, on the graph's current G^t, G^t':
+ * deletions (del_src, del_dst, del_mask) and insertions (ins_src, ins_mask)
+ * as in prdf_initial_affected (pass the effectiveness masks from
+ * prdf_graph_apply_batch to use the effective Delta^{t-}, Delta^{t+});
+ * prev_ranks: R^{t-1}, double[n]; ranks: double[n] output (may alias
+ * prev_ranks). dV_out: optional uint8[n] receiving the final deltaV.
+ */
+int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask,
+                      int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins,
+                      const double* prev_ranks, double* ranks, const prdf_params* p, uint8_t* dV_out,
+                      prdf_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRDF_H */

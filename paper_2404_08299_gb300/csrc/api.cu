@@ -1,0 +1,677 @@
+// C ABI of libprdf: graph handle, batch updates, partitions, frontier, and
+// the Static / DF / DF-P drivers (Alg. static, Alg. frontier of
+// arXiv 2404.08299). See include/prdf.h for the contract of each call.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace prdf {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int Workspace::init() {
+  if (host_i64) return PRDF_OK;
+  PRDF_CUDA(cudaMallocHost((void**)&host_i64, kHostSlots * sizeof(int64_t)));
+  return PRDF_OK;
+}
+
+Workspace::~Workspace() {
+  if (host_i64) cudaFreeHost(host_i64);
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void k_degrees(const int64_t* __restrict__ off, int32_t n, int32_t* __restrict__ deg,
+                          double* __restrict__ inv) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = off[v + 1] - off[v];
+    deg[v] = (int32_t)d;
+    inv[v] = d > 0 ? 1.0 / (double)d : 0.0;
+  }
+}
+
+// x[v] = R0[v] / |out(v)| (R0 = NULL: 1/n)
+__global__ void k_init_x(const double* __restrict__ R0, int32_t n, const double* __restrict__ inv,
+                         double* __restrict__ xa, double* __restrict__ xb) {
+  const double r = 1.0 / (double)n;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const double x = (R0 ? R0[v] : r) * inv[v];
+    xa[v] = x;
+    if (xb) xb[v] = x;
+  }
+}
+
+// R[v] = x[v] * |out(v)|
+__global__ void k_finalize(const double* __restrict__ x, const int32_t* __restrict__ deg, int32_t n,
+                           double* __restrict__ R) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    R[v] = x[v] * (double)deg[v];
+}
+
+__global__ void k_check_ids(const int32_t* a, const int32_t* b, int64_t cnt, int32_t n, int* bad) {
+  int f = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    if (a && (a[i] < 0 || a[i] >= n)) f = 1;
+    if (b && (b[i] < 0 || b[i] >= n)) f = 1;
+  }
+  f = __reduce_or_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0 && f) atomicOr(bad, 1);
+}
+
+// position of (u, v) in a sorted CSR row, or -1
+__device__ __forceinline__ int64_t find_edge(const int64_t* off, const int32_t* adj, int32_t u, int32_t v) {
+  int64_t lo = off[u], hi = off[u + 1];
+  const int64_t e = hi;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (adj[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return (lo < e && adj[lo] == v) ? lo : -1;
+}
+
+__global__ void k_mark_deleted(const int32_t* __restrict__ ds, const int32_t* __restrict__ dd, int64_t n_del,
+                               const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                               uint8_t* __restrict__ deleted) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_del; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = ds[i], v = dd[i];
+    if (u == v) continue;  // self-loops are never deleted
+    const int64_t p = find_edge(off, adj, u, v);
+    if (p >= 0) deleted[p] = 1;
+  }
+}
+
+// edge list of the surviving old edges (deleted slots get row -1) followed by the insertions
+__global__ void k_old_edges(int32_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                            const float* __restrict__ w, const uint8_t* __restrict__ deleted,
+                            int32_t* __restrict__ rows, int32_t* __restrict__ cols, float* __restrict__ wo) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = warp; u < n; u += nw) {
+    for (int64_t j = off[u] + lane; j < off[u + 1]; j += 32) {
+      rows[j] = deleted[j] ? -1 : (int32_t)u;
+      cols[j] = adj[j];
+      if (wo) wo[j] = w[j];
+    }
+  }
+}
+
+__global__ void k_append(const int32_t* __restrict__ is, const int32_t* __restrict__ id, const float* __restrict__ iw,
+                         int64_t n_ins, int64_t at, int32_t* __restrict__ rows, int32_t* __restrict__ cols,
+                         float* __restrict__ wo) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_ins; i += (int64_t)gridDim.x * blockDim.x) {
+    rows[at + i] = is[i];
+    cols[at + i] = id[i];
+    if (wo) wo[at + i] = iw[i];
+  }
+}
+
+__global__ void k_effective(const int32_t* __restrict__ s, const int32_t* __restrict__ d, int64_t cnt, int deletion,
+                            const int64_t* __restrict__ o_off, const int32_t* __restrict__ o_adj,
+                            const int64_t* __restrict__ n_off, const int32_t* __restrict__ n_adj,
+                            uint8_t* __restrict__ eff) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool in_old = find_edge(o_off, o_adj, s[i], d[i]) >= 0;
+    const bool in_new = find_edge(n_off, n_adj, s[i], d[i]) >= 0;
+    eff[i] = deletion ? (in_old && !in_new) : (!in_old && in_new);
+  }
+}
+
+int check_params(const prdf_params* p) {
+  if (!p) {
+    set_error("params is NULL");
+    return PRDF_EINVAL;
+  }
+  if (!(p->alpha > 0.0 && p->alpha < 1.0)) {
+    set_error("alpha must be in (0, 1)");
+    return PRDF_EINVAL;
+  }
+  if (!(p->tol > 0.0) || std::isnan(p->tol)) {
+    set_error("tol must be > 0");
+    return PRDF_EINVAL;
+  }
+  if (p->max_iter < 1) {
+    set_error("max_iter must be >= 1");
+    return PRDF_EINVAL;
+  }
+  if (std::isnan(p->tau_f) || std::isnan(p->tau_p)) {
+    set_error("tau_f / tau_p must not be NaN");
+    return PRDF_EINVAL;
+  }
+  if (p->precision != PRDF_FP64 && p->precision != PRDF_FP32_REFINE) {
+    set_error("unknown precision %d", p->precision);
+    return PRDF_EINVAL;
+  }
+  if (p->accumulate != PRDF_ACC_EXACT && p->accumulate != PRDF_ACC_FP64) {
+    set_error("unknown accumulate mode %d", p->accumulate);
+    return PRDF_EINVAL;
+  }
+  return PRDF_OK;
+}
+
+int ensure_degrees(prdf_graph* g, cudaStream_t s) {
+  PRDF_TRY(g->outdeg.alloc(g->n, s));
+  PRDF_TRY(g->inv_outdeg.alloc(g->n, s));
+  k_degrees<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(g->csr[PRDF_OUT].off.p, g->n, g->outdeg.p, g->inv_outdeg.p);
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+int ensure_partition(prdf_graph* g, int which, cudaStream_t s) {
+  if (g->pvalid[which]) return PRDF_OK;
+  PRDF_TRY(g->P[which].reserve(g->n, s));
+  PRDF_TRY(partition_by_degree(g->csr[which].off.p, g->n, g->thr[which], g->P[which].p, g->pcount[which], g->ws, s));
+  g->pvalid[which] = true;
+  return PRDF_OK;
+}
+
+void class_begins(const prdf_graph* g, int which, int64_t* cb) {
+  const int C = g->thr[which].n + 1;
+  cb[0] = 0;
+  for (int c = 0; c < C; ++c) cb[c + 1] = cb[c] + g->pcount[which][c];
+}
+
+int check_ids(prdf_graph* g, const int32_t* a, const int32_t* b, int64_t cnt, cudaStream_t s) {
+  if (cnt == 0) return PRDF_OK;
+  if ((!a && !b)) return PRDF_OK;
+  DBuf<int> bad;
+  PRDF_TRY(bad.alloc(1, s));
+  PRDF_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+  k_check_ids<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(a, b, cnt, g->n, bad.p);
+  PRDF_LAUNCH_CHECK();
+  PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  if (*(int*)g->ws.host_i64) {
+    set_error("vertex id outside [0, %d)", g->n);
+    return PRDF_EINVAL;
+  }
+  return PRDF_OK;
+}
+
+struct Timer {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  ~Timer() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+  int init() {
+    for (auto& x : e) PRDF_CUDA(cudaEventCreate(&x));
+    return PRDF_OK;
+  }
+};
+
+struct IterResult {
+  int iters = 0;          // sweeps up to and including the first converged one (or max_iter)
+  int converged = 0;
+  double final_delta = 0;
+  int final_buf = 0;      // 0: xa holds the result, 1: xb
+  int launched = 0;       // sweeps issued
+  float ms_sweep = 0;     // device time of the first `iters` sweeps (time_sweeps)
+  long long kernels = 0;  // kernels launched
+};
+
+int nonempty_classes(const int64_t* cb, int nclass) {
+  int k = 0;
+  for (int c = 0; c < nclass; ++c) k += cb[c + 1] > cb[c] ? 1 : 0;
+  return k;
+}
+
+// Launch sweeps (and, for DF/DF-P, the expand after each) until the L-inf
+// change of a sweep is <= tol or max_iter sweeps ran. The host reads the
+// residual every check_every sweeps; sweeps launched past convergence exit at
+// once on the device.
+int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, cudaStream_t s) {
+  const int n = g->n;
+  const int max_iter = p->max_iter;
+  PRDF_TRY(g->resid.reserve((size_t)max_iter + 1, s));
+  PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t) * ((size_t)max_iter + 1), s));
+  int64_t cb[prdf::kMaxThr + 2], cbo[prdf::kMaxThr + 2];
+  class_begins(g, PRDF_IN, cb);
+  const int nci = g->thr[PRDF_IN].n + 1, nco = g->thr[PRDF_OUT].n + 1;
+  if (dynamic) class_begins(g, PRDF_OUT, cbo);
+  const int kps = nonempty_classes(cb, nci) + (dynamic ? nonempty_classes(cbo, nco) : 0);
+  SweepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.off = g->csr[PRDF_IN].off.p;
+  a.adj = g->csr[PRDF_IN].adj.p;
+  a.P = g->P[PRDF_IN].p;
+  a.deg = g->outdeg.p;
+  a.inv_deg = g->inv_outdeg.p;
+  a.alpha = p->alpha;
+  a.c0 = (1.0 - p->alpha) / (double)n;
+  a.tol = p->tol;
+  a.dV = g->dV.p;
+  a.dN = g->dN.p;
+  a.wrote = g->wrote.p;
+  a.tau_f = p->tau_f;
+  a.tau_p = p->tau_p;
+  a.prune = p->prune;
+  const int check = p->check_every > 0 ? p->check_every : 8;
+  const bool exact = p->accumulate == PRDF_ACC_EXACT;
+  const bool timed = p->time_sweeps != 0;
+  std::vector<cudaEvent_t> ev;
+  struct EvGuard {
+    std::vector<cudaEvent_t>& v;
+    ~EvGuard() {
+      for (auto e : v) cudaEventDestroy(e);
+    }
+  } guard{ev};
+  int launched = 0;
+  bool done = false;
+  while (launched < max_iter && !done) {
+    const int upto = (launched + check < max_iter) ? launched + check : max_iter;
+    for (int i = launched; i < upto; ++i) {
+      a.x = (i & 1) ? g->xb.p : g->xa.p;
+      a.xn = (i & 1) ? g->xa.p : g->xb.p;
+      a.resid = g->resid.p + i;
+      a.prev = i > 0 ? g->resid.p + i - 1 : nullptr;
+      if (dynamic) PRDF_CUDA(cudaMemsetAsync(g->dN.p, 0, (size_t)n, s));
+      if (timed) {
+        cudaEvent_t e0, e1;
+        PRDF_CUDA(cudaEventCreate(&e0));
+        ev.push_back(e0);
+        PRDF_CUDA(cudaEventCreate(&e1));
+        ev.push_back(e1);
+        PRDF_CUDA(cudaEventRecord(e0, s));
+      }
+      PRDF_TRY(launch_sweep(a, cb, nci, exact, dynamic, s));
+      if (timed) PRDF_CUDA(cudaEventRecord(ev.back(), s));
+      if (dynamic)
+        PRDF_TRY(launch_expand(g->csr[PRDF_OUT].off.p, g->csr[PRDF_OUT].adj.p, g->P[PRDF_OUT].p, cbo, nco, g->dN.p,
+                               g->dV.p, g->resid.p + i, p->tol, s));
+    }
+    launched = upto;
+    PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid.p + launched - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    PRDF_CUDA(cudaStreamSynchronize(s));
+    double last;
+    memcpy(&last, g->ws.host_i64, sizeof(double));
+    done = last <= p->tol;
+  }
+  std::vector<uint64_t> hr((size_t)launched);
+  PRDF_CUDA(cudaMemcpyAsync(hr.data(), g->resid.p, sizeof(uint64_t) * launched, cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  int k = launched - 1;
+  res->converged = 0;
+  for (int i = 0; i < launched; ++i) {
+    double d;
+    memcpy(&d, &hr[i], sizeof(double));
+    if (d <= p->tol) {
+      k = i;
+      res->converged = 1;
+      break;
+    }
+  }
+  memcpy(&res->final_delta, &hr[k], sizeof(double));
+  res->iters = k + 1;
+  res->final_buf = (k & 1) ? 0 : 1;  // sweep k wrote xb if k is even
+  res->launched = launched;
+  res->kernels = (long long)launched * kps;
+  res->ms_sweep = 0;
+  if (timed)
+    for (int i = 0; i < res->iters; ++i) {
+      float ms = 0;
+      PRDF_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+      res->ms_sweep += ms;
+    }
+  return PRDF_OK;
+}
+
+int alloc_solver(prdf_graph* g, bool dynamic, cudaStream_t s) {
+  PRDF_TRY(g->xa.reserve(g->n, s));
+  PRDF_TRY(g->xb.reserve(g->n, s));
+  if (dynamic) {
+    PRDF_TRY(g->dV.reserve(g->n, s));
+    PRDF_TRY(g->dN.reserve(g->n, s));
+    PRDF_TRY(g->wrote.reserve(g->n, s));
+  }
+  PRDF_TRY(g->counter.reserve(1, s));
+  return PRDF_OK;
+}
+
+}  // namespace
+}  // namespace prdf
+
+using namespace prdf;
+
+extern "C" {
+
+void prdf_params_default(prdf_params* p) {
+  if (!p) return;
+  p->alpha = 0.85;
+  p->tol = 1e-10;
+  p->tau_f = 1e-6;
+  p->tau_p = 1e-6;
+  p->max_iter = 500;
+  p->precision = PRDF_FP64;
+  p->tol_fp32_rel = 1e-6;
+  p->accumulate = PRDF_ACC_EXACT;
+  p->prune = 1;
+  p->check_every = 8;
+  p->time_sweeps = 0;
+  p->stream = nullptr;
+}
+
+const char* prdf_last_error(void) { return g_err; }
+
+const char* prdf_strerror(int code) {
+  switch (code) {
+    case PRDF_OK: return "ok";
+    case PRDF_EINVAL: return "invalid argument";
+    case PRDF_ENOMEM: return "out of device memory";
+    case PRDF_ECUDA: return "CUDA error";
+    case PRDF_ETIMEOUT: return "bounded device wait expired";
+    case PRDF_ESTATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+int prdf_graph_create(int32_t n, const int32_t* src, const int32_t* dst, const float* w, int64_t m0, unsigned flags,
+                      void* stream, prdf_graph** out) {
+  if (!out || n < 1 || m0 < 0 || (m0 > 0 && (!src || !dst))) {
+    set_error("prdf_graph_create: bad arguments (n=%d, m0=%lld)", n, (long long)m0);
+    return PRDF_EINVAL;
+  }
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  prdf_graph* g = new (std::nothrow) prdf_graph();
+  if (!g) {
+    set_error("host allocation failed");
+    return PRDF_ENOMEM;
+  }
+  g->n = n;
+  g->weighted = w != nullptr;
+  g->stream = s;
+  // default class thresholds: thread <= 8, sub-warp <= 64, warp <= 2048, block above
+  for (int which = 0; which < 2; ++which) {
+    g->thr[which].n = 3;
+    g->thr[which].thr[0] = 8;
+    g->thr[which].thr[1] = 64;
+    g->thr[which].thr[2] = 2048;
+  }
+  int r = g->ws.init();
+  const bool loops = (flags & PRDF_ADD_SELF_LOOPS) != 0;
+  if (r == PRDF_OK) r = build_csr(n, m0, src, dst, w, loops, false, g->csr[PRDF_OUT], g->ws, s);
+  if (r == PRDF_OK) r = build_csr(n, m0, dst, src, w, loops, false, g->csr[PRDF_IN], g->ws, s);
+  if (r == PRDF_OK) r = ensure_degrees(g, s);
+  if (r == PRDF_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("graph build: %s", cudaGetErrorString(cudaGetLastError()));
+    r = PRDF_ECUDA;
+  }
+  if (r != PRDF_OK) {
+    delete g;
+    return r;
+  }
+  *out = g;
+  return PRDF_OK;
+}
+
+void prdf_graph_destroy(prdf_graph* g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->stream);
+  delete g;
+}
+
+int prdf_graph_size(const prdf_graph* g, int32_t* n_host, int64_t* m_host) {
+  if (!g) {
+    set_error("graph is NULL");
+    return PRDF_EINVAL;
+  }
+  if (n_host) *n_host = g->n;
+  if (m_host) *m_host = g->csr[PRDF_OUT].m;
+  return PRDF_OK;
+}
+
+int prdf_graph_export_csr(const prdf_graph* g, int which, int64_t* off, int32_t* adj, float* w, void* stream) {
+  if (!g || (which != PRDF_OUT && which != PRDF_IN)) {
+    set_error("bad graph or CSR selector");
+    return PRDF_EINVAL;
+  }
+  if (w && !g->weighted) {
+    set_error("graph has no weights");
+    return PRDF_ESTATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const Csr& c = g->csr[which];
+  if (off) PRDF_CUDA(cudaMemcpyAsync(off, c.off.p, sizeof(int64_t) * ((size_t)g->n + 1), cudaMemcpyDeviceToDevice, s));
+  if (adj && c.m) PRDF_CUDA(cudaMemcpyAsync(adj, c.adj.p, sizeof(int32_t) * (size_t)c.m, cudaMemcpyDeviceToDevice, s));
+  if (w && c.m) PRDF_CUDA(cudaMemcpyAsync(w, c.w.p, sizeof(float) * (size_t)c.m, cudaMemcpyDeviceToDevice, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  return PRDF_OK;
+}
+
+int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, int64_t n_del,
+                           const int32_t* ins_src, const int32_t* ins_dst, const float* ins_w, int64_t n_ins,
+                           uint8_t* del_eff, uint8_t* ins_eff, void* stream) {
+  if (!g || n_del < 0 || n_ins < 0 || (n_del > 0 && (!del_src || !del_dst)) || (n_ins > 0 && (!ins_src || !ins_dst))) {
+    set_error("prdf_graph_apply_batch: bad arguments");
+    return PRDF_EINVAL;
+  }
+  if (g->weighted && n_ins > 0 && !ins_w) {
+    set_error("weighted graph: insertions need weights");
+    return PRDF_ESTATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  PRDF_TRY(check_ids(g, del_src, del_dst, n_del, s));
+  PRDF_TRY(check_ids(g, ins_src, ins_dst, n_ins, s));
+  const int32_t n = g->n;
+  Csr& old = g->csr[PRDF_OUT];
+  const int64_t m = old.m;
+  DBuf<uint8_t> deleted;
+  PRDF_TRY(deleted.alloc((size_t)m, s));
+  PRDF_CUDA(cudaMemsetAsync(deleted.p, 0, (size_t)m, s));
+  if (n_del) k_mark_deleted<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_src, del_dst, n_del, old.off.p, old.adj.p, deleted.p);
+  const int64_t tot = m + n_ins;
+  DBuf<int32_t> rows, cols;
+  DBuf<float> ww;
+  PRDF_TRY(rows.alloc(tot, s));
+  PRDF_TRY(cols.alloc(tot, s));
+  if (g->weighted) PRDF_TRY(ww.alloc(tot, s));
+  k_old_edges<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(n, old.off.p, old.adj.p, g->weighted ? old.w.p : nullptr,
+                                                                        deleted.p, rows.p, cols.p, ww.p);
+  if (n_ins) k_append<<<grid_for(n_ins, kThreads), kThreads, 0, s>>>(ins_src, ins_dst, ins_w, n_ins, m, rows.p, cols.p, ww.p);
+  PRDF_LAUNCH_CHECK();
+  Csr nout, nin;
+  PRDF_TRY(build_csr(n, tot, rows.p, cols.p, ww.p, true, true, nout, g->ws, s));
+  PRDF_TRY(build_csr(n, tot, cols.p, rows.p, ww.p, true, true, nin, g->ws, s));
+  if (del_eff && n_del)
+    k_effective<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_src, del_dst, n_del, 1, old.off.p, old.adj.p,
+                                                               nout.off.p, nout.adj.p, del_eff);
+  if (ins_eff && n_ins)
+    k_effective<<<grid_for(n_ins, kThreads), kThreads, 0, s>>>(ins_src, ins_dst, n_ins, 0, old.off.p, old.adj.p,
+                                                               nout.off.p, nout.adj.p, ins_eff);
+  PRDF_LAUNCH_CHECK();
+  g->csr[PRDF_OUT] = static_cast<Csr&&>(nout);
+  g->csr[PRDF_IN] = static_cast<Csr&&>(nin);
+  g->csr[PRDF_OUT].m = nout.m;
+  g->csr[PRDF_IN].m = nin.m;
+  PRDF_TRY(ensure_degrees(g, s));
+  g->pvalid[0] = g->pvalid[1] = false;
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  return PRDF_OK;
+}
+
+int prdf_graph_set_thresholds(prdf_graph* g, int which, int n_thr, const int64_t* thr_host) {
+  if (!g || (which != PRDF_OUT && which != PRDF_IN) || n_thr < 1 || n_thr > kMaxThr || !thr_host) {
+    set_error("prdf_graph_set_thresholds: bad arguments");
+    return PRDF_EINVAL;
+  }
+  if (thr_host[0] < 0) {
+    set_error("thresholds must be >= 0");
+    return PRDF_EINVAL;
+  }
+  for (int i = 1; i < n_thr; ++i)
+    if (thr_host[i] <= thr_host[i - 1]) {
+      set_error("thresholds must be strictly increasing");
+      return PRDF_EINVAL;
+    }
+  g->thr[which].n = n_thr;
+  for (int i = 0; i < kMaxThr; ++i) g->thr[which].thr[i] = i < n_thr ? thr_host[i] : 0;
+  g->pvalid[which] = false;
+  return PRDF_OK;
+}
+
+int prdf_partition(prdf_graph* g, int which, int32_t* P, int64_t* counts_host, void* stream) {
+  if (!g || (which != PRDF_OUT && which != PRDF_IN) || !P || !counts_host) {
+    set_error("prdf_partition: bad arguments");
+    return PRDF_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  g->pvalid[which] = false;
+  PRDF_TRY(ensure_partition(g, which, s));
+  PRDF_CUDA(cudaMemcpyAsync(P, g->P[which].p, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToDevice, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  for (int c = 0; c <= g->thr[which].n; ++c) counts_host[c] = g->pcount[which][c];
+  return PRDF_OK;
+}
+
+int prdf_initial_affected(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask,
+                          int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins, uint8_t* dV,
+                          uint8_t* dN, void* stream) {
+  if (!g || !dV || !dN || n_del < 0 || n_ins < 0 || (n_del && (!del_src || !del_dst)) || (n_ins && !ins_src)) {
+    set_error("prdf_initial_affected: bad arguments");
+    return PRDF_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  PRDF_TRY(check_ids(g, del_src, del_dst, n_del, s));
+  PRDF_TRY(check_ids(g, ins_src, nullptr, n_ins, s));
+  PRDF_TRY(launch_initial_affected(del_src, del_dst, del_mask, n_del, ins_src, ins_mask, n_ins, dV, dN, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  return PRDF_OK;
+}
+
+int prdf_expand_affected(prdf_graph* g, const uint8_t* dN, uint8_t* dV, void* stream) {
+  if (!g || !dN || !dV) {
+    set_error("prdf_expand_affected: bad arguments");
+    return PRDF_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  PRDF_TRY(ensure_partition(g, PRDF_OUT, s));
+  int64_t cb[kMaxThr + 2];
+  class_begins(g, PRDF_OUT, cb);
+  PRDF_TRY(launch_expand(g->csr[PRDF_OUT].off.p, g->csr[PRDF_OUT].adj.p, g->P[PRDF_OUT].p, cb, g->thr[PRDF_OUT].n + 1,
+                         dN, dV, nullptr, 0.0, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  return PRDF_OK;
+}
+
+int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, double* ranks, prdf_stats* stats) {
+  if (!g || !ranks) {
+    set_error("prdf_pagerank_static: bad arguments");
+    return PRDF_EINVAL;
+  }
+  PRDF_TRY(check_params(p));
+  cudaStream_t s = (cudaStream_t)p->stream;
+  Timer t;
+  PRDF_TRY(t.init());
+  PRDF_TRY(alloc_solver(g, false, s));
+  PRDF_CUDA(cudaEventRecord(t.e[0], s));
+  // Alg. static: initialise ranks, partition G' by in-degree, iterate
+  k_init_x<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(R0, g->n, g->inv_outdeg.p, g->xa.p, nullptr);
+  PRDF_LAUNCH_CHECK();
+  g->pvalid[PRDF_IN] = false;
+  PRDF_TRY(ensure_partition(g, PRDF_IN, s));
+  PRDF_CUDA(cudaEventRecord(t.e[1], s));
+  IterResult it;
+  PRDF_TRY(iterate(g, p, false, &it, s));
+  k_finalize<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, g->outdeg.p, g->n, ranks);
+  PRDF_LAUNCH_CHECK();
+  PRDF_CUDA(cudaEventRecord(t.e[2], s));
+  PRDF_CUDA(cudaEventSynchronize(t.e[2]));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations = it.iters;
+    stats->converged = it.converged;
+    stats->final_delta = it.final_delta;
+    stats->sweeps_launched = it.launched;
+    cudaEventElapsedTime(&stats->ms_total, t.e[0], t.e[2]);
+    cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
+    cudaEventElapsedTime(&stats->ms_iterate, t.e[1], t.e[2]);
+    stats->ms_sweep = it.ms_sweep;
+    stats->edges_processed = (long long)it.iters * g->csr[PRDF_IN].m;
+    // init + partition (count, 3 scan kernels, scatter) + sweeps + finalize
+    stats->kernel_launches = 1 + 5 + it.kernels + 1;
+  }
+  return PRDF_OK;
+}
+
+int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask,
+                      int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins,
+                      const double* prev_ranks, double* ranks, const prdf_params* p, uint8_t* dV_out,
+                      prdf_stats* stats) {
+  if (!g || !prev_ranks || !ranks || n_del < 0 || n_ins < 0 || (n_del && (!del_src || !del_dst)) ||
+      (n_ins && !ins_src)) {
+    set_error("prdf_pagerank_dfp: bad arguments");
+    return PRDF_EINVAL;
+  }
+  PRDF_TRY(check_params(p));
+  cudaStream_t s = (cudaStream_t)p->stream;
+  PRDF_TRY(check_ids(g, del_src, del_dst, n_del, s));
+  PRDF_TRY(check_ids(g, ins_src, nullptr, n_ins, s));
+  Timer t;
+  PRDF_TRY(t.init());
+  PRDF_TRY(alloc_solver(g, true, s));
+  const int n = g->n;
+  PRDF_CUDA(cudaEventRecord(t.e[0], s));
+  // Alg. frontier: R = Rnew = R^{t-1}; partition G and G'; mark; iterate
+  k_init_x<<<grid_for(n, kThreads), kThreads, 0, s>>>(prev_ranks, n, g->inv_outdeg.p, g->xa.p, g->xb.p);
+  PRDF_LAUNCH_CHECK();
+  g->pvalid[PRDF_OUT] = g->pvalid[PRDF_IN] = false;
+  PRDF_TRY(ensure_partition(g, PRDF_OUT, s));
+  PRDF_TRY(ensure_partition(g, PRDF_IN, s));
+  PRDF_CUDA(cudaEventRecord(t.e[1], s));
+  PRDF_CUDA(cudaMemsetAsync(g->dV.p, 0, (size_t)n, s));
+  PRDF_CUDA(cudaMemsetAsync(g->dN.p, 0, (size_t)n, s));
+  PRDF_CUDA(cudaMemsetAsync(g->wrote.p, 0, (size_t)n, s));
+  PRDF_TRY(launch_initial_affected(del_src, del_dst, del_mask, n_del, ins_src, ins_mask, n_ins, g->dV.p, g->dN.p, s));
+  int64_t cbo[kMaxThr + 2];
+  class_begins(g, PRDF_OUT, cbo);
+  PRDF_TRY(launch_expand(g->csr[PRDF_OUT].off.p, g->csr[PRDF_OUT].adj.p, g->P[PRDF_OUT].p, cbo, g->thr[PRDF_OUT].n + 1,
+                         g->dN.p, g->dV.p, nullptr, 0.0, s));
+  PRDF_TRY(count_flags(g->dV.p, n, g->counter.p, s));
+  PRDF_CUDA(cudaEventRecord(t.e[2], s));
+  PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64 + 8, g->counter.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  IterResult it;
+  PRDF_TRY(iterate(g, p, true, &it, s));  // synchronises the stream
+  const long long aff0 = (long long)g->ws.host_i64[8];
+  k_finalize<<<grid_for(n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, g->outdeg.p, n, ranks);
+  PRDF_LAUNCH_CHECK();
+  PRDF_CUDA(cudaEventRecord(t.e[3], s));
+  if (dV_out) PRDF_CUDA(cudaMemcpyAsync(dV_out, g->dV.p, (size_t)n, cudaMemcpyDeviceToDevice, s));
+  PRDF_CUDA(cudaEventSynchronize(t.e[3]));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations = it.iters;
+    stats->converged = it.converged;
+    stats->final_delta = it.final_delta;
+    stats->sweeps_launched = it.launched;
+    cudaEventElapsedTime(&stats->ms_total, t.e[0], t.e[3]);
+    cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
+    cudaEventElapsedTime(&stats->ms_mark, t.e[1], t.e[2]);
+    cudaEventElapsedTime(&stats->ms_iterate, t.e[2], t.e[3]);
+    stats->ms_sweep = it.ms_sweep;
+    stats->edges_processed = -1;
+    stats->affected_initial = aff0;
+    int64_t cbo2[kMaxThr + 2];
+    class_begins(g, PRDF_OUT, cbo2);
+    // init + 2 partitions + initial marking + expand + count + sweeps/expands + finalize
+    stats->kernel_launches = 1 + 10 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo2, g->thr[PRDF_OUT].n + 1) +
+                             1 + it.kernels + 1;
+  }
+  return PRDF_OK;
+}
+
+}  // extern "C"

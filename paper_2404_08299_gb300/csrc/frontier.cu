@@ -1,0 +1,112 @@
+// Affected-vertex marking (Alg. affected, Appendix A.3 of arXiv 2404.08299):
+// initialAffected over the batch, expandAffected over the out-degree
+// partition of G with thread-, sub-warp-, warp- and block-per-vertex
+// kernels. Flags are uint8; every store writes 1, so concurrent marks of the
+// same vertex need no atomics.
+#include "internal.cuh"
+
+namespace prdf {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void k_initial_affected(const int32_t* __restrict__ del_src, const int32_t* __restrict__ del_dst,
+                                   const uint8_t* __restrict__ del_mask, int64_t n_del,
+                                   const int32_t* __restrict__ ins_src, const uint8_t* __restrict__ ins_mask,
+                                   int64_t n_ins, uint8_t* __restrict__ dV, uint8_t* __restrict__ dN) {
+  const int64_t tot = n_del + n_ins;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n_del) {
+      if (del_mask && !del_mask[i]) continue;
+      dN[del_src[i]] = 1;  // out-neighbours of the source are affected
+      dV[del_dst[i]] = 1;  // the target is affected
+    } else {
+      const int64_t k = i - n_del;
+      if (ins_mask && !ins_mask[k]) continue;
+      dN[ins_src[k]] = 1;
+    }
+  }
+}
+
+__device__ __forceinline__ bool converged(const uint64_t* r, double tol) { return r && bitsd(*r) <= tol; }
+
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_expand_group(const int64_t* __restrict__ off,
+                                                           const int32_t* __restrict__ adj,
+                                                           const int32_t* __restrict__ P, int64_t begin, int64_t end,
+                                                           const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
+                                                           const uint64_t* resid, double tol) {
+  if (converged(resid, tol)) return;
+  const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
+  const int64_t gid = (blockIdx.x * (int64_t)kThreads + threadIdx.x) / G;
+  const int64_t ng = ((int64_t)gridDim.x * kThreads) / G;
+  for (int64_t i = begin + gid; i < end; i += ng) {
+    const int32_t u = P[i];
+    if (!dN[u]) continue;
+    const int64_t b = off[u], e = off[u + 1];
+    for (int64_t j = b + lane; j < e; j += G) dV[adj[j]] = 1;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_expand_block(const int64_t* __restrict__ off,
+                                                           const int32_t* __restrict__ adj,
+                                                           const int32_t* __restrict__ P, int64_t begin, int64_t end,
+                                                           const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
+                                                           const uint64_t* resid, double tol) {
+  if (converged(resid, tol)) return;
+  for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
+    const int32_t u = P[i];
+    if (!dN[u]) continue;
+    const int64_t b = off[u], e = off[u + 1];
+    for (int64_t j = b + threadIdx.x; j < e; j += kThreads) dV[adj[j]] = 1;
+  }
+}
+
+__global__ void k_count_flags(const uint8_t* __restrict__ f, int64_t n, unsigned long long* __restrict__ out) {
+  int64_t c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    c += f[i] ? 1 : 0;
+  c = warp_sum_i64(c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+
+}  // namespace
+
+int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask, int64_t n_del,
+                            const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins, uint8_t* dV, uint8_t* dN,
+                            cudaStream_t s) {
+  if (n_del + n_ins == 0) return PRDF_OK;
+  k_initial_affected<<<grid_for(n_del + n_ins, kThreads), kThreads, 0, s>>>(del_src, del_dst, del_mask, n_del, ins_src,
+                                                                             ins_mask, n_ins, dV, dN);
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, const int64_t* cb, int nclass,
+                  const uint8_t* dN, uint8_t* dV, const uint64_t* resid, double tol, cudaStream_t s) {
+  const int maxg = kSMs * 8;
+  for (int c = 0; c < nclass; ++c) {
+    const int64_t b = cb[c], e = cb[c + 1];
+    if (e <= b) continue;
+    const int64_t cnt = e - b;
+    const int kind = (nclass == 4) ? c : (c == nclass - 1 ? 3 : c);
+    switch (kind) {
+      case 0: k_expand_group<1><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, resid, tol); break;
+      case 1: k_expand_group<8><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, resid, tol); break;
+      case 2: k_expand_group<32><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, resid, tol); break;
+      default: k_expand_block<<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, resid, tol); break;
+    }
+  }
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+int count_flags(const uint8_t* f, int64_t n, unsigned long long* dev_out, cudaStream_t s) {
+  PRDF_CUDA(cudaMemsetAsync(dev_out, 0, sizeof(unsigned long long), s));
+  k_count_flags<<<grid_for(n, kThreads, kSMs * 4), kThreads, 0, s>>>(f, n, dev_out);
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+}  // namespace prdf

@@ -1,0 +1,430 @@
+// CSR construction on the device: the CSR of G and of its transpose G'
+// (Section 4.1, 4.3 of arXiv 2404.08299) from an edge list, with duplicate
+// edges merged and exactly one self-loop per vertex (Section 3.1, 5.1.3).
+//
+// Pipeline (all hand-written kernels):
+//   row histogram -> exclusive scan -> atomic scatter into row buckets ->
+//   per-row sort + unique, by row-length class:
+//     <= 8      one thread, 19-comparator sorting network in registers
+//     <= 32     one warp, bitonic network over shuffles
+//     <= 16384  one block, bitonic sort in shared memory
+//     larger    one bit per possible column (bitmap), emitted in order
+//   -> exclusive scan of unique counts -> compaction into the final CSR.
+// Rows are sorted by 64-bit composite keys (column << 32 | ~weight bits), so
+// the first entry of each run of equal columns carries the largest weight.
+#include "internal.cuh"
+
+namespace prdf {
+
+namespace {
+
+constexpr uint64_t kSent = ~0ull;
+constexpr int kThrThread = 8;
+constexpr int kThrWarp = 32;
+constexpr int kThrBlock = 16384;
+constexpr int kSortBlockThreads = 512;
+constexpr int64_t kBitmapBudget = 512ll << 20;  // bytes of row bitmaps per pass
+constexpr int kHugeWordsPerThread = 32;
+constexpr int kHugeChunkWords = 256 * kHugeWordsPerThread;
+
+__device__ __forceinline__ bool entry_ok(int32_t r, int32_t c) { return r >= 0 && c >= 0; }
+
+__device__ __forceinline__ uint64_t make_key(int32_t col, float w) {
+  return ((uint64_t)(uint32_t)col << 32) | (uint64_t)(uint32_t)(~__float_as_uint(w));
+}
+__device__ __forceinline__ int32_t key_col(uint64_t k) { return (int32_t)(k >> 32); }
+__device__ __forceinline__ float key_w(uint64_t k) { return __uint_as_float(~(uint32_t)(k & 0xFFFFFFFFull)); }
+
+__device__ __forceinline__ void cswap(uint64_t& a, uint64_t& b) {
+  const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+  a = lo;
+  b = hi;
+}
+
+__global__ void k_validate(const int32_t* __restrict__ rows, const int32_t* __restrict__ cols,
+                           const float* __restrict__ w, int64_t m0, int32_t n, int allow_skip, int* bad) {
+  int flag = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m0; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rows[i], c = cols[i];
+    const bool skip = allow_skip && !entry_ok(r, c);
+    if (!skip && (r < 0 || r >= n || c < 0 || c >= n)) flag |= 1;
+    if (!skip && w) {
+      const float x = w[i];
+      if (!(x > 0.f) || !isfinite(x)) flag |= 2;
+    }
+  }
+  flag = __reduce_or_sync(0xffffffffu, flag);
+  if ((threadIdx.x & 31) == 0 && flag) atomicOr(bad, flag);
+}
+
+__global__ void k_fill_u32(uint32_t* a, int64_t n, uint32_t v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+__global__ void k_row_count(const int32_t* __restrict__ rows, const int32_t* __restrict__ cols, int64_t m0,
+                            uint32_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m0; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rows[i], c = cols[i];
+    if (entry_ok(r, c)) atomicAdd(&cnt[r], 1u);
+  }
+}
+
+__global__ void k_init_rows(int32_t n, const int64_t* __restrict__ start, uint32_t* __restrict__ fill,
+                            uint64_t* __restrict__ tmp) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    fill[v] = 1;
+    tmp[start[v]] = make_key((int32_t)v, 0.f);  // self-loop; weight 0 marks "added"
+  }
+}
+
+__global__ void k_scatter(const int32_t* __restrict__ rows, const int32_t* __restrict__ cols,
+                          const float* __restrict__ w, int64_t m0, const int64_t* __restrict__ start,
+                          uint32_t* __restrict__ fill, uint64_t* __restrict__ tmp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m0; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rows[i], c = cols[i];
+    if (!entry_ok(r, c)) continue;
+    const int64_t pos = start[r] + atomicAdd(&fill[r], 1u);
+    tmp[pos] = make_key(c, w ? w[i] : 0.f);
+  }
+}
+
+// ---- rows of length <= 8: one thread, Batcher odd-even merge network ----
+__global__ void k_sort_thread(const int32_t* __restrict__ list, int64_t count, const int64_t* __restrict__ start,
+                              const uint64_t* __restrict__ tmp, uint64_t* __restrict__ out, uint32_t* __restrict__ ucnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = list[i];
+    const int64_t b = start[v];
+    const int L = (int)(start[v + 1] - b);
+    uint64_t k[kThrThread];
+#pragma unroll
+    for (int j = 0; j < kThrThread; ++j) k[j] = j < L ? tmp[b + j] : kSent;
+    cswap(k[0], k[1]); cswap(k[2], k[3]); cswap(k[4], k[5]); cswap(k[6], k[7]);
+    cswap(k[0], k[2]); cswap(k[1], k[3]); cswap(k[4], k[6]); cswap(k[5], k[7]);
+    cswap(k[1], k[2]); cswap(k[5], k[6]);
+    cswap(k[0], k[4]); cswap(k[1], k[5]); cswap(k[2], k[6]); cswap(k[3], k[7]);
+    cswap(k[2], k[4]); cswap(k[3], k[5]);
+    cswap(k[1], k[2]); cswap(k[3], k[4]); cswap(k[5], k[6]);
+    uint32_t u = 0;
+#pragma unroll
+    for (int j = 0; j < kThrThread; ++j) {
+      const bool keep = k[j] != kSent && (j == 0 || key_col(k[j]) != key_col(k[j - 1]));
+      if (keep) out[b + u++] = k[j];
+    }
+    ucnt[v] = u;
+  }
+}
+
+// ---- rows of length <= 32: one warp, bitonic over shuffles ----
+__global__ void k_sort_warp(const int32_t* __restrict__ list, int64_t count, const int64_t* __restrict__ start,
+                            const uint64_t* __restrict__ tmp, uint64_t* __restrict__ out, uint32_t* __restrict__ ucnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < count; i += nwarps) {
+    const int32_t v = list[i];
+    const int64_t b = start[v];
+    const int L = (int)(start[v + 1] - b);
+    uint64_t key = lane < L ? tmp[b + lane] : kSent;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const uint64_t o = __shfl_xor_sync(0xffffffffu, key, j);
+        const bool up = (lane & k) == 0;
+        const bool lower = (lane & j) == 0;
+        key = (lower == up) ? (key < o ? key : o) : (key < o ? o : key);
+      }
+    }
+    const uint64_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool keep = key != kSent && (lane == 0 || key_col(prev) != key_col(key));
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) out[b + __popc(bal & ((1u << lane) - 1u))] = key;
+    if (lane == 0) ucnt[v] = __popc(bal);
+  }
+}
+
+// block-wide exclusive scan for NT threads (NT a multiple of 32, <= 1024)
+template <int NT>
+__device__ __forceinline__ uint32_t block_scan_u32(uint32_t v, uint32_t* total, uint32_t* sh /* NT/32 */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) sh[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < NT / 32 ? sh[lane] : 0;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < NT / 32) sh[lane] = wi - w;
+    if (lane == NT / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  const uint32_t r = incl - v + sh[wid];
+  __syncthreads();
+  return r;
+}
+
+// ---- rows of length <= 16384: one block, bitonic sort in shared memory ----
+__global__ void __launch_bounds__(kSortBlockThreads) k_sort_block(const int32_t* __restrict__ list, int64_t count,
+                                                                  const int64_t* __restrict__ start,
+                                                                  const uint64_t* __restrict__ tmp,
+                                                                  uint64_t* __restrict__ out,
+                                                                  uint32_t* __restrict__ ucnt) {
+  extern __shared__ uint64_t sk[];
+  __shared__ uint32_t scan_sh[kSortBlockThreads / 32];
+  __shared__ uint32_t total;
+  for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
+    const int32_t v = list[i];
+    const int64_t b = start[v];
+    const int L = (int)(start[v + 1] - b);
+    int P2 = 64;
+    while (P2 < L) P2 <<= 1;
+    for (int j = threadIdx.x; j < P2; j += kSortBlockThreads) sk[j] = j < L ? tmp[b + j] : kSent;
+    __syncthreads();
+    for (int k = 2; k <= P2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < P2; t += kSortBlockThreads) {
+          const int p = t ^ j;
+          if (p > t) {
+            const uint64_t a = sk[t], c = sk[p];
+            const bool up = (t & k) == 0;
+            if ((a > c) == up) {
+              sk[t] = c;
+              sk[p] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // stable compaction of the first entry of each column run
+    const int per = P2 / kSortBlockThreads > 0 ? P2 / kSortBlockThreads : 1;
+    const int j0 = threadIdx.x * per;
+    uint32_t mine = 0;
+    for (int j = j0; j < j0 + per && j < P2; ++j)
+      mine += (sk[j] != kSent && (j == 0 || key_col(sk[j]) != key_col(sk[j - 1]))) ? 1u : 0u;
+    uint32_t pos = block_scan_u32<kSortBlockThreads>(mine, &total, scan_sh);
+    for (int j = j0; j < j0 + per && j < P2; ++j)
+      if (sk[j] != kSent && (j == 0 || key_col(sk[j]) != key_col(sk[j - 1]))) out[b + pos++] = sk[j];
+    if (threadIdx.x == 0) ucnt[v] = total;
+    __syncthreads();
+  }
+}
+
+// ---- longer rows: one bit per column ----
+__global__ void k_huge_set(const int32_t* __restrict__ rowlist, const int64_t* __restrict__ start,
+                           const uint64_t* __restrict__ tmp, uint32_t* __restrict__ bm, int64_t words) {
+  const int32_t v = rowlist[blockIdx.y];
+  const int64_t b = start[v], e = start[v + 1];
+  uint32_t* row = bm + (int64_t)blockIdx.y * words;
+  for (int64_t j = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < e; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = key_col(tmp[j]);
+    atomicOr(&row[c >> 5], 1u << (c & 31));
+  }
+}
+
+__global__ void k_huge_count(const uint32_t* __restrict__ bm, int64_t words, int64_t nchunks, int64_t* __restrict__ cc) {
+  const uint32_t* row = bm + (int64_t)blockIdx.y * words;
+  const int64_t w0 = (int64_t)blockIdx.x * kHugeChunkWords + (int64_t)threadIdx.x * kHugeWordsPerThread;
+  uint32_t s = 0;
+#pragma unroll 8
+  for (int k = 0; k < kHugeWordsPerThread; ++k)
+    if (w0 + k < words) s += __popc(row[w0 + k]);
+  __shared__ uint32_t sh[8];
+  __shared__ uint32_t tot;
+  block_scan_u32<256>(s, &tot, sh);
+  if (threadIdx.x == 0) cc[(int64_t)blockIdx.y * nchunks + blockIdx.x] = tot;
+}
+
+__global__ void k_huge_emit(const int32_t* __restrict__ rowlist, const int64_t* __restrict__ start,
+                            const uint32_t* __restrict__ bm, int64_t words, int64_t nchunks,
+                            const int64_t* __restrict__ ccoff, uint64_t* __restrict__ out, uint32_t* __restrict__ ucnt) {
+  const int32_t v = rowlist[blockIdx.y];
+  const uint32_t* row = bm + (int64_t)blockIdx.y * words;
+  const int64_t rowbase = ccoff[(int64_t)blockIdx.y * nchunks];
+  const int64_t w0 = (int64_t)blockIdx.x * kHugeChunkWords + (int64_t)threadIdx.x * kHugeWordsPerThread;
+  uint32_t s = 0;
+  for (int k = 0; k < kHugeWordsPerThread; ++k)
+    if (w0 + k < words) s += __popc(row[w0 + k]);
+  __shared__ uint32_t sh[8];
+  __shared__ uint32_t tot;
+  uint32_t pos = block_scan_u32<256>(s, &tot, sh);
+  int64_t o = start[v] + (ccoff[(int64_t)blockIdx.y * nchunks + blockIdx.x] - rowbase) + pos;
+  for (int k = 0; k < kHugeWordsPerThread; ++k) {
+    if (w0 + k >= words) break;
+    uint32_t word = row[w0 + k];
+    while (word) {
+      const int bit = __ffs(word) - 1;
+      word &= word - 1;
+      out[o++] = make_key((int32_t)((w0 + k) * 32 + bit), 0.f);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ucnt[v] = (uint32_t)(ccoff[(int64_t)(blockIdx.y + 1) * nchunks] - rowbase);
+}
+
+// weights of bitmap rows: max over duplicates via integer max on positive float bits
+__global__ void k_huge_weights(const int32_t* __restrict__ rowlist, const int64_t* __restrict__ start,
+                               const uint64_t* __restrict__ tmp, const uint32_t* __restrict__ ucnt,
+                               uint64_t* __restrict__ out) {
+  const int32_t v = rowlist[blockIdx.y];
+  const int64_t b = start[v], e = start[v + 1];
+  const int64_t u = ucnt[v];
+  for (int64_t j = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < e; j += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = tmp[j];
+    const int32_t c = key_col(k);
+    int64_t lo = b, hi = b + u;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (key_col(out[mid]) < c) lo = mid + 1; else hi = mid;
+    }
+    // low 32 bits hold ~weight: the largest weight has the smallest low word
+    atomicMin((unsigned long long*)&out[lo], (unsigned long long)k);
+  }
+}
+
+__global__ void k_compact(int32_t n, const int64_t* __restrict__ start, const uint64_t* __restrict__ sorted,
+                          const int64_t* __restrict__ off, int32_t* __restrict__ adj, float* __restrict__ w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const int64_t b = start[v], o = off[v], L = off[v + 1] - o;
+    for (int64_t j = lane; j < L; j += 32) {
+      const uint64_t k = sorted[b + j];
+      adj[o + j] = key_col(k);
+      if (w) {
+        const float x = key_w(k);
+        w[o + j] = x > 0.f ? x : 1.0f;  // an added self-loop carries weight 1
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, const float* w, bool self_loops,
+              bool allow_skip, Csr& out, Workspace& ws, cudaStream_t s) {
+  if (n < 1 || m0 < 0 || m0 >= (1ll << 32)) {
+    set_error("build_csr: n=%d m0=%lld out of range", n, (long long)m0);
+    return PRDF_EINVAL;
+  }
+  const int T = 256;
+  // validate ids (and weights)
+  {
+    DBuf<int> bad;
+    PRDF_TRY(bad.alloc(1, s));
+    PRDF_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+    if (m0 > 0) {
+      k_validate<<<grid_for(m0, T), T, 0, s>>>(rows, cols, w, m0, n, allow_skip ? 1 : 0, bad.p);
+      PRDF_LAUNCH_CHECK();
+    }
+    int hb = 0;
+    PRDF_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PRDF_CUDA(cudaStreamSynchronize(s));
+    if (hb & 1) {
+      set_error("edge list has a vertex id outside [0, %d)", n);
+      return PRDF_EINVAL;
+    }
+    if (hb & 2) {
+      set_error("edge weights must be finite and > 0");
+      return PRDF_EINVAL;
+    }
+  }
+  const int64_t N = n;
+  DBuf<uint32_t> cnt, fill, ucnt;
+  DBuf<int64_t> start;
+  PRDF_TRY(cnt.alloc(N, s));
+  PRDF_TRY(fill.alloc(N, s));
+  PRDF_TRY(ucnt.alloc(N, s));
+  PRDF_TRY(start.alloc(N + 1, s));
+  k_fill_u32<<<grid_for(N, T), T, 0, s>>>(cnt.p, N, self_loops ? 1u : 0u);
+  if (m0 > 0) k_row_count<<<grid_for(m0, T), T, 0, s>>>(rows, cols, m0, cnt.p);
+  PRDF_LAUNCH_CHECK();
+  PRDF_TRY(exclusive_scan_u32(cnt.p, N, start.p, ws, s));
+  int64_t M = 0;
+  PRDF_CUDA(cudaMemcpyAsync(ws.host_i64, start.p + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  M = ws.host_i64[0];
+  DBuf<uint64_t> tmp, srt;
+  PRDF_TRY(tmp.alloc(M > 0 ? M : 1, s));
+  PRDF_TRY(srt.alloc(M > 0 ? M : 1, s));
+  if (self_loops) {
+    k_init_rows<<<grid_for(N, T), T, 0, s>>>(n, start.p, fill.p, tmp.p);
+  } else {
+    k_fill_u32<<<grid_for(N, T), T, 0, s>>>(fill.p, N, 0u);
+  }
+  if (m0 > 0) k_scatter<<<grid_for(m0, T), T, 0, s>>>(rows, cols, w, m0, start.p, fill.p, tmp.p);
+  PRDF_LAUNCH_CHECK();
+
+  // classify rows by raw length
+  DBuf<int32_t> rowP;
+  PRDF_TRY(rowP.alloc(N, s));
+  PartThr t;
+  t.n = 3;
+  t.thr[0] = kThrThread;
+  t.thr[1] = kThrWarp;
+  t.thr[2] = kThrBlock;
+  int64_t cls[4];
+  PRDF_TRY(partition_by_degree(start.p, N, t, rowP.p, cls, ws, s));
+  const int32_t* l0 = rowP.p;
+  const int32_t* l1 = l0 + cls[0];
+  const int32_t* l2 = l1 + cls[1];
+  const int32_t* l3 = l2 + cls[2];
+  if (cls[0]) k_sort_thread<<<grid_for(cls[0], T), T, 0, s>>>(l0, cls[0], start.p, tmp.p, srt.p, ucnt.p);
+  if (cls[1]) k_sort_warp<<<grid_for(cls[1] * 32, T), T, 0, s>>>(l1, cls[1], start.p, tmp.p, srt.p, ucnt.p);
+  if (cls[2]) {
+    const int smem = kThrBlock * (int)sizeof(uint64_t);
+    PRDF_CUDA(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int grid = (int)(cls[2] < kSMs * 2 ? cls[2] : kSMs * 2);
+    k_sort_block<<<grid, kSortBlockThreads, smem, s>>>(l2, cls[2], start.p, tmp.p, srt.p, ucnt.p);
+  }
+  PRDF_LAUNCH_CHECK();
+  if (cls[3]) {
+    const int64_t words = (N + 31) / 32;
+    const int64_t nchunks = (words + kHugeChunkWords - 1) / kHugeChunkWords;
+    int64_t per = kBitmapBudget / (words * 4);
+    if (per < 1) per = 1;
+    if (per > 65535) per = 65535;
+    DBuf<uint32_t> bm;
+    DBuf<int64_t> cc, ccoff;
+    const int64_t rows_batch = cls[3] < per ? cls[3] : per;
+    PRDF_TRY(bm.alloc(rows_batch * words, s));
+    PRDF_TRY(cc.alloc(rows_batch * nchunks, s));
+    PRDF_TRY(ccoff.alloc(rows_batch * nchunks + 1, s));
+    for (int64_t h0 = 0; h0 < cls[3]; h0 += rows_batch) {
+      const int64_t rb = (cls[3] - h0) < rows_batch ? (cls[3] - h0) : rows_batch;
+      PRDF_CUDA(cudaMemsetAsync(bm.p, 0, (size_t)(rb * words) * 4, s));
+      k_huge_set<<<dim3(64, (unsigned)rb), T, 0, s>>>(l3 + h0, start.p, tmp.p, bm.p, words);
+      k_huge_count<<<dim3((unsigned)nchunks, (unsigned)rb), 256, 0, s>>>(bm.p, words, nchunks, cc.p);
+      PRDF_LAUNCH_CHECK();
+      PRDF_TRY(exclusive_scan_i64(cc.p, rb * nchunks, ccoff.p, ws, s));
+      k_huge_emit<<<dim3((unsigned)nchunks, (unsigned)rb), 256, 0, s>>>(l3 + h0, start.p, bm.p, words, nchunks,
+                                                                          ccoff.p, srt.p, ucnt.p);
+      if (w) k_huge_weights<<<dim3(64, (unsigned)rb), T, 0, s>>>(l3 + h0, start.p, tmp.p, ucnt.p, srt.p);
+      PRDF_LAUNCH_CHECK();
+    }
+  }
+  // final offsets and compaction
+  PRDF_TRY(out.off.alloc(N + 1, s));
+  PRDF_TRY(exclusive_scan_u32(ucnt.p, N, out.off.p, ws, s));
+  PRDF_CUDA(cudaMemcpyAsync(ws.host_i64, out.off.p + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  out.m = ws.host_i64[0];
+  PRDF_TRY(out.adj.alloc(out.m > 0 ? out.m : 1, s));
+  if (w) PRDF_TRY(out.w.alloc(out.m > 0 ? out.m : 1, s));
+  else out.w.release();
+  k_compact<<<grid_for(N * 32, T), T, 0, s>>>(n, start.p, srt.p, out.off.p, out.adj.p, w ? out.w.p : nullptr);
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+}  // namespace prdf

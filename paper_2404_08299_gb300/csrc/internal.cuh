@@ -1,0 +1,103 @@
+// Internal declarations shared by the translation units of libprdf.
+#pragma once
+
+#include "common.cuh"
+
+namespace prdf {
+
+constexpr int kMaxThr = 3;  // at most four degree classes
+
+struct PartThr {
+  int n = 0;                    // number of thresholds (classes = n + 1)
+  int64_t thr[kMaxThr] = {0, 0, 0};
+};
+
+// Scratch reused across calls on one graph. Calls on a graph do not overlap.
+struct Workspace {
+  DBuf<int64_t> scan;       // tile sums of the device-wide scan
+  DBuf<int64_t> part_cnt;   // per-tile class counts of the partition
+  DBuf<int64_t> part_base;  // their exclusive scan
+  int64_t* host_i64 = nullptr;  // pinned host scratch, kHostSlots entries
+  static constexpr int kHostSlots = 64;
+  int init();
+  ~Workspace();
+};
+
+// Exclusive prefix sums: out[i] = sum(in[0..i)), out[n] = total.
+int exclusive_scan_u32(const uint32_t* in, int64_t n, int64_t* out, Workspace& ws, cudaStream_t s);
+int exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, Workspace& ws, cudaStream_t s);
+
+// Alg. partition over the rows of a CSR (degree = off[v+1] - off[v]).
+int partition_by_degree(const int64_t* off, int64_t n, const PartThr& t, int32_t* P, int64_t* counts_host,
+                        Workspace& ws, cudaStream_t s);
+
+// A device CSR with optional float weights.
+struct Csr {
+  DBuf<int64_t> off;  // n + 1
+  DBuf<int32_t> adj;  // m
+  DBuf<float> w;      // m or empty
+  int64_t m = 0;
+};
+
+// Build a CSR of unique{(rows[i], cols[i])} (plus one self-loop per row if
+// self_loops), rows sorted ascending. Entries with a negative row or column
+// are skipped when allow_skip is set, otherwise they are an error. Weights
+// (optional) of merged duplicates: maximum; added self-loops: 1.0.
+int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, const float* w, bool self_loops,
+              bool allow_skip, Csr& out, Workspace& ws, cudaStream_t s);
+
+// Per-sweep arguments of the pull rank kernels (Alg. update).
+struct SweepArgs {
+  const int64_t* off;      // in-CSR offsets of G'
+  const int32_t* adj;      // in-CSR sources
+  const int32_t* P;        // in-degree partition (all classes)
+  const double* x;         // x[u] = R[u] / |out(u)| of the previous iteration
+  double* xn;              // next x
+  const int32_t* deg;      // |out(v)| (self-loop included)
+  const double* inv_deg;   // 1 / |out(v)|
+  double alpha, c0;        // damping, (1 - alpha) / n
+  uint64_t* resid;         // L-inf change of this sweep (bits of a non-negative double), atomic max
+  const uint64_t* prev;    // L-inf change of the previous sweep, or null on the first sweep
+  double tol;              // the sweep exits at once if *prev <= tol (already converged)
+  // DF / DF-P only
+  uint8_t* dV;             // affected flags (read; cleared on prune)
+  uint8_t* dN;             // expand flags (set when the change exceeds tau_f)
+  uint8_t* wrote;          // 1 where this vertex's slot in xn was written by the previous sweep
+  double tau_f, tau_p;
+  int prune;               // DF-P (Eq. 2, prune) or DF (Eq. 1)
+};
+
+// Launch one rank sweep (all degree classes) for Static (dynamic = false) or DF/DF-P.
+int launch_sweep(const SweepArgs& a, const int64_t* class_begin, int nclass, bool exact, bool dynamic,
+                 cudaStream_t s);
+
+// Alg. affected kernels (frontier.cu)
+int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask, int64_t n_del,
+                            const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins, uint8_t* dV, uint8_t* dN,
+                            cudaStream_t s);
+// expandAffected over the out-degree partition; skipped on the device when *resid <= tol
+int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, const int64_t* cb, int nclass,
+                  const uint8_t* dN, uint8_t* dV, const uint64_t* resid, double tol, cudaStream_t s);
+int count_flags(const uint8_t* f, int64_t n, unsigned long long* dev_out, cudaStream_t s);
+
+}  // namespace prdf
+
+// The graph handle of the C ABI.
+struct prdf_graph {
+  int32_t n = 0;
+  bool weighted = false;
+  cudaStream_t stream = nullptr;
+  prdf::Csr csr[2];                  // [PRDF_OUT] = G, [PRDF_IN] = G'
+  prdf::DBuf<int32_t> outdeg;        // |out(v)|
+  prdf::DBuf<double> inv_outdeg;     // 1 / |out(v)|
+  prdf::PartThr thr[2];              // class thresholds per CSR
+  prdf::DBuf<int32_t> P[2];          // partitions
+  int64_t pcount[2][prdf::kMaxThr + 1] = {};
+  bool pvalid[2] = {false, false};
+  prdf::Workspace ws;
+  // solver scratch
+  prdf::DBuf<double> xa, xb;
+  prdf::DBuf<uint64_t> resid;
+  prdf::DBuf<uint8_t> dV, dN, wrote;
+  prdf::DBuf<unsigned long long> counter;
+};

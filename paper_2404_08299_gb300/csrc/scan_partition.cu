@@ -1,0 +1,209 @@
+// Device-wide exclusive scan and the stable degree partition (Alg. partition,
+// Appendix A.2 of arXiv 2404.08299), generalised to up to four classes.
+#include "internal.cuh"
+
+namespace prdf {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 2048 elements per block
+
+// Exclusive scan of one value per thread across a block of kScanThreads.
+template <class T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* total) {
+  __shared__ T warp_tot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    T w = lane < kScanThreads / 32 ? warp_tot[lane] : T(0);
+    T wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = wi - w;  // exclusive warp offsets
+    if (lane == kScanThreads / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  T res = incl - v + warp_tot[wid];
+  __syncthreads();
+  return res;
+}
+
+template <class TIn>
+__global__ void k_tile_sums(const TIn* __restrict__ in, int64_t n, int64_t* __restrict__ tile_sum) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) s += (int64_t)in[base + k];
+  __shared__ int64_t tot;
+  block_exclusive_scan<int64_t>(s, &tot);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+// In-place exclusive scan of tile sums by one block; writes the grand total to ts[ntiles].
+__global__ void k_scan_tile_sums(int64_t* ts, int64_t ntiles) {
+  __shared__ int64_t carry_s;
+  __shared__ int64_t tot;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int64_t c = 0; c < ntiles; c += kScanTile) {
+    const int64_t base = c + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = (base + k < ntiles) ? ts[base + k] : 0;
+      s += v[k];
+    }
+    int64_t ex = block_exclusive_scan<int64_t>(s, &tot) + carry_s;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (base + k < ntiles) ts[base + k] = ex;
+      ex += v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ts[ntiles] = carry_s;
+}
+
+template <class TIn>
+__global__ void k_scan_apply(const TIn* __restrict__ in, int64_t n, const int64_t* __restrict__ tile_off,
+                             int64_t* __restrict__ out) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? (int64_t)in[base + k] : 0;
+    s += v[k];
+  }
+  __shared__ int64_t tot;
+  int64_t ex = block_exclusive_scan<int64_t>(s, &tot) + tile_off[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = ex;
+    ex += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = tile_off[gridDim.x];
+}
+
+// ---------------------------------------------------------- partition ----
+
+constexpr int kPartItems = 8;
+constexpr int kPartTile = kScanThreads * kPartItems;
+
+__device__ __forceinline__ int degree_class(int64_t d, const PartThr& t) {
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxThr; ++k) c += (k < t.n && d > t.thr[k]) ? 1 : 0;
+  return c;
+}
+
+// count[c * ntiles + tile] = number of vertices of class c in the tile
+__global__ void k_part_count(const int64_t* __restrict__ off, int64_t n, PartThr t, int64_t* __restrict__ count) {
+  const int64_t base = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartItems;
+  uint64_t packed = 0;  // 16-bit count per class
+#pragma unroll
+  for (int k = 0; k < kPartItems; ++k) {
+    const int64_t v = base + k;
+    if (v < n) packed += 1ull << (16 * degree_class(off[v + 1] - off[v], t));
+  }
+  __shared__ uint64_t tot;
+  block_exclusive_scan<uint64_t>(packed, &tot);
+  if (threadIdx.x == 0)
+    for (int c = 0; c <= t.n; ++c) count[(int64_t)c * gridDim.x + blockIdx.x] = (int64_t)((tot >> (16 * c)) & 0xFFFF);
+}
+
+// P[base[c][tile] + rank within tile] = v, ranks in ascending vertex order (stable).
+__global__ void k_part_scatter(const int64_t* __restrict__ off, int64_t n, PartThr t, const int64_t* __restrict__ base,
+                               int32_t* __restrict__ P) {
+  const int64_t first = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartItems;
+  int cls[kPartItems];
+  uint64_t packed = 0;
+#pragma unroll
+  for (int k = 0; k < kPartItems; ++k) {
+    const int64_t v = first + k;
+    cls[k] = v < n ? degree_class(off[v + 1] - off[v], t) : -1;
+    if (cls[k] >= 0) packed += 1ull << (16 * cls[k]);
+  }
+  __shared__ uint64_t tot;
+  uint64_t ex = block_exclusive_scan<uint64_t>(packed, &tot);
+#pragma unroll
+  for (int k = 0; k < kPartItems; ++k) {
+    if (cls[k] < 0) continue;
+    const int c = cls[k];
+    const int64_t pos = base[(int64_t)c * gridDim.x + blockIdx.x] + (int64_t)((ex >> (16 * c)) & 0xFFFF);
+    P[pos] = (int32_t)(first + k);
+    ex += 1ull << (16 * c);
+  }
+}
+
+}  // namespace
+
+int exclusive_scan_u32(const uint32_t* in, int64_t n, int64_t* out, Workspace& ws, cudaStream_t s) {
+  const int64_t nt = (n + kScanTile - 1) / kScanTile;
+  if (nt == 0) {
+    PRDF_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+    return PRDF_OK;
+  }
+  PRDF_TRY(ws.scan.reserve((size_t)nt + 1, s));
+  k_tile_sums<uint32_t><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, ws.scan.p);
+  k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(ws.scan.p, nt);
+  k_scan_apply<uint32_t><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, ws.scan.p, out);
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+int exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, Workspace& ws, cudaStream_t s) {
+  const int64_t nt = (n + kScanTile - 1) / kScanTile;
+  if (nt == 0) {
+    PRDF_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+    return PRDF_OK;
+  }
+  PRDF_TRY(ws.scan.reserve((size_t)nt + 1, s));
+  k_tile_sums<int64_t><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, ws.scan.p);
+  k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(ws.scan.p, nt);
+  k_scan_apply<int64_t><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, ws.scan.p, out);
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+int partition_by_degree(const int64_t* off, int64_t n, const PartThr& t, int32_t* P, int64_t* counts_host,
+                        Workspace& ws, cudaStream_t s) {
+  const int64_t nt = (n + kPartTile - 1) / kPartTile;
+  const int C = t.n + 1;
+  if (nt == 0) {
+    for (int c = 0; c < C; ++c) counts_host[c] = 0;
+    return PRDF_OK;
+  }
+  PRDF_TRY(ws.part_cnt.reserve((size_t)C * nt, s));
+  PRDF_TRY(ws.part_base.reserve((size_t)C * nt + 1, s));
+  k_part_count<<<(unsigned)nt, kScanThreads, 0, s>>>(off, n, t, ws.part_cnt.p);
+  PRDF_LAUNCH_CHECK();
+  PRDF_TRY(exclusive_scan_i64(ws.part_cnt.p, C * nt, ws.part_base.p, ws, s));
+  k_part_scatter<<<(unsigned)nt, kScanThreads, 0, s>>>(off, n, t, ws.part_base.p, P);
+  PRDF_LAUNCH_CHECK();
+  // class sizes from the class boundaries of the flattened scan
+  int64_t* hb = ws.host_i64;
+  for (int c = 0; c <= C; ++c)
+    PRDF_CUDA(cudaMemcpyAsync(hb + c, ws.part_base.p + (int64_t)c * nt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  for (int c = 0; c < C; ++c) counts_host[c] = hb[c + 1] - hb[c];
+  return PRDF_OK;
+}
+
+}  // namespace prdf

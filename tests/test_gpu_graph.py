@@ -1,0 +1,173 @@
+"""GPU parity of the integer parts of the hot path, bit-exact against the oracle:
+CSR / transposed CSR build (Section 3.1, 4.3), set-semantics batch update
+(Section 3.3), degree partition (Alg. partition), initialAffected and
+expandAffected (Alg. affected)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import adversarial_edges, dev, host, huge_row_edges
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2404_08299_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def prdf():
+    import paper_2404_08299_gb300 as p
+    return p
+
+
+def gpu_graph(n, src, dst, w=None):
+    return prdf().Graph(n, dev(src, torch.int32), dev(dst, torch.int32), None if w is None else dev(w, torch.float32))
+
+
+def check_csr(g, og):
+    P = prdf()
+    off, adj, _ = g.export_csr(P.PRDF_OUT)
+    assert np.array_equal(host(off), og.out_off)
+    assert np.array_equal(host(adj), og.out_adj)
+    off, adj, _ = g.export_csr(P.PRDF_IN)
+    assert np.array_equal(host(off), og.in_off)
+    assert np.array_equal(host(adj), og.in_adj)
+
+
+@pytest.mark.parametrize("name,n,src,dst", adversarial_edges())
+def test_csr_build_adversarial(name, n, src, dst):
+    check_csr(gpu_graph(n, src, dst), oracle.graph(n, src, dst))
+
+
+@pytest.mark.parametrize("scale,nsamp", [(10, 16000), (16, 1 << 20)])
+def test_csr_build_rmat(scale, nsamp):
+    n, s, d = synth.rmat(scale, nsamp, seed=1)
+    check_csr(gpu_graph(n, s, d), oracle.graph(n, s, d))
+
+
+def test_csr_build_grid():
+    n, s, d = synth.grid(128, 0.05, seed=1)
+    check_csr(gpu_graph(n, s, d), oracle.graph(n, s, d))
+
+
+def test_csr_build_bitmap_and_block_rows():
+    n, s, d = huge_row_edges()
+    g = gpu_graph(n, s, d)
+    og = oracle.graph(n, s, d)
+    check_csr(g, og)
+    assert np.diff(og.out_off).max() > 16384 and np.diff(og.in_off).max() > 16384
+
+
+def test_csr_weights_take_max_of_duplicates():
+    n, s, d = huge_row_edges(n=1 << 14, hub_deg=30000)
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.5, 1.5, len(s)).astype(np.float32)
+    g = gpu_graph(n, s, d, w)
+    P = prdf()
+    for which, (r, c) in ((P.PRDF_OUT, (s, d)), (P.PRDF_IN, (d, s))):
+        off, adj, ww = g.export_csr(which)
+        off, adj, ww = host(off), host(adj), host(ww)
+        best = {}
+        for a, b, x in zip(r.tolist(), c.tolist(), w.tolist()):
+            best[(a, b)] = max(best.get((a, b), 0.0), x)
+        rows = np.repeat(np.arange(n), np.diff(off))
+        for a, b, x in zip(rows.tolist(), adj.tolist(), ww.tolist()):
+            want = best.get((a, b), 1.0 if a == b else None)
+            assert want is not None and np.float32(want) == np.float32(x), (a, b, x, want)
+
+
+def test_csr_rejects_out_of_range_ids():
+    with pytest.raises(prdf().PrdfError) as e:
+        gpu_graph(4, np.array([0, 4], np.int32), np.array([1, 1], np.int32))
+    assert e.value.code == -1
+    with pytest.raises(prdf().PrdfError):
+        gpu_graph(4, np.array([0, -1], np.int32), np.array([1, 1], np.int32))
+
+
+@pytest.mark.parametrize("thr", [[2], [0], [8, 64, 2048], [1, 3], [4, 16]])
+def test_partition_bit_exact(thr):
+    n, s, d = synth.rmat(12, 60000, seed=2)
+    g = gpu_graph(n, s, d)
+    og = oracle.graph(n, s, d)
+    P = prdf()
+    for which, off in ((P.PRDF_IN, og.in_off), (P.PRDF_OUT, og.out_off)):
+        g.set_thresholds(which, thr)
+        Pg, cnt = g.partition(which)
+        Po, cnto = oracle.partition(off, thr)
+        assert np.array_equal(host(Pg), Po)
+        assert cnt[:len(thr) + 1] == cnto.tolist()
+
+
+def test_partition_ragged_tiles():
+    # n not a multiple of the 2048-vertex tile, one class empty
+    n = 2048 * 3 + 77
+    s = synth.randint(9000, n, 4)
+    d = synth.randint(9000, n, 5)
+    g = gpu_graph(n, s, d)
+    og = oracle.graph(n, s, d)
+    g.set_thresholds(prdf().PRDF_IN, [1000])
+    Pg, cnt = g.partition(prdf().PRDF_IN)
+    Po, cnto = oracle.partition(og.in_off, [1000])
+    assert np.array_equal(host(Pg), Po) and cnt[:2] == cnto.tolist() and cnto[1] == 0
+
+
+@pytest.mark.parametrize("seed,size", [(1, 50), (2, 400), (3, 3000)])
+def test_apply_batch_bit_exact(seed, size):
+    n, s, d = synth.rmat(11, 30000, seed=seed)
+    g = gpu_graph(n, s, d)
+    og = oracle.graph(n, s, d)
+    ds, dd, is_, id_ = synth.batch(n, og.out_off, og.out_adj, size, seed=seed, s1=3)
+    # adversarial entries: self-loop deletion, deleted+reinserted, duplicate insertion, missing deletion
+    e_u = int(np.flatnonzero(np.diff(og.out_off) > 1)[0])
+    row = og.out_adj[og.out_off[e_u]:og.out_off[e_u + 1]]
+    e_v = int(row[row != e_u][0])
+    ds = np.concatenate([ds, [5, e_u, 0]]).astype(np.int32)
+    dd = np.concatenate([dd, [5, e_v, n - 1]]).astype(np.int32)
+    is_ = np.concatenate([is_, [e_u, is_[0]]]).astype(np.int32)
+    id_ = np.concatenate([id_, [e_v, id_[0]]]).astype(np.int32)
+    de, ie = g.apply_batch(dev(ds), dev(dd), dev(is_), dev(id_))
+    og1, dmo, imo = oracle.apply_batch(og, ds, dd, is_, id_)
+    check_csr(g, og1)
+    assert np.array_equal(host(de), dmo)
+    assert np.array_equal(host(ie), imo)
+
+
+def test_apply_batch_empty_and_consecutive():
+    n, s, d = synth.rmat(10, 12000, seed=9)
+    g = gpu_graph(n, s, d)
+    og = oracle.graph(n, s, d)
+    e = np.zeros(0, np.int32)
+    de, ie = g.apply_batch(dev(e), dev(e), dev(e), dev(e))
+    check_csr(g, og)
+    for b in range(3):
+        ds, dd, is_, id_ = synth.batch(n, og.out_off, og.out_adj, 100, seed=9, s1=1, s2=b)
+        g.apply_batch(dev(ds), dev(dd), dev(is_), dev(id_))
+        og, _, _ = oracle.apply_batch(og, ds, dd, is_, id_)
+        check_csr(g, og)
+
+
+def test_initial_and_expand_affected_bit_exact():
+    n, s, d = synth.rmat(13, 120000, seed=4)
+    g = gpu_graph(n, s, d)
+    og = oracle.graph(n, s, d)
+    ds, dd, is_, id_ = synth.batch(n, og.out_off, og.out_adj, 500, seed=4)
+    dmask = (np.arange(len(ds)) % 3 != 0).astype(np.uint8)
+    dV = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    dN = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    g.initial_affected(dev(ds), dev(dd), dev(is_), dV, dN, del_mask=dev(dmask))
+    dVo, dNo = oracle.initial_affected(n, ds, dd, is_, del_mask=dmask)
+    assert np.array_equal(host(dV), dVo) and np.array_equal(host(dN), dNo)
+    # expand from identical input flags, for several class splits (thread/warp/block kernels)
+    rng = np.random.default_rng(0)
+    for thr in ([8, 64, 2048], [2], [0, 1, 4]):
+        g.set_thresholds(prdf().PRDF_OUT, thr)
+        dN_in = (rng.random(n) < 0.05).astype(np.uint8)
+        dV_in = (rng.random(n) < 0.02).astype(np.uint8)
+        dVg = dev(dV_in)
+        g.expand_affected(dev(dN_in), dVg)
+        assert np.array_equal(host(dVg), oracle.expand_affected(og.out_off, og.out_adj, dN_in, dV_in))
