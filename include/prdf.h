@@ -164,6 +164,26 @@ int prdf_graph_set_thresholds(prdf_graph* g, int which, int n_thr, const int64_t
  */
 int prdf_partition(prdf_graph* g, int which, int32_t* P, int64_t* counts_host, void* stream);
 
+/*
+ * Alg. partition of prdf_partition, for callers that cannot allocate device
+ * memory at this point (their memory is handed out up front by a pool that
+ * owns all of it, or their path must not take the device-wide
+ * synchronisation that cudaMalloc/cudaFree can imply). The paper has no
+ * counterpart: this is a library service. It allocates nothing: its scratch
+ * is a fixed device array inside the library (about 512 KB, held by every
+ * GPU that loads the library until exit).
+ * off: int64[n+1] device CSR offsets (degree = off[v+1] - off[v]);
+ * thresholds as in prdf_graph_set_thresholds (n_thr in 1..3, host array);
+ * P: int32[n] device output; counts_host: host int64[n_thr+1] output.
+ * n must be in [1, 16777216]; larger n returns PRDF_EINVAL with a message.
+ * The first call on each device looks the scratch's device address up
+ * (make it before any stream capture). Calls share the scratch: calls that
+ * overlap on the GPU race and must be serialised by the caller. Returns
+ * after the results are complete on `stream`.
+ */
+int prdf_partition_noalloc(const int64_t* off, int32_t n, int n_thr, const int64_t* thr_host, int32_t* P,
+                           int64_t* counts_host, void* stream);
+
 /* ------------------------------------------------------------- frontier -- */
 
 /*

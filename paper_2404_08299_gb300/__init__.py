@@ -79,6 +79,7 @@ _SIGNATURES = {
     "prdf_graph_apply_batch": (_INT, [_P, _P, _P, _I64, _P, _P, _P, _I64, _P, _P, _P]),
     "prdf_graph_set_thresholds": (_INT, [_P, _INT, _INT, _P]),
     "prdf_partition": (_INT, [_P, _INT, _P, _P, _P]),
+    "prdf_partition_noalloc": (_INT, [_P, _I32, _INT, _P, _P, _P, _P]),
     "prdf_initial_affected": (_INT, [_P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P, _P]),
     "prdf_expand_affected": (_INT, [_P, _P, _P, _P]),
     "prdf_pagerank_static": (_INT, [_P, _P, _P, _P, _P]),
@@ -141,6 +142,18 @@ def params(**kw) -> _Params:
         setattr(p, k, v)
     p.stream = _stream()
     return p
+
+
+def partition_noalloc(off: torch.Tensor, thresholds):
+    """Alg. partition of a device CSR offset array without any device allocation
+    (prdf_partition_noalloc). Returns (P int32[n], class sizes)."""
+    n = off.numel() - 1
+    P = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    thr = (ctypes.c_int64 * len(thresholds))(*[int(t) for t in thresholds])
+    counts = (ctypes.c_int64 * 4)()
+    _check(lib().prdf_partition_noalloc(_ptr(off, torch.int64, name="off"), n, len(thresholds), thr, _ptr(P), counts,
+                                        _stream()))
+    return P[:n], list(counts)[:len(thresholds) + 1]
 
 
 class Graph:

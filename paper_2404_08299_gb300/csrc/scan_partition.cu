@@ -1,5 +1,7 @@
 // Device-wide exclusive scan and the stable degree partition (Alg. partition,
 // Appendix A.2 of arXiv 2404.08299), generalised to up to four classes.
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace prdf {
@@ -206,4 +208,102 @@ int partition_by_degree(const int64_t* off, int64_t n, const PartThr& t, int32_t
   return PRDF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Alg. partition for callers that cannot allocate device memory.
+//
+// Some callers may not call cudaMalloc (or any allocator) at the point where
+// they partition: their device memory is handed out up front by a pool that
+// owns all of it, or they run on a path that must not take the allocator's
+// device-wide synchronisation. prdf_partition_noalloc serves them: it runs
+// the same kernels as prdf_partition, but its scratch (per-tile class counts,
+// their scan, and the scan's tile sums) lives in the fixed file-scope device
+// array below, sized for at most kNoAllocMaxN vertices. Every GPU that loads
+// the library holds this array (about 512 KB) until the process exits.
+//
+// The array's name means nothing as a device address in host code, so the
+// first call on each device (with that device current) looks its address up
+// with cudaGetSymbolAddress and caches it; make that first call before any
+// stream capture. All calls share the one array, which keeps the last call's
+// contents: each call overwrites every entry it reads before reading it, so
+// nothing needs clearing, but calls that overlap on the GPU (other streams,
+// other threads) race on it and must be serialised by the caller.
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 1ll << 24;
+constexpr int64_t kNoAllocMaxTiles = (kNoAllocMaxN + kPartTile - 1) / kPartTile;
+constexpr int64_t kNoAllocCnt = (int64_t)(kMaxThr + 1) * kNoAllocMaxTiles;
+constexpr int64_t kNoAllocScan = (kNoAllocCnt + kScanTile - 1) / kScanTile + 1;
+constexpr int64_t kNoAllocWords = kNoAllocCnt + (kNoAllocCnt + 1) + kNoAllocScan;
+
+static __device__ __align__(256) int64_t g_noalloc_scratch[kNoAllocWords];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int64_t* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once per device).
+int noalloc_scratch(int64_t** out) {
+  int dev = 0;
+  PRDF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("device ordinal %d beyond %d", dev, kNoAllocMaxDevices);
+    return PRDF_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    PRDF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = (int64_t*)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return PRDF_OK;
+}
+
+}  // namespace
+
 }  // namespace prdf
+
+extern "C" int prdf_partition_noalloc(const int64_t* off, int32_t n, int n_thr, const int64_t* thr_host, int32_t* P,
+                                      int64_t* counts_host, void* stream) {
+  using namespace prdf;
+  if (!off || !P || !counts_host || !thr_host || n < 1 || n_thr < 1 || n_thr > kMaxThr) {
+    set_error("prdf_partition_noalloc: bad arguments");
+    return PRDF_EINVAL;
+  }
+  if ((int64_t)n > kNoAllocMaxN) {
+    set_error("prdf_partition_noalloc: n = %d exceeds the fixed scratch limit of %lld vertices", n,
+              (long long)kNoAllocMaxN);
+    return PRDF_EINVAL;
+  }
+  PartThr t;
+  t.n = n_thr;
+  for (int i = 0; i < n_thr; ++i) {
+    if (thr_host[i] < 0 || (i > 0 && thr_host[i] <= thr_host[i - 1])) {
+      set_error("prdf_partition_noalloc: thresholds must be >= 0 and strictly increasing");
+      return PRDF_EINVAL;
+    }
+    t.thr[i] = thr_host[i];
+  }
+  int64_t* scratch = nullptr;
+  PRDF_TRY(noalloc_scratch(&scratch));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nt = ((int64_t)n + kPartTile - 1) / kPartTile;
+  const int C = n_thr + 1;
+  const int64_t cn = (int64_t)C * nt;
+  int64_t* cnt = scratch;
+  int64_t* base = scratch + kNoAllocCnt;
+  int64_t* sums = base + kNoAllocCnt + 1;
+  const int64_t nt2 = (cn + kScanTile - 1) / kScanTile;
+  k_part_count<<<(unsigned)nt, kScanThreads, 0, s>>>(off, n, t, cnt);
+  k_tile_sums<int64_t><<<(unsigned)nt2, kScanThreads, 0, s>>>(cnt, cn, sums);
+  k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(sums, nt2);
+  k_scan_apply<int64_t><<<(unsigned)nt2, kScanThreads, 0, s>>>(cnt, cn, sums, base);
+  k_part_scatter<<<(unsigned)nt, kScanThreads, 0, s>>>(off, n, t, base, P);
+  PRDF_LAUNCH_CHECK();
+  int64_t hb[kMaxThr + 2];
+  for (int c = 0; c <= C; ++c)
+    PRDF_CUDA(cudaMemcpyAsync(hb + c, base + (int64_t)c * nt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  for (int c = 0; c < C; ++c) counts_host[c] = hb[c + 1] - hb[c];
+  return PRDF_OK;
+}
