@@ -149,18 +149,21 @@ int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t*
  * Degree thresholds between the vertex classes of one CSR's kernels
  * (Alg. partition generalised to n_thr+1 classes). Class 0 holds
  * degree <= thr[0], class c holds thr[c-1] < degree <= thr[c], the last class
- * degree > thr[n_thr-1]. For PRDF_IN the classes are the thread-, warp- and
- * block-per-vertex rank kernels (n_thr = 2); for PRDF_OUT the thread-, warp-
- * and block-per-vertex marking kernels (n_thr = 2). thr_host: host int64[n_thr],
- * strictly increasing, thr[0] >= 0.
+ * degree > thr[n_thr-1]; 1 <= n_thr <= 7. For PRDF_IN the classes select the
+ * rank-sweep kernels (the last class one block per vertex, the one before it
+ * one warp per vertex, lower classes 1, 4 or 16 lanes per vertex by their
+ * upper bound; default thresholds 1, 4, 16, 128, 4096); for PRDF_OUT the
+ * marking kernels (thread, 8 lanes, warp, block; default 8, 64, 2048).
+ * thr_host: host int64[n_thr], strictly increasing, thr[0] >= 0.
  */
 int prdf_graph_set_thresholds(prdf_graph* g, int which, int n_thr, const int64_t* thr_host);
 
 /*
  * Alg. partition: stable partition of vertex ids by the degree of one CSR
  * into the classes above; P int32[n] (device) receives the ids, class by
- * class, each class in ascending id order; counts_host (host int64[n_thr+1])
- * receives the class sizes (N_P = counts_host[0] for the paper's two classes).
+ * class, each class in ascending id order; counts_host (host int64[n_thr+1],
+ * at most 8) receives the class sizes (N_P = counts_host[0] for the paper's
+ * two classes).
  */
 int prdf_partition(prdf_graph* g, int which, int32_t* P, int64_t* counts_host, void* stream);
 

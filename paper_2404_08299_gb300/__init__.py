@@ -221,7 +221,7 @@ class Graph:
     def partition(self, which: int = PRDF_IN):
         n = self.n
         P = torch.empty(n, dtype=torch.int32, device="cuda")
-        counts = (ctypes.c_int64 * 4)()
+        counts = (ctypes.c_int64 * 8)()
         _check(lib().prdf_partition(self._h, which, _ptr(P), counts, _stream()))
         return P, list(counts)
 

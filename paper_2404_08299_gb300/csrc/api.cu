@@ -34,31 +34,35 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__global__ void k_degrees(const int64_t* __restrict__ off, int32_t n, int32_t* __restrict__ deg,
+__global__ void k_degrees(const int64_t* __restrict__ off, int32_t n, double* __restrict__ deg,
                           double* __restrict__ inv) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = off[v + 1] - off[v];
-    deg[v] = (int32_t)d;
+    deg[v] = (double)d;
     inv[v] = d > 0 ? 1.0 / (double)d : 0.0;
   }
 }
 
-// x[v] = R0[v] / |out(v)| (R0 = NULL: 1/n)
-__global__ void k_init_x(const double* __restrict__ R0, int32_t n, const double* __restrict__ inv,
-                         double* __restrict__ xa, double* __restrict__ xb) {
+// x[i] = R0[perm[i]] / |out(perm[i])| in the sweep numbering (R0 = NULL: 1/n)
+__global__ void k_init_x(const double* __restrict__ R0, const int32_t* __restrict__ perm, int32_t n,
+                         const double* __restrict__ inv, double* __restrict__ xa, double* __restrict__ xb) {
   const double r = 1.0 / (double)n;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const double x = (R0 ? R0[v] : r) * inv[v];
-    xa[v] = x;
-    if (xb) xb[v] = x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = (R0 ? R0[perm[i]] : r) * inv[i];
+    xa[i] = x;
+    if (xb) xb[i] = x;
   }
 }
 
-// R[v] = x[v] * |out(v)|
-__global__ void k_finalize(const double* __restrict__ x, const int32_t* __restrict__ deg, int32_t n,
-                           double* __restrict__ R) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    R[v] = x[v] * (double)deg[v];
+// R[perm[i]] = x[i] * |out(perm[i])|; dV_out[perm[i]] = dV[i]
+__global__ void k_finalize(const double* __restrict__ x, const double* __restrict__ deg,
+                           const int32_t* __restrict__ perm, int32_t n, double* __restrict__ R,
+                           const uint8_t* __restrict__ dV, uint8_t* __restrict__ dV_out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = perm[i];
+    R[v] = x[i] * deg[i];
+    if (dV_out) dV_out[v] = dV[i];
+  }
 }
 
 __global__ void k_check_ids(const int32_t* a, const int32_t* b, int64_t cnt, int32_t n, int* bad) {
@@ -178,6 +182,24 @@ int ensure_partition(prdf_graph* g, int which, cudaStream_t s) {
   return PRDF_OK;
 }
 
+int ensure_relabelled(prdf_graph* g, bool need_pout, cudaStream_t s) {
+  Relabel& r = g->rl;
+  bool same = r.valid && r.thr.n == g->thr[PRDF_IN].n;
+  for (int i = 0; same && i < r.thr.n; ++i) same = r.thr.thr[i] == g->thr[PRDF_IN].thr[i];
+  if (!same) PRDF_TRY(build_relabelled(g, s));
+  if (need_pout && !r.pout_valid) {
+    PRDF_TRY(r.pout.reserve(g->n, s));
+    PRDF_TRY(partition_by_degree(r.out.off.p, g->n, g->thr[PRDF_OUT], r.pout.p, r.pout_count, g->ws, s));
+    r.pout_valid = true;
+  }
+  return PRDF_OK;
+}
+
+void begins_from_counts(const int64_t* count, int C, int64_t* cb) {
+  cb[0] = 0;
+  for (int c = 0; c < C; ++c) cb[c + 1] = cb[c] + count[c];
+}
+
 void class_begins(const prdf_graph* g, int which, int64_t* cb) {
   const int C = g->thr[which].n + 1;
   cb[0] = 0;
@@ -238,20 +260,21 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
   const int max_iter = p->max_iter;
   PRDF_TRY(g->resid.reserve((size_t)max_iter + 1, s));
   PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t) * ((size_t)max_iter + 1), s));
+  const Relabel& rl = g->rl;
   int64_t cb[prdf::kMaxThr + 2], cbo[prdf::kMaxThr + 2];
-  class_begins(g, PRDF_IN, cb);
-  const int nci = g->thr[PRDF_IN].n + 1, nco = g->thr[PRDF_OUT].n + 1;
-  if (dynamic) class_begins(g, PRDF_OUT, cbo);
+  const int nci = rl.thr.n + 1, nco = g->thr[PRDF_OUT].n + 1;
+  begins_from_counts(rl.count, nci, cb);
+  if (dynamic) begins_from_counts(rl.pout_count, nco, cbo);
   const int kps = nonempty_classes(cb, nci) + (dynamic ? nonempty_classes(cbo, nco) : 0);
   SweepArgs a;
   memset(&a, 0, sizeof(a));
-  a.off = g->csr[PRDF_IN].off.p;
-  a.adj = g->csr[PRDF_IN].adj.p;
-  a.P = g->P[PRDF_IN].p;
-  a.deg = g->outdeg.p;
-  a.inv_deg = g->inv_outdeg.p;
+  a.off = rl.in.off.p;
+  a.adj = rl.in.adj.p;
+  a.degd = rl.degd.p;
+  a.inv_deg = rl.inv_deg.p;
   a.alpha = p->alpha;
   a.c0 = (1.0 - p->alpha) / (double)n;
+  a.self_loops = g->self_loops ? 1 : 0;
   a.tol = p->tol;
   a.dV = g->dV.p;
   a.dN = g->dN.p;
@@ -287,11 +310,11 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
         ev.push_back(e1);
         PRDF_CUDA(cudaEventRecord(e0, s));
       }
-      PRDF_TRY(launch_sweep(a, cb, nci, exact, dynamic, s));
+      PRDF_TRY(launch_sweep(a, rl.thr, cb, exact, dynamic, s));
       if (timed) PRDF_CUDA(cudaEventRecord(ev.back(), s));
       if (dynamic)
-        PRDF_TRY(launch_expand(g->csr[PRDF_OUT].off.p, g->csr[PRDF_OUT].adj.p, g->P[PRDF_OUT].p, cbo, nco, g->dN.p,
-                               g->dV.p, g->resid.p + i, p->tol, s));
+        PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, g->resid.p + i,
+                               p->tol, s));
     }
     launched = upto;
     PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid.p + launched - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
@@ -394,18 +417,24 @@ int prdf_graph_create(int32_t n, const int32_t* src, const int32_t* dst, const f
   g->n = n;
   g->weighted = w != nullptr;
   g->stream = s;
-  // default class thresholds: thread <= 8, sub-warp <= 64, warp <= 2048, block above
-  for (int which = 0; which < 2; ++which) {
-    g->thr[which].n = 3;
-    g->thr[which].thr[0] = 8;
-    g->thr[which].thr[1] = 64;
-    g->thr[which].thr[2] = 2048;
+  // default class thresholds. In-degree (rank sweep): self-loop only, <= 4,
+  // <= 16 (4 lanes), <= 128 (16 lanes), <= 4096 (warp), block above.
+  // Out-degree (marking): thread <= 8, 8 lanes <= 64, warp <= 2048, block above.
+  {
+    const int64_t tin[5] = {1, 4, 16, 128, 4096};
+    g->thr[PRDF_IN].n = 5;
+    for (int i = 0; i < 5; ++i) g->thr[PRDF_IN].thr[i] = tin[i];
+    const int64_t tout[3] = {8, 64, 2048};
+    g->thr[PRDF_OUT].n = 3;
+    for (int i = 0; i < 3; ++i) g->thr[PRDF_OUT].thr[i] = tout[i];
   }
   int r = g->ws.init();
   const bool loops = (flags & PRDF_ADD_SELF_LOOPS) != 0;
+  g->self_loops = loops;
   if (r == PRDF_OK) r = build_csr(n, m0, src, dst, w, loops, false, g->csr[PRDF_OUT], g->ws, s);
   if (r == PRDF_OK) r = build_csr(n, m0, dst, src, w, loops, false, g->csr[PRDF_IN], g->ws, s);
   if (r == PRDF_OK) r = ensure_degrees(g, s);
+  if (r == PRDF_OK) r = build_relabelled(g, s);
   if (r == PRDF_OK && cudaStreamSynchronize(s) != cudaSuccess) {
     set_error("graph build: %s", cudaGetErrorString(cudaGetLastError()));
     r = PRDF_ECUDA;
@@ -493,12 +522,14 @@ int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t*
     k_effective<<<grid_for(n_ins, kThreads), kThreads, 0, s>>>(ins_src, ins_dst, n_ins, 0, old.off.p, old.adj.p,
                                                                nout.off.p, nout.adj.p, ins_eff);
   PRDF_LAUNCH_CHECK();
+  g->self_loops = true;  // the rebuild gives every vertex its self-loop
   g->csr[PRDF_OUT] = static_cast<Csr&&>(nout);
   g->csr[PRDF_IN] = static_cast<Csr&&>(nin);
   g->csr[PRDF_OUT].m = nout.m;
   g->csr[PRDF_IN].m = nin.m;
   PRDF_TRY(ensure_degrees(g, s));
   g->pvalid[0] = g->pvalid[1] = false;
+  PRDF_TRY(build_relabelled(g, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
   return PRDF_OK;
 }
@@ -547,7 +578,7 @@ int prdf_initial_affected(prdf_graph* g, const int32_t* del_src, const int32_t* 
   cudaStream_t s = (cudaStream_t)stream;
   PRDF_TRY(check_ids(g, del_src, del_dst, n_del, s));
   PRDF_TRY(check_ids(g, ins_src, nullptr, n_ins, s));
-  PRDF_TRY(launch_initial_affected(del_src, del_dst, del_mask, n_del, ins_src, ins_mask, n_ins, dV, dN, s));
+  PRDF_TRY(launch_initial_affected(del_src, del_dst, del_mask, n_del, ins_src, ins_mask, n_ins, nullptr, dV, dN, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
   return PRDF_OK;
 }
@@ -579,14 +610,16 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
   PRDF_TRY(alloc_solver(g, false, s));
   PRDF_CUDA(cudaEventRecord(t.e[0], s));
   // Alg. static: initialise ranks, partition G' by in-degree, iterate
-  k_init_x<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(R0, g->n, g->inv_outdeg.p, g->xa.p, nullptr);
+  // the in-degree partition is the class-contiguous numbering, built with the
+  // graph and rebuilt here only if the thresholds changed
+  PRDF_TRY(ensure_relabelled(g, false, s));
+  k_init_x<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(R0, g->rl.perm.p, g->n, g->rl.inv_deg.p, g->xa.p, nullptr);
   PRDF_LAUNCH_CHECK();
-  g->pvalid[PRDF_IN] = false;
-  PRDF_TRY(ensure_partition(g, PRDF_IN, s));
   PRDF_CUDA(cudaEventRecord(t.e[1], s));
   IterResult it;
   PRDF_TRY(iterate(g, p, false, &it, s));
-  k_finalize<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, g->outdeg.p, g->n, ranks);
+  k_finalize<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, g->rl.degd.p,
+                                                           g->rl.perm.p, g->n, ranks, nullptr, nullptr);
   PRDF_LAUNCH_CHECK();
   PRDF_CUDA(cudaEventRecord(t.e[2], s));
   PRDF_CUDA(cudaEventSynchronize(t.e[2]));
@@ -601,8 +634,8 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
     cudaEventElapsedTime(&stats->ms_iterate, t.e[1], t.e[2]);
     stats->ms_sweep = it.ms_sweep;
     stats->edges_processed = (long long)it.iters * g->csr[PRDF_IN].m;
-    // init + partition (count, 3 scan kernels, scatter) + sweeps + finalize
-    stats->kernel_launches = 1 + 5 + it.kernels + 1;
+    // init + sweeps + finalize
+    stats->kernel_launches = 1 + it.kernels + 1;
   }
   return PRDF_OK;
 }
@@ -626,30 +659,32 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
   const int n = g->n;
   PRDF_CUDA(cudaEventRecord(t.e[0], s));
   // Alg. frontier: R = Rnew = R^{t-1}; partition G and G'; mark; iterate
-  k_init_x<<<grid_for(n, kThreads), kThreads, 0, s>>>(prev_ranks, n, g->inv_outdeg.p, g->xa.p, g->xb.p);
+  // partitions: G' by in-degree is the sweep numbering; G by out-degree (for marking) per call
+  g->rl.pout_valid = false;
+  PRDF_TRY(ensure_relabelled(g, true, s));
+  const Relabel& rl = g->rl;
+  k_init_x<<<grid_for(n, kThreads), kThreads, 0, s>>>(prev_ranks, rl.perm.p, n, rl.inv_deg.p, g->xa.p, g->xb.p);
   PRDF_LAUNCH_CHECK();
-  g->pvalid[PRDF_OUT] = g->pvalid[PRDF_IN] = false;
-  PRDF_TRY(ensure_partition(g, PRDF_OUT, s));
-  PRDF_TRY(ensure_partition(g, PRDF_IN, s));
   PRDF_CUDA(cudaEventRecord(t.e[1], s));
   PRDF_CUDA(cudaMemsetAsync(g->dV.p, 0, (size_t)n, s));
   PRDF_CUDA(cudaMemsetAsync(g->dN.p, 0, (size_t)n, s));
   PRDF_CUDA(cudaMemsetAsync(g->wrote.p, 0, (size_t)n, s));
-  PRDF_TRY(launch_initial_affected(del_src, del_dst, del_mask, n_del, ins_src, ins_mask, n_ins, g->dV.p, g->dN.p, s));
+  PRDF_TRY(launch_initial_affected(del_src, del_dst, del_mask, n_del, ins_src, ins_mask, n_ins, rl.inv.p, g->dV.p,
+                                   g->dN.p, s));
   int64_t cbo[kMaxThr + 2];
-  class_begins(g, PRDF_OUT, cbo);
-  PRDF_TRY(launch_expand(g->csr[PRDF_OUT].off.p, g->csr[PRDF_OUT].adj.p, g->P[PRDF_OUT].p, cbo, g->thr[PRDF_OUT].n + 1,
-                         g->dN.p, g->dV.p, nullptr, 0.0, s));
+  begins_from_counts(rl.pout_count, g->thr[PRDF_OUT].n + 1, cbo);
+  PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, g->thr[PRDF_OUT].n + 1, g->dN.p, g->dV.p,
+                         nullptr, 0.0, s));
   PRDF_TRY(count_flags(g->dV.p, n, g->counter.p, s));
   PRDF_CUDA(cudaEventRecord(t.e[2], s));
   PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64 + 8, g->counter.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   IterResult it;
   PRDF_TRY(iterate(g, p, true, &it, s));  // synchronises the stream
   const long long aff0 = (long long)g->ws.host_i64[8];
-  k_finalize<<<grid_for(n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, g->outdeg.p, n, ranks);
+  k_finalize<<<grid_for(n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, rl.degd.p, rl.perm.p, n,
+                                                       ranks, g->dV.p, dV_out);
   PRDF_LAUNCH_CHECK();
   PRDF_CUDA(cudaEventRecord(t.e[3], s));
-  if (dV_out) PRDF_CUDA(cudaMemcpyAsync(dV_out, g->dV.p, (size_t)n, cudaMemcpyDeviceToDevice, s));
   PRDF_CUDA(cudaEventSynchronize(t.e[3]));
   PRDF_CUDA(cudaStreamSynchronize(s));
   if (stats) {
@@ -665,11 +700,9 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
     stats->ms_sweep = it.ms_sweep;
     stats->edges_processed = -1;
     stats->affected_initial = aff0;
-    int64_t cbo2[kMaxThr + 2];
-    class_begins(g, PRDF_OUT, cbo2);
-    // init + 2 partitions + initial marking + expand + count + sweeps/expands + finalize
-    stats->kernel_launches = 1 + 10 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo2, g->thr[PRDF_OUT].n + 1) +
-                             1 + it.kernels + 1;
+    // out-degree partition + init + initial marking + expand + count + sweeps/expands + finalize
+    stats->kernel_launches = 5 + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, g->thr[PRDF_OUT].n + 1) + 1 +
+                             it.kernels + 1;
   }
   return PRDF_OK;
 }

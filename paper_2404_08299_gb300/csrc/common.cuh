@@ -126,62 +126,97 @@ __device__ __forceinline__ float warp_sum_f32(float v) {
 //
 // GB300 issues FP64 additions at about 1.6 per clock per SM (measured), 70x
 // below FP32, so an FP64 add per edge would bound the sweep by the FP64 pipe
-// instead of HBM. In-neighbour sums of non-negative FP64 terms below 2^7 are
-// therefore accumulated exactly in a 128-bit integer with 2^-120 resolution
-// (integer pipes), and the exact sum is rounded once to FP64 (round to
-// nearest even). The result is the correctly rounded sum, independent of
-// summation order, so every kernel shape and thread count gives the same bits.
-// Terms below 2^-120 are truncated (absolute error < 2^-120 per term).
+// instead of HBM. In-neighbour sums of non-negative FP64 terms are therefore
+// accumulated exactly in a 128-bit integer (four 32-bit words, resolution
+// 2^-124) on the integer pipes, and the exact sum is rounded once to FP64
+// (round to nearest, ties to even). The result is the correctly rounded sum,
+// independent of summation order, so every kernel shape and thread count
+// gives the same bits. Valid for terms in [0, 8) and sums below 16; a term
+// below 2^-72 is dropped (absolute error < 2^-72 per term).
 
-constexpr int kFixFrac = 120;
+constexpr int kFixFrac = 124;
 
-typedef unsigned __int128 fix128;
+struct Fix4 {
+  uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;  // value = (w3:w2:w1:w0) * 2^-124
 
-__device__ __forceinline__ fix128 fix_from_double(double x) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x);
-  const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
-  const uint64_t m = (b & 0x000FFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
-  // x = m * 2^(max(e,1) - 1075); in units of 2^-120 that is m << (max(e,1) - 955)
-  const int s = (int)(e ? e : 1u) - (1075 - kFixFrac);
-  fix128 t = (fix128)m;
-  if (s >= 0) t <<= (unsigned)s;
-  else t = (s > -64) ? (t >> (unsigned)(-s)) : (fix128)0;
-  return t;
-}
-
-__device__ __forceinline__ void fix_add(fix128& acc, double x) { acc += fix_from_double(x); }
-
-// Round a fixed-point value (units 2^-120) to the nearest double, ties to even.
-__device__ __forceinline__ double fix_to_double(fix128 a) {
-  if (a == 0) return 0.0;
-  const uint64_t hi = (uint64_t)(a >> 64), lo = (uint64_t)a;
-  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
-  const fix128 nrm = a << (unsigned)lz;  // leading one at bit 127
-  const uint64_t top = (uint64_t)(nrm >> 64);
-  const uint64_t rest = (uint64_t)nrm;
-  uint64_t mant = top >> 11;  // 53 significant bits
-  const uint64_t rb = top & 0x7FFull;
-  const bool sticky = rest != 0;
-  const bool up = rb > 0x400ull || (rb == 0x400ull && (sticky || (mant & 1ull)));
-  mant += up ? 1ull : 0ull;
-  int ex = (127 - lz) - kFixFrac;  // unbiased exponent of the leading one
-  if (mant >> 53) {
-    mant >>= 1;
-    ++ex;
+  __device__ __forceinline__ void add4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3) {
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.cc.u32 %2, %2, %6;\n\t"
+        "addc.u32 %3, %3, %7;"
+        : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3)
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3));
   }
-  const uint64_t bits = ((uint64_t)(ex + 1023) << 52) | (mant & 0x000FFFFFFFFFFFFFull);
-  return __longlong_as_double((long long)bits);
-}
 
-__device__ __forceinline__ fix128 warp_sum_fix(fix128 v) {
+  // add the non-negative double whose bit pattern is xb
+  __device__ __forceinline__ void add(uint64_t xb) {
+    const uint32_t hi = (uint32_t)(xb >> 32), lo = (uint32_t)xb;
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+    // the mantissa's least significant bit sits at 2^(e - 1075) = 2^-124 * 2^(e - 951)
+    const int p = (int)e - (1075 - kFixFrac);
+    const bool ok = p >= 0;
+    const uint32_t pp = ok ? (uint32_t)p : 0u;
+    const uint32_t b = pp & 31u, w = pp >> 5;
+    const uint32_t t0 = lo << b;
+    const uint32_t t1 = __funnelshift_l(lo, mh, b);
+    const uint32_t t2 = __funnelshift_l(mh, 0u, b);
+    uint32_t a0 = w == 0 ? t0 : 0u;
+    uint32_t a1 = w == 0 ? t1 : (w == 1 ? t0 : 0u);
+    uint32_t a2 = w == 0 ? t2 : (w == 1 ? t1 : t0);
+    uint32_t a3 = w == 0 ? 0u : (w == 1 ? t2 : t1);
+    if (!ok) a0 = a1 = a2 = a3 = 0u;
+    add4(a0, a1, a2, a3);
+  }
+
+  __device__ __forceinline__ void add_words(const uint32_t* s) { add4(s[0], s[1], s[2], s[3]); }
+  __device__ __forceinline__ void store(uint32_t* s) const {
+    s[0] = w0;
+    s[1] = w1;
+    s[2] = w2;
+    s[3] = w3;
+  }
+
+  template <int G>
+  __device__ __forceinline__ void group_reduce() {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)v, o);
-    uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(v >> 64), o);
-    v += ((fix128)hi << 64) | lo;
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const uint32_t a0 = __shfl_xor_sync(0xffffffffu, w0, o);
+      const uint32_t a1 = __shfl_xor_sync(0xffffffffu, w1, o);
+      const uint32_t a2 = __shfl_xor_sync(0xffffffffu, w2, o);
+      const uint32_t a3 = __shfl_xor_sync(0xffffffffu, w3, o);
+      add4(a0, a1, a2, a3);
+    }
   }
-  return v;
-}
+
+  // round to the nearest double, ties to even
+  __device__ __forceinline__ double to_double() const {
+    const uint64_t H = ((uint64_t)w3 << 32) | w2, L = ((uint64_t)w1 << 32) | w0;
+    if ((H | L) == 0) return 0.0;
+    const int lz = H ? __clzll((long long)H) : 64 + __clzll((long long)L);
+    uint64_t nH, nL;
+    if (lz == 0) {
+      nH = H;
+      nL = L;
+    } else if (lz < 64) {
+      nH = (H << lz) | (L >> (64 - lz));
+      nL = L << lz;
+    } else {
+      nH = L << (lz - 64);
+      nL = 0;
+    }
+    uint64_t mant = nH >> 11;  // 53 significant bits, leading one at bit 52
+    const uint64_t rb = nH & 0x7FFull;
+    const bool up = rb > 0x400ull || (rb == 0x400ull && (nL != 0 || (mant & 1ull)));
+    mant += up ? 1ull : 0ull;
+    int ex = (127 - lz) - kFixFrac;  // unbiased exponent of the leading one
+    if (mant >> 53) {
+      mant >>= 1;
+      ++ex;
+    }
+    return __longlong_as_double((long long)(((uint64_t)(ex + 1023) << 52) | (mant & 0x000FFFFFFFFFFFFFull)));
+  }
+};
 
 // non-negative doubles order like their bit patterns
 __device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
@@ -193,34 +228,50 @@ __device__ __forceinline__ double bitsd(uint64_t b) { return __longlong_as_doubl
 // (evict-last policy on the gathers).
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 __device__ __forceinline__ int ld_stream_i32(const int32_t* p, uint64_t pol) {
   int v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
 __device__ __forceinline__ int4 ld_stream_i32x4(const int32_t* p, uint64_t pol) {
   int4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                : "l"(p), "l"(pol));
   return v;
 }
+__device__ __forceinline__ int64_t ld_stream_i64(const int64_t* p, uint64_t pol) {
+  int64_t v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_stream_f64(const double* p, uint64_t pol) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+// gathered FP64 value returned as its bit pattern (stays on the integer pipes)
+__device__ __forceinline__ uint64_t ld_gather_b64(const double* p, uint64_t pol) {
+  uint64_t v;
+  asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
 __device__ __forceinline__ double ld_gather_f64(const double* p, uint64_t pol) {
   double v;
-  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
   return v;
 }
 __device__ __forceinline__ float ld_gather_f32(const float* p, uint64_t pol) {
   float v;
-  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
   return v;
 }
 

@@ -14,17 +14,20 @@ constexpr int kThreads = 256;
 __global__ void k_initial_affected(const int32_t* __restrict__ del_src, const int32_t* __restrict__ del_dst,
                                    const uint8_t* __restrict__ del_mask, int64_t n_del,
                                    const int32_t* __restrict__ ins_src, const uint8_t* __restrict__ ins_mask,
-                                   int64_t n_ins, uint8_t* __restrict__ dV, uint8_t* __restrict__ dN) {
+                                   int64_t n_ins, const int32_t* __restrict__ map, uint8_t* __restrict__ dV,
+                                   uint8_t* __restrict__ dN) {
   const int64_t tot = n_del + n_ins;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
     if (i < n_del) {
       if (del_mask && !del_mask[i]) continue;
-      dN[del_src[i]] = 1;  // out-neighbours of the source are affected
-      dV[del_dst[i]] = 1;  // the target is affected
+      const int32_t u = del_src[i], v = del_dst[i];
+      dN[map ? map[u] : u] = 1;  // out-neighbours of the source are affected
+      dV[map ? map[v] : v] = 1;  // the target is affected
     } else {
       const int64_t k = i - n_del;
       if (ins_mask && !ins_mask[k]) continue;
-      dN[ins_src[k]] = 1;
+      const int32_t u = ins_src[k];
+      dN[map ? map[u] : u] = 1;
     }
   }
 }
@@ -74,11 +77,11 @@ __global__ void k_count_flags(const uint8_t* __restrict__ f, int64_t n, unsigned
 }  // namespace
 
 int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask, int64_t n_del,
-                            const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins, uint8_t* dV, uint8_t* dN,
-                            cudaStream_t s) {
+                            const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins, const int32_t* map,
+                            uint8_t* dV, uint8_t* dN, cudaStream_t s) {
   if (n_del + n_ins == 0) return PRDF_OK;
   k_initial_affected<<<grid_for(n_del + n_ins, kThreads), kThreads, 0, s>>>(del_src, del_dst, del_mask, n_del, ins_src,
-                                                                             ins_mask, n_ins, dV, dN);
+                                                                             ins_mask, n_ins, map, dV, dN);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }

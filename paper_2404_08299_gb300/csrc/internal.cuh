@@ -5,11 +5,11 @@
 
 namespace prdf {
 
-constexpr int kMaxThr = 3;  // at most four degree classes
+constexpr int kMaxThr = 7;  // at most eight degree classes
 
 struct PartThr {
   int n = 0;                    // number of thresholds (classes = n + 1)
-  int64_t thr[kMaxThr] = {0, 0, 0};
+  int64_t thr[kMaxThr] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 // Scratch reused across calls on one graph. Calls on a graph do not overlap.
@@ -46,16 +46,31 @@ struct Csr {
 int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, const float* w, bool self_loops,
               bool allow_skip, Csr& out, Workspace& ws, cudaStream_t s);
 
+// The graph renumbered so that each in-degree class is a contiguous id range
+// (new id i = vertex perm[i], perm being the in-degree partition).
+struct Relabel {
+  bool valid = false;
+  PartThr thr;                       // in-degree classes the numbering follows
+  int64_t count[kMaxThr + 1] = {};   // class sizes; class c is ids [sum(count[<c]), +count[c])
+  DBuf<int32_t> perm;                // new -> old
+  DBuf<int32_t> inv;                 // old -> new
+  Csr in, out;                       // G' and G in the new numbering
+  DBuf<double> degd, inv_deg;        // |out(i)| and 1/|out(i)| in the new numbering
+  DBuf<int32_t> pout;                // out-degree partition of `out` (new ids), for marking
+  int64_t pout_count[kMaxThr + 1] = {};
+  bool pout_valid = false;
+};
+
 // Per-sweep arguments of the pull rank kernels (Alg. update).
 struct SweepArgs {
   const int64_t* off;      // in-CSR offsets of G'
   const int32_t* adj;      // in-CSR sources
-  const int32_t* P;        // in-degree partition (all classes)
   const double* x;         // x[u] = R[u] / |out(u)| of the previous iteration
   double* xn;              // next x
-  const int32_t* deg;      // |out(v)| (self-loop included)
+  const double* degd;      // |out(v)| (self-loop included), as a double
   const double* inv_deg;   // 1 / |out(v)|
   double alpha, c0;        // damping, (1 - alpha) / n
+  int self_loops;          // every vertex has exactly one self-loop (graph built with PRDF_ADD_SELF_LOOPS)
   uint64_t* resid;         // L-inf change of this sweep (bits of a non-negative double), atomic max
   const uint64_t* prev;    // L-inf change of the previous sweep, or null on the first sweep
   double tol;              // the sweep exits at once if *prev <= tol (already converged)
@@ -68,13 +83,13 @@ struct SweepArgs {
 };
 
 // Launch one rank sweep (all degree classes) for Static (dynamic = false) or DF/DF-P.
-int launch_sweep(const SweepArgs& a, const int64_t* class_begin, int nclass, bool exact, bool dynamic,
+int launch_sweep(const SweepArgs& a, const PartThr& t, const int64_t* class_begin, bool exact, bool dynamic,
                  cudaStream_t s);
 
-// Alg. affected kernels (frontier.cu)
+// Alg. affected kernels (frontier.cu). map (nullable): vertex id -> flag index.
 int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask, int64_t n_del,
-                            const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins, uint8_t* dV, uint8_t* dN,
-                            cudaStream_t s);
+                            const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins, const int32_t* map,
+                            uint8_t* dV, uint8_t* dN, cudaStream_t s);
 // expandAffected over the out-degree partition; skipped on the device when *resid <= tol
 int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, const int64_t* cb, int nclass,
                   const uint8_t* dN, uint8_t* dV, const uint64_t* resid, double tol, cudaStream_t s);
@@ -86,9 +101,10 @@ int count_flags(const uint8_t* f, int64_t n, unsigned long long* dev_out, cudaSt
 struct prdf_graph {
   int32_t n = 0;
   bool weighted = false;
+  bool self_loops = true;           // every vertex has exactly one self-loop
   cudaStream_t stream = nullptr;
   prdf::Csr csr[2];                  // [PRDF_OUT] = G, [PRDF_IN] = G'
-  prdf::DBuf<int32_t> outdeg;        // |out(v)|
+  prdf::DBuf<double> outdeg;         // |out(v)| as a double
   prdf::DBuf<double> inv_outdeg;     // 1 / |out(v)|
   prdf::PartThr thr[2];              // class thresholds per CSR
   prdf::DBuf<int32_t> P[2];          // partitions
@@ -100,4 +116,9 @@ struct prdf_graph {
   prdf::DBuf<uint64_t> resid;
   prdf::DBuf<uint8_t> dV, dN, wrote;
   prdf::DBuf<unsigned long long> counter;
+  prdf::Relabel rl;                  // class-contiguous copy used by the sweeps
 };
+
+namespace prdf {
+int build_relabelled(prdf_graph* g, cudaStream_t s);
+}

@@ -115,19 +115,32 @@ __device__ __forceinline__ int degree_class(int64_t d, const PartThr& t) {
   return c;
 }
 
+// Class counts of a thread's vertices, packed as 16-bit fields: classes 0-3 in
+// p[0], classes 4-7 in p[1] (a tile has at most 2048 vertices).
+struct Packed2 {
+  uint64_t p[2] = {0, 0};
+  __device__ __forceinline__ void add(int c) { p[c >> 2] += 1ull << (16 * (c & 3)); }
+  __device__ __forceinline__ int64_t get(int c) const { return (int64_t)((p[c >> 2] >> (16 * (c & 3))) & 0xFFFF); }
+};
+
 // count[c * ntiles + tile] = number of vertices of class c in the tile
 __global__ void k_part_count(const int64_t* __restrict__ off, int64_t n, PartThr t, int64_t* __restrict__ count) {
   const int64_t base = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartItems;
-  uint64_t packed = 0;  // 16-bit count per class
+  Packed2 pk;
 #pragma unroll
   for (int k = 0; k < kPartItems; ++k) {
     const int64_t v = base + k;
-    if (v < n) packed += 1ull << (16 * degree_class(off[v + 1] - off[v], t));
+    if (v < n) pk.add(degree_class(off[v + 1] - off[v], t));
   }
-  __shared__ uint64_t tot;
-  block_exclusive_scan<uint64_t>(packed, &tot);
-  if (threadIdx.x == 0)
-    for (int c = 0; c <= t.n; ++c) count[(int64_t)c * gridDim.x + blockIdx.x] = (int64_t)((tot >> (16 * c)) & 0xFFFF);
+  __shared__ uint64_t tot0, tot1;
+  block_exclusive_scan<uint64_t>(pk.p[0], &tot0);
+  if (t.n >= 4) block_exclusive_scan<uint64_t>(pk.p[1], &tot1);
+  if (threadIdx.x == 0) {
+    Packed2 tot;
+    tot.p[0] = tot0;
+    tot.p[1] = t.n >= 4 ? tot1 : 0;
+    for (int c = 0; c <= t.n; ++c) count[(int64_t)c * gridDim.x + blockIdx.x] = tot.get(c);
+  }
 }
 
 // P[base[c][tile] + rank within tile] = v, ranks in ascending vertex order (stable).
@@ -135,22 +148,24 @@ __global__ void k_part_scatter(const int64_t* __restrict__ off, int64_t n, PartT
                                int32_t* __restrict__ P) {
   const int64_t first = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartItems;
   int cls[kPartItems];
-  uint64_t packed = 0;
+  Packed2 pk;
 #pragma unroll
   for (int k = 0; k < kPartItems; ++k) {
     const int64_t v = first + k;
     cls[k] = v < n ? degree_class(off[v + 1] - off[v], t) : -1;
-    if (cls[k] >= 0) packed += 1ull << (16 * cls[k]);
+    if (cls[k] >= 0) pk.add(cls[k]);
   }
-  __shared__ uint64_t tot;
-  uint64_t ex = block_exclusive_scan<uint64_t>(packed, &tot);
+  __shared__ uint64_t tot0, tot1;
+  Packed2 ex;
+  ex.p[0] = block_exclusive_scan<uint64_t>(pk.p[0], &tot0);
+  if (t.n >= 4) ex.p[1] = block_exclusive_scan<uint64_t>(pk.p[1], &tot1);
 #pragma unroll
   for (int k = 0; k < kPartItems; ++k) {
     if (cls[k] < 0) continue;
     const int c = cls[k];
-    const int64_t pos = base[(int64_t)c * gridDim.x + blockIdx.x] + (int64_t)((ex >> (16 * c)) & 0xFFFF);
+    const int64_t pos = base[(int64_t)c * gridDim.x + blockIdx.x] + ex.get(c);
     P[pos] = (int32_t)(first + k);
-    ex += 1ull << (16 * c);
+    ex.add(c);
   }
 }
 
@@ -231,7 +246,8 @@ namespace {
 
 constexpr int64_t kNoAllocMaxN = 1ll << 24;
 constexpr int64_t kNoAllocMaxTiles = (kNoAllocMaxN + kPartTile - 1) / kPartTile;
-constexpr int64_t kNoAllocCnt = (int64_t)(kMaxThr + 1) * kNoAllocMaxTiles;
+constexpr int kNoAllocMaxThr = 3;  // at most four classes
+constexpr int64_t kNoAllocCnt = (int64_t)(kNoAllocMaxThr + 1) * kNoAllocMaxTiles;
 constexpr int64_t kNoAllocScan = (kNoAllocCnt + kScanTile - 1) / kScanTile + 1;
 constexpr int64_t kNoAllocWords = kNoAllocCnt + (kNoAllocCnt + 1) + kNoAllocScan;
 
@@ -266,7 +282,7 @@ int noalloc_scratch(int64_t** out) {
 extern "C" int prdf_partition_noalloc(const int64_t* off, int32_t n, int n_thr, const int64_t* thr_host, int32_t* P,
                                       int64_t* counts_host, void* stream) {
   using namespace prdf;
-  if (!off || !P || !counts_host || !thr_host || n < 1 || n_thr < 1 || n_thr > kMaxThr) {
+  if (!off || !P || !counts_host || !thr_host || n < 1 || n_thr < 1 || n_thr > kNoAllocMaxThr) {
     set_error("prdf_partition_noalloc: bad arguments");
     return PRDF_EINVAL;
   }
@@ -300,7 +316,7 @@ extern "C" int prdf_partition_noalloc(const int64_t* off, int32_t n, int n_thr, 
   k_scan_apply<int64_t><<<(unsigned)nt2, kScanThreads, 0, s>>>(cnt, cn, sums, base);
   k_part_scatter<<<(unsigned)nt, kScanThreads, 0, s>>>(off, n, t, base, P);
   PRDF_LAUNCH_CHECK();
-  int64_t hb[kMaxThr + 2];
+  int64_t hb[kNoAllocMaxThr + 2];
   for (int c = 0; c <= C; ++c)
     PRDF_CUDA(cudaMemcpyAsync(hb + c, base + (int64_t)c * nt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   PRDF_CUDA(cudaStreamSynchronize(s));

@@ -3,12 +3,19 @@
 // (Eq. 1 / Eq. 2 on affected vertices, with prune and expand flags).
 //
 // State: x[u] = R[u] / |out(u)|, so a sweep gathers one FP64 value per
-// in-edge. Each vertex v is processed by a group of G lanes (G = 1, 8, 32)
-// or a whole block, chosen by in-degree class (the paper's thread-per-vertex
-// and block-per-vertex kernels, with two middle classes added). The L-inf
-// change of the sweep is reduced in the epilogue (warp max, block max, one
-// 64-bit atomic max per block on the bit pattern of a non-negative double);
-// rank writes stay one plain store per vertex.
+// in-edge. The sweeps run on the class-contiguous numbering (relabel.cu):
+// class c is the id range [begin, end). Vertices are split by in-degree class (the paper's thread- and
+// block-per-vertex kernels, refined into narrower classes so the lanes of a
+// warp carry similar work): each vertex is processed by a group of G lanes
+// (G = 1, 4, 16, 32) or by a whole block. The L-inf change of the sweep is
+// reduced in the epilogue (warp max, block max, one 64-bit atomic max per
+// block on the bit pattern of a non-negative double); rank writes stay one
+// plain store per vertex.
+//
+// GB300 issues FP64 instructions at ~1.6 per clock per SM, so gathered
+// values stay in 64-bit integer registers and are summed exactly on the
+// integer pipes (common.cuh); FP64 arithmetic is limited to a few
+// instructions per vertex.
 //
 // A sweep whose predecessor already met the tolerance exits at once, so the
 // host can launch several sweeps ahead of its convergence check.
@@ -19,123 +26,122 @@ namespace prdf {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 8;
 
+// Exact accumulator (4 x 32-bit words, 2^-124 resolution) or plain FP64.
 template <bool EXACT>
 struct Acc;
 
 template <>
 struct Acc<true> {
-  fix128 v = 0;
-  __device__ __forceinline__ void add(double x) { fix_add(v, x); }
+  Fix4 v;
+  __device__ __forceinline__ void add(uint64_t xb) { v.add(xb); }
   template <int G>
-  __device__ __forceinline__ void group_reduce() {
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)v, o);
-      uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(v >> 64), o);
-      v += ((fix128)hi << 64) | lo;
-    }
-  }
-  __device__ __forceinline__ double value() const { return fix_to_double(v); }
-  __device__ __forceinline__ void merge_raw(uint64_t lo, uint64_t hi) { v += ((fix128)hi << 64) | lo; }
-  __device__ __forceinline__ uint64_t lo() const { return (uint64_t)v; }
-  __device__ __forceinline__ uint64_t hi() const { return (uint64_t)(v >> 64); }
+  __device__ __forceinline__ void group_reduce() { v.template group_reduce<G>(); }
+  __device__ __forceinline__ double value() const { return v.to_double(); }
+  __device__ __forceinline__ void to_shared(uint32_t* s) const { v.store(s); }
+  __device__ __forceinline__ void from_shared(const uint32_t* s) { v.add_words(s); }
 };
 
 template <>
 struct Acc<false> {
   double v = 0;
-  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add(uint64_t xb) { v += bitsd(xb); }
   template <int G>
   __device__ __forceinline__ void group_reduce() {
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   }
   __device__ __forceinline__ double value() const { return v; }
-  __device__ __forceinline__ void merge_raw(uint64_t lo, uint64_t) { v += bitsd(lo); }
-  __device__ __forceinline__ uint64_t lo() const { return dbits(v); }
-  __device__ __forceinline__ uint64_t hi() const { return 0; }
+  __device__ __forceinline__ void to_shared(uint32_t* s) const {
+    const uint64_t b = dbits(v);
+    s[0] = (uint32_t)b;
+    s[1] = (uint32_t)(b >> 32);
+  }
+  __device__ __forceinline__ void from_shared(const uint32_t* s) {
+    v += bitsd(((uint64_t)s[1] << 32) | s[0]);
+  }
 };
 
-// Per-lane gather over row [b, e) of G' with stride G and kUnroll loads in flight.
-template <int G, bool EXACT>
+// Per-lane gather over row [b, e) of G' with stride G and U loads in flight.
+template <int G, int U, bool EXACT>
 __device__ __forceinline__ void gather_row(const SweepArgs& a, int64_t b, int64_t e, int lane, int32_t v,
-                                           Acc<EXACT>& acc, double& xself, uint64_t pf, uint64_t pl) {
-  for (int64_t j0 = b + lane; j0 < e; j0 += (int64_t)G * kUnroll) {
-    int32_t u[kUnroll];
+                                           Acc<EXACT>& acc, uint64_t& xself, uint64_t pf, uint64_t pl) {
+  for (int64_t j0 = b + lane; j0 < e; j0 += (int64_t)G * U) {
+    int32_t u[U];
 #pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
+    for (int k = 0; k < U; ++k) {
       const int64_t j = j0 + (int64_t)k * G;
       u[k] = j < e ? ld_stream_i32(a.adj + j, pf) : -1;
     }
-    double xv[kUnroll];
+    uint64_t xv[U];
 #pragma unroll
-    for (int k = 0; k < kUnroll; ++k) xv[k] = u[k] >= 0 ? ld_gather_f64(a.x + u[k], pl) : 0.0;
+    for (int k = 0; k < U; ++k) xv[k] = u[k] >= 0 ? ld_gather_b64(a.x + u[k], pl) : 0ull;
 #pragma unroll
-    for (int k = 0; k < kUnroll; ++k) {
+    for (int k = 0; k < U; ++k) {
       if (u[k] >= 0) acc.add(xv[k]);
-      if (u[k] == v) xself = xv[k];
+      xself = (u[k] == v) ? xv[k] : xself;
     }
   }
 }
 
 // Vectorised variant for a row handled by NT lanes: 16-byte index loads for
-// the aligned body, scalar loads for the head and tail.
-template <int NT, bool EXACT>
+// the aligned body (KV of them in flight per lane), scalar head and tail.
+template <int NT, int KV, bool EXACT>
 __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, int64_t e, int lane, int32_t v,
-                                               Acc<EXACT>& acc, double& xself, uint64_t pf, uint64_t pl) {
+                                               Acc<EXACT>& acc, uint64_t& xself, uint64_t pf, uint64_t pl) {
   int64_t ba = (b + 3) & ~(int64_t)3;
   if (ba > e) ba = e;
   const int64_t ea = ba + ((e - ba) & ~(int64_t)3);
-  // head and tail: at most 3 + 3 scalar elements
   {
     const int64_t nh = ba - b, nt = e - ea;
-    if (lane < nh) {
-      const int32_t u = ld_stream_i32(a.adj + b + lane, pf);
-      const double xv = ld_gather_f64(a.x + u, pl);
+    int64_t j = -1;
+    if (lane < nh) j = b + lane;
+    else if (lane >= 4 && lane < 4 + nt) j = ea + (lane - 4);
+    if (j >= 0) {
+      const int32_t u = ld_stream_i32(a.adj + j, pf);
+      const uint64_t xv = ld_gather_b64(a.x + u, pl);
       acc.add(xv);
-      if (u == v) xself = xv;
-    } else if (lane >= 4 && lane < 4 + nt) {
-      const int32_t u = ld_stream_i32(a.adj + ea + (lane - 4), pf);
-      const double xv = ld_gather_f64(a.x + u, pl);
-      acc.add(xv);
-      if (u == v) xself = xv;
+      xself = (u == v) ? xv : xself;
     }
   }
-  constexpr int kV = 2;  // int4 loads in flight per lane
-  for (int64_t q0 = ba + 4 * (int64_t)lane; q0 < ea; q0 += 4 * (int64_t)NT * kV) {
-    int4 u4[kV];
+  for (int64_t q0 = ba + 4 * (int64_t)lane; q0 < ea; q0 += 4 * (int64_t)NT * KV) {
+    int4 u4[KV];
 #pragma unroll
-    for (int k = 0; k < kV; ++k) {
+    for (int k = 0; k < KV; ++k) {
       const int64_t q = q0 + 4 * (int64_t)NT * k;
       u4[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
     }
-    double xv[4 * kV];
+    uint64_t xv[4 * KV];
 #pragma unroll
-    for (int k = 0; k < kV; ++k) {
-      xv[4 * k + 0] = u4[k].x >= 0 ? ld_gather_f64(a.x + u4[k].x, pl) : 0.0;
-      xv[4 * k + 1] = u4[k].y >= 0 ? ld_gather_f64(a.x + u4[k].y, pl) : 0.0;
-      xv[4 * k + 2] = u4[k].z >= 0 ? ld_gather_f64(a.x + u4[k].z, pl) : 0.0;
-      xv[4 * k + 3] = u4[k].w >= 0 ? ld_gather_f64(a.x + u4[k].w, pl) : 0.0;
+    for (int k = 0; k < KV; ++k) {
+      xv[4 * k + 0] = u4[k].x >= 0 ? ld_gather_b64(a.x + u4[k].x, pl) : 0ull;
+      xv[4 * k + 1] = u4[k].y >= 0 ? ld_gather_b64(a.x + u4[k].y, pl) : 0ull;
+      xv[4 * k + 2] = u4[k].z >= 0 ? ld_gather_b64(a.x + u4[k].z, pl) : 0ull;
+      xv[4 * k + 3] = u4[k].w >= 0 ? ld_gather_b64(a.x + u4[k].w, pl) : 0ull;
     }
 #pragma unroll
-    for (int k = 0; k < kV; ++k) {
-      const int us[4] = {u4[k].x, u4[k].y, u4[k].z, u4[k].w};
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (us[t] >= 0) acc.add(xv[4 * k + t]);
-        if (us[t] == v) xself = xv[4 * k + t];
-      }
+    for (int k = 0; k < KV; ++k) {
+      if (u4[k].x < 0) continue;  // a whole int4 is valid or not
+      acc.add(xv[4 * k + 0]);
+      acc.add(xv[4 * k + 1]);
+      acc.add(xv[4 * k + 2]);
+      acc.add(xv[4 * k + 3]);
+      xself = (u4[k].x == v) ? xv[4 * k + 0] : xself;
+      xself = (u4[k].y == v) ? xv[4 * k + 1] : xself;
+      xself = (u4[k].z == v) ? xv[4 * k + 2] : xself;
+      xself = (u4[k].w == v) ? xv[4 * k + 3] : xself;
     }
   }
 }
 
 // Vertex epilogue: Eq. 1 (Static, DF) or Eq. 2 (DF-P), prune / expand flags,
-// next x, and this vertex's |r - R[v]|.
+// next x, and this vertex's |r - R[v]| as bits. Four FP64 instructions on the
+// Static path.
 template <bool DYN>
-__device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v, double c, double xself) {
-  const double d = (double)a.deg[v];
+__device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v, double c, uint64_t xself_b,
+                                                  uint64_t pf) {
+  const double xself = bitsd(xself_b);
+  const double d = ld_stream_f64(a.degd + v, pf);
   const double rold = xself * d;  // R[v] of the previous iteration
   double r;
   if (DYN && a.prune) {
@@ -152,7 +158,7 @@ __device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v,
     if (dr > a.tau_f * m) a.dN[v] = 1;
     a.wrote[v] = 1;
   }
-  a.xn[v] = r * a.inv_deg[v];
+  a.xn[v] = r * ld_stream_f64(a.inv_deg + v, pf);
   return dbits(dr);
 }
 
@@ -180,10 +186,24 @@ __device__ __forceinline__ void block_max_to(uint64_t dmax, uint64_t* out) {
   }
 }
 
-// G lanes per vertex (G = 1, 8, 32). The loop is uniform across each warp
-// (a warp owns 32/G consecutive list entries per step), so the group
-// shuffles always see all 32 lanes.
-template <int G, bool EXACT, bool DYN>
+// Work item of a group: list entry, vertex, its row of G' and the first
+// G*U indices of the row (this lane's share).
+template <int U>
+struct Item {
+  int32_t v;
+  int64_t b, e;
+  int32_t u[U];
+};
+
+// G lanes per vertex (G = 1, 4, 16), U indices per lane per round. The loop is
+// uniform across each warp (a warp owns 32/G consecutive list entries per
+// step), so the group shuffles always see all 32 lanes. Software pipeline:
+// the list entry of the item two steps ahead and the offsets and first
+// indices of the next item are loaded while the current item's gathers are
+// in flight, so a step costs about one memory round trip instead of four.
+// With self-loops on every vertex, a row of length 1 is [v] itself and needs
+// no offsets or indices.
+template <int G, int U, bool EXACT, bool DYN, bool SELF1>
 __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a, int64_t begin, int64_t end) {
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
@@ -192,48 +212,123 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a, int
   const int gw = (threadIdx.x & 31) / G;  // group within warp
   const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const int64_t step = nwarps * kGroupsPerWarp;
   uint64_t dmax = 0;
-  for (int64_t base = begin + warp * kGroupsPerWarp; base < end; base += nwarps * kGroupsPerWarp) {
-    const int64_t i = base + gw;
-    bool active = i < end;
-    int32_t v = active ? a.P[i] : -1;
-    if (DYN && active && skip_unaffected(a, v)) active = false;
+
+  auto load_v = [&](int64_t i) -> int32_t { return i < end ? (int32_t)i : -1; };
+  auto load_item = [&](int32_t v, Item<U>& it) {
+    it.v = v;
+    it.b = 0;
+    it.e = 0;
+    if (v >= 0) {
+      if (SELF1) {
+        it.b = 0;
+        it.e = 1;
+      } else {
+        it.b = ld_stream_i64(a.off + v, pf);
+        it.e = ld_stream_i64(a.off + v + 1, pf);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t j = it.b + lane + (int64_t)k * G;
+      if (SELF1) it.u[k] = (v >= 0 && k == 0 && lane == 0) ? v : -1;
+      else it.u[k] = (v >= 0 && j < it.e) ? ld_stream_i32(a.adj + j, pf) : -1;
+    }
+  };
+
+  int64_t base = begin + warp * kGroupsPerWarp;
+  Item<U> cur;
+  load_item(load_v(base + gw), cur);
+  int32_t v_next = load_v(base + step + gw);
+  for (; base < end; base += step) {
+    // gathers of the current item
+    uint64_t xv[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) xv[k] = cur.u[k] >= 0 ? ld_gather_b64(a.x + cur.u[k], pl) : 0ull;
+    // prefetch: next item's row and first indices, and the list entry after it
+    Item<U> nxt;
+    load_item(v_next, nxt);
+    v_next = load_v(base + 2 * step + gw);
+
+    bool active = cur.v >= 0;
+    if (DYN && active && skip_unaffected(a, cur.v)) active = false;
     Acc<EXACT> acc;
-    double xself = 0.0;
+    uint64_t xself = 0;
     if (active) {
-      const int64_t b = a.off[v], e = a.off[v + 1];
-      if (G == 32) gather_row_vec<32, EXACT>(a, b, e, lane, v, acc, xself, pf, pl);
-      else gather_row<G, EXACT>(a, b, e, lane, v, acc, xself, pf, pl);
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (cur.u[k] >= 0) acc.add(xv[k]);
+        xself = (cur.u[k] == cur.v) ? xv[k] : xself;
+      }
+      // rest of a row longer than G*U (not reached with the default classes)
+      if (!SELF1 && cur.e - cur.b > (int64_t)G * U)
+        gather_row<G, U, EXACT>(a, cur.b + (int64_t)G * U, cur.e, lane, cur.v, acc, xself, pf, pl);
     }
     if (G > 1) {
       acc.template group_reduce<G>();
-      uint64_t xb = dbits(xself);
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) {
-        const uint64_t t = __shfl_xor_sync(0xffffffffu, xb, o);
-        xb = t > xb ? t : xb;
+        const uint64_t t = __shfl_xor_sync(0xffffffffu, xself, o);
+        xself = t > xself ? t : xself;
       }
-      xself = bitsd(xb);
     }
     if (active && lane == 0) {
-      const uint64_t db = finish_vertex<DYN>(a, v, acc.value(), xself);
+      const uint64_t db = finish_vertex<DYN>(a, cur.v, acc.value(), xself, pf);
       dmax = db > dmax ? db : dmax;
     }
+    cur = nxt;
+  }
+  block_max_to(dmax, a.resid);
+}
+
+// one warp per vertex, 16-byte index loads; the next vertex's list entry and
+// row offsets are loaded while the current row is gathered
+template <int KV, bool EXACT, bool DYN>
+__global__ void __launch_bounds__(kThreads) k_sweep_warp(const SweepArgs a, int64_t begin, int64_t end) {
+  if (a.prev && bitsd(*a.prev) <= a.tol) return;
+  const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  uint64_t dmax = 0;
+  int64_t i = begin + warp;
+  int32_t v = i < end ? (int32_t)i : -1;
+  int64_t b = v >= 0 ? ld_stream_i64(a.off + v, pf) : 0, e = v >= 0 ? ld_stream_i64(a.off + v + 1, pf) : 0;
+  for (; i < end; i += nwarps) {
+    const int64_t inx = i + nwarps;
+    const int32_t vn = inx < end ? (int32_t)inx : -1;
+    bool active = true;
+    if (DYN && skip_unaffected(a, v)) active = false;
+    Acc<EXACT> acc;
+    uint64_t xself = 0;
+    if (active) gather_row_vec<32, KV, EXACT>(a, b, e, lane, v, acc, xself, pf, pl);
+    const int64_t bn = vn >= 0 ? ld_stream_i64(a.off + vn, pf) : 0, en = vn >= 0 ? ld_stream_i64(a.off + vn + 1, pf) : 0;
+    acc.template group_reduce<32>();
+    xself = warp_max_u64(xself);
+    if (active && lane == 0) {
+      const uint64_t db = finish_vertex<DYN>(a, v, acc.value(), xself, pf);
+      dmax = db > dmax ? db : dmax;
+    }
+    v = vn;
+    b = bn;
+    e = en;
   }
   block_max_to(dmax, a.resid);
 }
 
 // one block per vertex (high in-degree)
-template <bool EXACT, bool DYN>
+template <int KV, bool EXACT, bool DYN>
 __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a, int64_t begin, int64_t end) {
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
-  __shared__ uint64_t s_lo[kThreads / 32], s_hi[kThreads / 32], s_x[kThreads / 32];
+  __shared__ uint32_t s_acc[kThreads / 32][4];
+  __shared__ uint64_t s_x[kThreads / 32];
   __shared__ int s_skip;
   uint64_t dmax = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
-    const int32_t v = a.P[i];
+    const int32_t v = (int32_t)i;
     if (DYN) {
       if (threadIdx.x == 0) s_skip = skip_unaffected(a, v) ? 1 : 0;
       __syncthreads();
@@ -243,13 +338,12 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a, int
     }
     const int64_t b = a.off[v], e = a.off[v + 1];
     Acc<EXACT> acc;
-    double xself = 0.0;
-    gather_row_vec<kThreads, EXACT>(a, b, e, threadIdx.x, v, acc, xself, pf, pl);
+    uint64_t xself = 0;
+    gather_row_vec<kThreads, KV, EXACT>(a, b, e, threadIdx.x, v, acc, xself, pf, pl);
     acc.template group_reduce<32>();
-    const uint64_t xb = warp_max_u64(dbits(xself));
+    const uint64_t xb = warp_max_u64(xself);
     if (lane == 0) {
-      s_lo[wid] = acc.lo();
-      s_hi[wid] = acc.hi();
+      acc.to_shared(s_acc[wid]);
       s_x[wid] = xb;
     }
     __syncthreads();
@@ -257,10 +351,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a, int
       Acc<EXACT> tot;
       uint64_t xm = 0;
       for (int k = 0; k < kThreads / 32; ++k) {
-        tot.merge_raw(s_lo[k], s_hi[k]);
+        tot.from_shared(s_acc[k]);
         xm = s_x[k] > xm ? s_x[k] : xm;
       }
-      const uint64_t db = finish_vertex<DYN>(a, v, tot.value(), bitsd(xm));
+      const uint64_t db = finish_vertex<DYN>(a, v, tot.value(), xm, pf);
       dmax = db > dmax ? db : dmax;
     }
     __syncthreads();
@@ -268,20 +362,43 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a, int
   block_max_to(dmax, a.resid);
 }
 
+// Kernel shape of class c: the last class is block-per-vertex, the one before
+// it warp-per-vertex; lower classes by their upper degree bound.
+enum Kind { kT1 = 0, kT4, kG4, kG16, kWarp, kBlock };
+
+Kind class_kind(const PartThr& t, int c) {
+  const int C = t.n + 1;
+  if (c == C - 1) return kBlock;
+  if (c == C - 2 && C >= 3) return kWarp;
+  const int64_t hi = t.thr[c];
+  if (hi <= 1) return kT1;
+  if (hi <= 4) return kT4;
+  if (hi <= 16) return kG4;
+  if (hi <= 128) return kG16;
+  return kWarp;
+}
+
 template <bool EXACT, bool DYN>
-int launch_all(const SweepArgs& a, const int64_t* cb, int nclass, cudaStream_t s) {
-  // class c covers P[cb[c], cb[c+1]); the group size per class: 1, 8, 32, block
+int launch_all(const SweepArgs& a, const PartThr& t, const int64_t* cb, cudaStream_t s) {
   const int maxg = kSMs * 8;
-  for (int c = 0; c < nclass; ++c) {
+  const int C = t.n + 1;
+  for (int c = 0; c < C; ++c) {
     const int64_t b = cb[c], e = cb[c + 1];
     if (e <= b) continue;
     const int64_t cnt = e - b;
-    const int kind = (nclass == 4) ? c : (c == nclass - 1 ? 3 : c);  // last class is always block-per-vertex
+    const Kind kind = class_kind(t, c);
+    // a class holding only rows of length <= 1 on a graph with all self-loops: the row is [v]
+    const bool self1 = a.self_loops && kind == kT1 && t.thr[c] <= 1;
     switch (kind) {
-      case 0: k_sweep_group<1, EXACT, DYN><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      case 1: k_sweep_group<8, EXACT, DYN><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      case 2: k_sweep_group<32, EXACT, DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      default: k_sweep_block<EXACT, DYN><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kT1:
+        if (self1) k_sweep_group<1, 1, EXACT, DYN, true><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
+        else k_sweep_group<1, 1, EXACT, DYN, false><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
+        break;
+      case kT4: k_sweep_group<1, 4, EXACT, DYN, false><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG4: k_sweep_group<4, 4, EXACT, DYN, false><<<grid_for(cnt * 4, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG16: k_sweep_group<16, 8, EXACT, DYN, false><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kWarp: k_sweep_warp<2, EXACT, DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      default: k_sweep_block<4, EXACT, DYN><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e); break;
     }
   }
   PRDF_LAUNCH_CHECK();
@@ -290,10 +407,10 @@ int launch_all(const SweepArgs& a, const int64_t* cb, int nclass, cudaStream_t s
 
 }  // namespace
 
-int launch_sweep(const SweepArgs& a, const int64_t* class_begin, int nclass, bool exact, bool dynamic,
+int launch_sweep(const SweepArgs& a, const PartThr& t, const int64_t* class_begin, bool exact, bool dynamic,
                  cudaStream_t s) {
-  if (exact) return dynamic ? launch_all<true, true>(a, class_begin, nclass, s) : launch_all<true, false>(a, class_begin, nclass, s);
-  return dynamic ? launch_all<false, true>(a, class_begin, nclass, s) : launch_all<false, false>(a, class_begin, nclass, s);
+  if (exact) return dynamic ? launch_all<true, true>(a, t, class_begin, s) : launch_all<true, false>(a, t, class_begin, s);
+  return dynamic ? launch_all<false, true>(a, t, class_begin, s) : launch_all<false, false>(a, t, class_begin, s);
 }
 
 }  // namespace prdf
