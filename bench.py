@@ -133,6 +133,68 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measure_mixed(g, R64, m, args):
+    """FP32 sweeps with compensated sums to ||dR|| <= 1e-6 ||R|| (relative), then FP64 sweeps to the
+    same L-inf 1e-10: time to tolerance beside the FP64 path and the L-inf distance to its result."""
+    import torch
+    import paper_2404_08299_gb300 as prdf
+    for _ in range(2):
+        g.pagerank_static(precision=prdf.PRDF_FP32_REFINE)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        R, st = g.pagerank_static(precision=prdf.PRDF_FP32_REFINE)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"time_to_tol_ms": ms, "sweeps_fp32": st.iterations_fp32,
+            "sweeps_fp64": st.iterations - st.iterations_fp32, "converged": bool(st.converged),
+            "gteps": st.iterations * m / (ms * 1e-3) / 1e9,
+            "linf_vs_fp64_path": float((R - R64).abs().max()),
+            "note": "FP32 stage stops at ||dR||_inf <= 1e-6 ||R||_inf; FP64 stage to L-inf 1e-10"}
+
+
+def measure_dfp(g, n, m, args):
+    """DF-P after random batches (80% uniform insertions, 20% deletions of existing non-self-loop edges)
+    of size f*|E|, consecutive batches per size, each starting from the previous DF-P ranks. Reports
+    DF-P time (partition + marking + sweeps + expansion, batch application excluded as in the paper),
+    GPU Static time from scratch on the same snapshot, and the L1 error of DF-P against a GPU Static
+    solve at L-inf 1e-13 (the oracle pins the same path on smaller graphs)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2404_08299_gb300 as prdf
+    R_prev, _ = g.pagerank_static()
+    out = []
+    for fi, f in enumerate(args.dfp_sizes):
+        t_dfp, t_static, errs, iters, aff = [], [], [], [], []
+        for b in range(args.dfp_batches):
+            off, adj, _ = g.export_csr(prdf.PRDF_OUT)
+            size = max(1, int(round(f * m)))
+            ds, dd, is_, id_ = synth.batch(n, off.cpu().numpy(), adj.cpu().numpy(), size, seed=1, s1=fi, s2=b)
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            de, ie = g.apply_batch(t(ds), t(dd), t(is_), t(id_))
+            torch.cuda.synchronize()
+            R, st, _ = g.pagerank_dfp(t(ds), t(dd), t(is_), R_prev, del_mask=de, ins_mask=ie)
+            Rs, sts = g.pagerank_static()
+            Rt, _ = g.pagerank_static(tol=1e-13)
+            t_dfp.append(st.ms_total)
+            t_static.append(sts.ms_total)
+            errs.append(float((R - Rt).abs().sum()))
+            iters.append(st.iterations)
+            aff.append(st.affected_initial)
+            R_prev = R
+        out.append({"batch_fraction": f, "batch_size": int(round(f * m)), "batches": args.dfp_batches,
+                    "dfp_ms": statistics.median(t_dfp), "static_ms": statistics.median(t_static),
+                    "speedup_vs_static": statistics.median(t_static) / statistics.median(t_dfp),
+                    "dfp_sweeps": statistics.median(iters), "affected_initial": int(statistics.median(aff)),
+                    "l1_err_max": max(errs)})
+    return out
+
+
 def cpu_baseline(n, src, dst, m, target_s):
     """The FP64 oracle (as it stands) on the host cores: a bounded sample of sweeps
     of the same Static iteration on the same graph."""
@@ -196,6 +258,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sweeps", type=int, default=2)
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed-precision and DF-P side measurements")
+    ap.add_argument("--dfp-sizes", type=float, nargs="*", default=[1e-7, 1e-5, 1e-3])
+    ap.add_argument("--dfp-batches", type=int, default=3)
     ap.add_argument("--profile-run", action="store_true",
                     help="build the graph and run one solve capped at --max-iter sweeps (for ncu captures)")
     ap.add_argument("--max-iter", type=int, default=500)
@@ -286,6 +351,10 @@ def main():
     peak, peak_kind = measured_peaks()
     traffic = recorded_traffic()
 
+    extras = {}
+    if not args.no_extras:
+        extras["fp32_refined"] = measure_mixed(g, R, m, args)
+
     # end to end through the public API with host buffers: H2D edge list, graph build, solve, D2H ranks
     h_R = torch.empty(n, dtype=torch.float64).pin_memory()
     e2e_ms = []
@@ -311,6 +380,9 @@ def main():
         e2e_step = float(t.item())
     e2e_val = world * st2.iterations * m / (e2e_step * 1e-3) / 1e9
 
+    if not args.no_extras and args.dfp_sizes:
+        extras["dfp"] = measure_dfp(g, n, m, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n, src, dst, m, args.cpu_seconds)
@@ -335,6 +407,7 @@ def main():
             "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 8 * m0, "d2h_bytes_per_step": 8 * n,
                     "ms_per_step": e2e_step},
             "gpu_launches": int(sum(s.kernel_launches for s in sts)),
+            "extras": extras,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

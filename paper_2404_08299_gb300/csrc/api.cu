@@ -54,6 +54,24 @@ __global__ void k_init_x(const double* __restrict__ R0, const int32_t* __restric
   }
 }
 
+// FP32 stage set-up: y[i] = R0[perm[i]] / |out| (R0 = NULL: 1/n) and FP32 degrees
+__global__ void k_init_y(const double* __restrict__ R0, const int32_t* __restrict__ perm, int32_t n,
+                         const double* __restrict__ deg, const double* __restrict__ inv, float* __restrict__ y,
+                         float* __restrict__ degf, float* __restrict__ invf) {
+  const double r = 1.0 / (double)n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    y[i] = (float)((R0 ? R0[perm[i]] : r) * inv[i]);
+    degf[i] = (float)deg[i];
+    invf[i] = (float)inv[i];
+  }
+}
+
+// FP64 stage start: x = y (exact widening)
+__global__ void k_widen(const float* __restrict__ y, int32_t n, double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (double)y[i];
+}
+
 // R[perm[i]] = x[i] * |out(perm[i])|; dV_out[perm[i]] = dV[i]
 __global__ void k_finalize(const double* __restrict__ x, const double* __restrict__ deg,
                            const int32_t* __restrict__ perm, int32_t n, double* __restrict__ R,
@@ -352,6 +370,68 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
   return PRDF_OK;
 }
 
+// FP32 stage: sweeps until max|dR| <= tol_fp32_rel * max R or max_iter sweeps.
+// Returns the sweeps run and which y buffer holds the result.
+int iterate32(prdf_graph* g, const prdf_params* p, int* iters, int* final_buf, long long* kernels, cudaStream_t s) {
+  const int max_iter = p->max_iter;
+  PRDF_TRY(g->resid32.reserve(2 * ((size_t)max_iter + 1), s));
+  PRDF_CUDA(cudaMemsetAsync(g->resid32.p, 0, sizeof(uint32_t) * 2 * ((size_t)max_iter + 1), s));
+  const Relabel& rl = g->rl;
+  int64_t cb[kMaxThr + 2];
+  const int nci = rl.thr.n + 1;
+  begins_from_counts(rl.count, nci, cb);
+  Sweep32Args a;
+  memset(&a, 0, sizeof(a));
+  a.off = rl.in.off.p;
+  a.adj = rl.in.adj.p;
+  a.degf = g->degf.p;
+  a.invf = g->invf.p;
+  a.alpha = (float)p->alpha;
+  a.c0 = (float)((1.0 - p->alpha) / (double)g->n);
+  a.self_loops = g->self_loops ? 1 : 0;
+  a.tol_rel = (float)p->tol_fp32_rel;
+  const int check = p->check_every > 0 ? p->check_every : 8;
+  int launched = 0;
+  bool done = false;
+  while (launched < max_iter && !done) {
+    const int upto = (launched + check < max_iter) ? launched + check : max_iter;
+    for (int i = launched; i < upto; ++i) {
+      a.y = (i & 1) ? g->yb.p : g->ya.p;
+      a.yn = (i & 1) ? g->ya.p : g->yb.p;
+      a.resid = g->resid32.p + 2 * i;
+      a.prev = i > 0 ? g->resid32.p + 2 * (i - 1) : nullptr;
+      PRDF_TRY(launch_sweep32(a, rl.thr, cb, s));
+    }
+    launched = upto;
+    PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid32.p + 2 * (launched - 1), 2 * sizeof(uint32_t),
+                              cudaMemcpyDeviceToHost, s));
+    PRDF_CUDA(cudaStreamSynchronize(s));
+    uint32_t hb[2];
+    memcpy(hb, g->ws.host_i64, sizeof(hb));
+    float d, r;
+    memcpy(&d, &hb[0], 4);
+    memcpy(&r, &hb[1], 4);
+    done = d <= (float)p->tol_fp32_rel * r;
+  }
+  std::vector<uint32_t> hr(2 * (size_t)launched);
+  PRDF_CUDA(cudaMemcpyAsync(hr.data(), g->resid32.p, sizeof(uint32_t) * 2 * launched, cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  int k = launched - 1;
+  for (int i = 0; i < launched; ++i) {
+    float d, r;
+    memcpy(&d, &hr[2 * i], 4);
+    memcpy(&r, &hr[2 * i + 1], 4);
+    if (d <= (float)p->tol_fp32_rel * r) {
+      k = i;
+      break;
+    }
+  }
+  *iters = k + 1;
+  *final_buf = (k & 1) ? 0 : 1;
+  *kernels = (long long)launched * nonempty_classes(cb, nci);
+  return PRDF_OK;
+}
+
 int alloc_solver(prdf_graph* g, bool dynamic, cudaStream_t s) {
   PRDF_TRY(g->xa.reserve(g->n, s));
   PRDF_TRY(g->xb.reserve(g->n, s));
@@ -613,11 +693,32 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
   // the in-degree partition is the class-contiguous numbering, built with the
   // graph and rebuilt here only if the thresholds changed
   PRDF_TRY(ensure_relabelled(g, false, s));
-  k_init_x<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(R0, g->rl.perm.p, g->n, g->rl.inv_deg.p, g->xa.p, nullptr);
-  PRDF_LAUNCH_CHECK();
-  PRDF_CUDA(cudaEventRecord(t.e[1], s));
+  int iters32 = 0;
+  long long kernels32 = 0;
+  prdf_params p64 = *p;
+  if (p->precision == PRDF_FP32_REFINE) {
+    // FP32 stage, then FP64 sweeps from its result
+    PRDF_TRY(g->ya.reserve(g->n, s));
+    PRDF_TRY(g->yb.reserve(g->n, s));
+    PRDF_TRY(g->degf.reserve(g->n, s));
+    PRDF_TRY(g->invf.reserve(g->n, s));
+    k_init_y<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(R0, g->rl.perm.p, g->n, g->rl.degd.p, g->rl.inv_deg.p,
+                                                           g->ya.p, g->degf.p, g->invf.p);
+    PRDF_LAUNCH_CHECK();
+    PRDF_CUDA(cudaEventRecord(t.e[1], s));
+    int fb32 = 0;
+    PRDF_TRY(iterate32(g, p, &iters32, &fb32, &kernels32, s));
+    k_widen<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(fb32 ? g->yb.p : g->ya.p, g->n, g->xa.p);
+    PRDF_LAUNCH_CHECK();
+    p64.max_iter = p->max_iter - iters32 > 0 ? p->max_iter - iters32 : 1;
+    kernels32 += 2;
+  } else {
+    k_init_x<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(R0, g->rl.perm.p, g->n, g->rl.inv_deg.p, g->xa.p, nullptr);
+    PRDF_LAUNCH_CHECK();
+    PRDF_CUDA(cudaEventRecord(t.e[1], s));
+  }
   IterResult it;
-  PRDF_TRY(iterate(g, p, false, &it, s));
+  PRDF_TRY(iterate(g, &p64, false, &it, s));
   k_finalize<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, g->rl.degd.p,
                                                            g->rl.perm.p, g->n, ranks, nullptr, nullptr);
   PRDF_LAUNCH_CHECK();
@@ -625,7 +726,8 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
   PRDF_CUDA(cudaEventSynchronize(t.e[2]));
   if (stats) {
     memset(stats, 0, sizeof(*stats));
-    stats->iterations = it.iters;
+    stats->iterations = it.iters + iters32;
+    stats->iterations_fp32 = iters32;
     stats->converged = it.converged;
     stats->final_delta = it.final_delta;
     stats->sweeps_launched = it.launched;
@@ -633,9 +735,9 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
     cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
     cudaEventElapsedTime(&stats->ms_iterate, t.e[1], t.e[2]);
     stats->ms_sweep = it.ms_sweep;
-    stats->edges_processed = (long long)it.iters * g->csr[PRDF_IN].m;
+    stats->edges_processed = (long long)(it.iters + iters32) * g->csr[PRDF_IN].m;
     // init + sweeps + finalize
-    stats->kernel_launches = 1 + it.kernels + 1;
+    stats->kernel_launches = 1 + kernels32 + it.kernels + 1;
   }
   return PRDF_OK;
 }

@@ -2,7 +2,7 @@
 // initialAffected over the batch, expandAffected over the out-degree
 // partition of G with thread-, sub-warp-, warp- and block-per-vertex
 // kernels. Flags are uint8; every store writes 1, so concurrent marks of the
-// same vertex need no atomics.
+// same vertex need no atomics, and a flag already set is not stored again.
 #include "internal.cuh"
 
 namespace prdf {
@@ -48,7 +48,10 @@ __global__ void __launch_bounds__(kThreads) k_expand_group(const int64_t* __rest
     const int32_t u = P[i];
     if (!dN[u]) continue;
     const int64_t b = off[u], e = off[u + 1];
-    for (int64_t j = b + lane; j < e; j += G) dV[adj[j]] = 1;
+    for (int64_t j = b + lane; j < e; j += G) {
+      const int32_t w = adj[j];
+      if (!dV[w]) dV[w] = 1;  // most targets are already marked when the frontier is large
+    }
   }
 }
 
@@ -62,7 +65,10 @@ __global__ void __launch_bounds__(kThreads) k_expand_block(const int64_t* __rest
     const int32_t u = P[i];
     if (!dN[u]) continue;
     const int64_t b = off[u], e = off[u + 1];
-    for (int64_t j = b + threadIdx.x; j < e; j += kThreads) dV[adj[j]] = 1;
+    for (int64_t j = b + threadIdx.x; j < e; j += kThreads) {
+      const int32_t w = adj[j];
+      if (!dV[w]) dV[w] = 1;
+    }
   }
 }
 

@@ -82,6 +82,22 @@ struct SweepArgs {
   int prune;               // DF-P (Eq. 2, prune) or DF (Eq. 1)
 };
 
+// FP32 stage of the mixed-precision Static sweep (sweep32.cu).
+struct Sweep32Args {
+  const int64_t* off;      // in-CSR offsets of G' (class-contiguous numbering)
+  const int32_t* adj;      // in-CSR sources
+  const float* y;          // y[u] = R[u] / |out(u)| in FP32
+  float* yn;               // next y
+  const float* degf;       // |out(v)| as float
+  const float* invf;       // 1 / |out(v)| as float
+  float alpha, c0;
+  int self_loops;
+  uint32_t* resid;         // [0]: max |r - R[v]|, [1]: max r of this sweep (FP32 bits, atomic max)
+  const uint32_t* prev;    // previous sweep's pair, or null
+  float tol_rel;           // the sweep exits at once if prev[0] <= tol_rel * prev[1]
+};
+int launch_sweep32(const Sweep32Args& a, const PartThr& t, const int64_t* class_begin, cudaStream_t s);
+
 // Launch one rank sweep (all degree classes) for Static (dynamic = false) or DF/DF-P.
 int launch_sweep(const SweepArgs& a, const PartThr& t, const int64_t* class_begin, bool exact, bool dynamic,
                  cudaStream_t s);
@@ -113,6 +129,8 @@ struct prdf_graph {
   prdf::Workspace ws;
   // solver scratch
   prdf::DBuf<double> xa, xb;
+  prdf::DBuf<float> ya, yb, degf, invf;  // FP32 stage state and degrees (class-contiguous numbering)
+  prdf::DBuf<uint32_t> resid32;
   prdf::DBuf<uint64_t> resid;
   prdf::DBuf<uint8_t> dV, dN, wrote;
   prdf::DBuf<unsigned long long> counter;

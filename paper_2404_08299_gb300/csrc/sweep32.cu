@@ -1,0 +1,315 @@
+// FP32 stage of the mixed-precision Static PageRank (an extension of the
+// paper's Alg. static / Eq. 1): rank state y = R / |out| stored in FP32, so a
+// sweep gathers 4 bytes per in-edge, and in-neighbour sums accumulated with
+// compensated summation (Kahan-Babuska: TwoSum of every term, errors summed
+// separately) on the FP32 pipes. Each sweep reports max |r - R[v]| and
+// max r as FP32 bit patterns; the host stops the stage when
+// max|dR| <= tol_fp32_rel * max R and continues in FP64 (api.cu).
+// Same class-contiguous numbering and kernel shapes as the FP64 sweep.
+#include "internal.cuh"
+
+namespace prdf {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// compensated FP32 sum: value = s + e
+struct Kahan {
+  float s = 0.f, e = 0.f;
+  __device__ __forceinline__ void add(float y) {
+    const float t = s + y;
+    const float bp = t - s;
+    e += (s - (t - bp)) + (y - bp);
+    s = t;
+  }
+  __device__ __forceinline__ void merge(float s2, float e2) {
+    add(s2);
+    e += e2;
+  }
+  template <int G>
+  __device__ __forceinline__ void group_reduce() {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
+      merge(s2, e2);
+    }
+  }
+  __device__ __forceinline__ float value() const { return s + e; }
+};
+
+__device__ __forceinline__ uint32_t ld_gather_b32(const float* p, uint64_t pol) {
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_stream_f32(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+template <int G, int U>
+__device__ __forceinline__ void gather32(const Sweep32Args& a, int64_t b, int64_t e, int lane, int32_t v, Kahan& acc,
+                                         uint32_t& yself, uint64_t pf, uint64_t pl) {
+  for (int64_t j0 = b + lane; j0 < e; j0 += (int64_t)G * U) {
+    int32_t u[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t j = j0 + (int64_t)k * G;
+      u[k] = j < e ? ld_stream_i32(a.adj + j, pf) : -1;
+    }
+    uint32_t yv[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) yv[k] = u[k] >= 0 ? ld_gather_b32(a.y + u[k], pl) : 0u;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (u[k] >= 0) acc.add(__uint_as_float(yv[k]));
+      yself = (u[k] == v) ? yv[k] : yself;
+    }
+  }
+}
+
+template <int NT, int KV>
+__device__ __forceinline__ void gather32_vec(const Sweep32Args& a, int64_t b, int64_t e, int lane, int32_t v,
+                                             Kahan& acc, uint32_t& yself, uint64_t pf, uint64_t pl) {
+  int64_t ba = (b + 3) & ~(int64_t)3;
+  if (ba > e) ba = e;
+  const int64_t ea = ba + ((e - ba) & ~(int64_t)3);
+  {
+    const int64_t nh = ba - b, nt = e - ea;
+    int64_t j = -1;
+    if (lane < nh) j = b + lane;
+    else if (lane >= 4 && lane < 4 + nt) j = ea + (lane - 4);
+    if (j >= 0) {
+      const int32_t u = ld_stream_i32(a.adj + j, pf);
+      const uint32_t yv = ld_gather_b32(a.y + u, pl);
+      acc.add(__uint_as_float(yv));
+      yself = (u == v) ? yv : yself;
+    }
+  }
+  for (int64_t q0 = ba + 4 * (int64_t)lane; q0 < ea; q0 += 4 * (int64_t)NT * KV) {
+    int4 u4[KV];
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      const int64_t q = q0 + 4 * (int64_t)NT * k;
+      u4[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
+    }
+    uint32_t yv[4 * KV];
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      yv[4 * k + 0] = u4[k].x >= 0 ? ld_gather_b32(a.y + u4[k].x, pl) : 0u;
+      yv[4 * k + 1] = u4[k].y >= 0 ? ld_gather_b32(a.y + u4[k].y, pl) : 0u;
+      yv[4 * k + 2] = u4[k].z >= 0 ? ld_gather_b32(a.y + u4[k].z, pl) : 0u;
+      yv[4 * k + 3] = u4[k].w >= 0 ? ld_gather_b32(a.y + u4[k].w, pl) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      if (u4[k].x < 0) continue;
+      acc.add(__uint_as_float(yv[4 * k + 0]));
+      acc.add(__uint_as_float(yv[4 * k + 1]));
+      acc.add(__uint_as_float(yv[4 * k + 2]));
+      acc.add(__uint_as_float(yv[4 * k + 3]));
+      yself = (u4[k].x == v) ? yv[4 * k + 0] : yself;
+      yself = (u4[k].y == v) ? yv[4 * k + 1] : yself;
+      yself = (u4[k].z == v) ? yv[4 * k + 2] : yself;
+      yself = (u4[k].w == v) ? yv[4 * k + 3] : yself;
+    }
+  }
+}
+
+// Eq. 1 in FP32; returns |r - R[v]| and r (both non-negative) as bit patterns
+__device__ __forceinline__ void finish32(const Sweep32Args& a, int32_t v, float c, uint32_t yself_b, uint64_t pf,
+                                        uint32_t& db, uint32_t& rb) {
+  const float d = ld_stream_f32(a.degf + v, pf);
+  const float rold = __uint_as_float(yself_b) * d;
+  const float r = fmaf(a.alpha, c, a.c0);
+  a.yn[v] = r * ld_stream_f32(a.invf + v, pf);
+  db = __float_as_uint(fabsf(r - rold));
+  rb = __float_as_uint(r);
+}
+
+__device__ __forceinline__ bool converged32(const Sweep32Args& a) {
+  if (!a.prev) return false;
+  const float d = __uint_as_float(a.prev[0]), rm = __uint_as_float(a.prev[1]);
+  return d <= a.tol_rel * rm;
+}
+
+__device__ __forceinline__ void block_max2_to(uint32_t dmax, uint32_t rmax, uint32_t* out) {
+  __shared__ uint32_t sd[32], sr[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sd[wid] = dmax;
+    sr[wid] = rmax;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t x = lane < (int)(blockDim.x >> 5) ? sd[lane] : 0u;
+    uint32_t y = lane < (int)(blockDim.x >> 5) ? sr[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+      y = max(y, __shfl_xor_sync(0xffffffffu, y, o));
+    }
+    if (lane == 0) {
+      if (x) atomicMax(out, x);
+      if (y) atomicMax(out + 1, y);
+    }
+  }
+}
+
+template <int G, int U, bool SELF1>
+__global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a, int64_t begin, int64_t end) {
+  if (converged32(a)) return;
+  const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
+  constexpr int kGroupsPerWarp = 32 / G;
+  const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
+  const int gw = (threadIdx.x & 31) / G;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  uint32_t dmax = 0, rmax = 0;
+  for (int64_t base = begin + warp * kGroupsPerWarp; base < end; base += nwarps * kGroupsPerWarp) {
+    const int64_t i = base + gw;
+    const bool active = i < end;
+    const int32_t v = (int32_t)i;
+    Kahan acc;
+    uint32_t yself = 0;
+    if (active) {
+      if (SELF1) {
+        yself = lane == 0 ? ld_gather_b32(a.y + v, pl) : 0u;
+        if (lane == 0) acc.add(__uint_as_float(yself));
+      } else {
+        const int64_t b = ld_stream_i64(a.off + v, pf), e = ld_stream_i64(a.off + v + 1, pf);
+        gather32<G, U>(a, b, e, lane, v, acc, yself, pf, pl);
+      }
+    }
+    if (G > 1) {
+      acc.template group_reduce<G>();
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) yself = max(yself, __shfl_xor_sync(0xffffffffu, yself, o));
+    }
+    if (active && lane == 0) {
+      uint32_t db, rb;
+      finish32(a, v, acc.value(), yself, pf, db, rb);
+      dmax = max(dmax, db);
+      rmax = max(rmax, rb);
+    }
+  }
+  block_max2_to(dmax, rmax, a.resid);
+}
+
+template <int KV>
+__global__ void __launch_bounds__(kThreads) k_sweep32_warp(const Sweep32Args a, int64_t begin, int64_t end) {
+  if (converged32(a)) return;
+  const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  uint32_t dmax = 0, rmax = 0;
+  for (int64_t i = begin + warp; i < end; i += nwarps) {
+    const int32_t v = (int32_t)i;
+    const int64_t b = ld_stream_i64(a.off + v, pf), e = ld_stream_i64(a.off + v + 1, pf);
+    Kahan acc;
+    uint32_t yself = 0;
+    gather32_vec<32, KV>(a, b, e, lane, v, acc, yself, pf, pl);
+    acc.template group_reduce<32>();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) yself = max(yself, __shfl_xor_sync(0xffffffffu, yself, o));
+    if (lane == 0) {
+      uint32_t db, rb;
+      finish32(a, v, acc.value(), yself, pf, db, rb);
+      dmax = max(dmax, db);
+      rmax = max(rmax, rb);
+    }
+  }
+  block_max2_to(dmax, rmax, a.resid);
+}
+
+template <int KV>
+__global__ void __launch_bounds__(kThreads) k_sweep32_block(const Sweep32Args a, int64_t begin, int64_t end) {
+  if (converged32(a)) return;
+  const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
+  __shared__ float s_s[kThreads / 32], s_e[kThreads / 32];
+  __shared__ uint32_t s_y[kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t dmax = 0, rmax = 0;
+  for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
+    const int32_t v = (int32_t)i;
+    const int64_t b = a.off[v], e = a.off[v + 1];
+    Kahan acc;
+    uint32_t yself = 0;
+    gather32_vec<kThreads, KV>(a, b, e, threadIdx.x, v, acc, yself, pf, pl);
+    acc.template group_reduce<32>();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) yself = max(yself, __shfl_xor_sync(0xffffffffu, yself, o));
+    if (lane == 0) {
+      s_s[wid] = acc.s;
+      s_e[wid] = acc.e;
+      s_y[wid] = yself;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Kahan tot;
+      uint32_t ym = 0;
+      for (int k = 0; k < kThreads / 32; ++k) {
+        tot.merge(s_s[k], s_e[k]);
+        ym = max(ym, s_y[k]);
+      }
+      uint32_t db, rb;
+      finish32(a, v, tot.value(), ym, pf, db, rb);
+      dmax = max(dmax, db);
+      rmax = max(rmax, rb);
+    }
+    __syncthreads();
+  }
+  block_max2_to(dmax, rmax, a.resid);
+}
+
+enum Kind32 { kT1 = 0, kT4, kG4, kG16, kWarp, kBlock };
+
+Kind32 class_kind32(const PartThr& t, int c) {
+  const int C = t.n + 1;
+  if (c == C - 1) return kBlock;
+  if (c == C - 2 && C >= 3) return kWarp;
+  const int64_t hi = t.thr[c];
+  if (hi <= 1) return kT1;
+  if (hi <= 4) return kT4;
+  if (hi <= 16) return kG4;
+  if (hi <= 128) return kG16;
+  return kWarp;
+}
+
+}  // namespace
+
+int launch_sweep32(const Sweep32Args& a, const PartThr& t, const int64_t* cb, cudaStream_t s) {
+  const int maxg = kSMs * 8;
+  const int C = t.n + 1;
+  for (int c = 0; c < C; ++c) {
+    const int64_t b = cb[c], e = cb[c + 1];
+    if (e <= b) continue;
+    const int64_t cnt = e - b;
+    const Kind32 kind = class_kind32(t, c);
+    const bool self1 = a.self_loops && kind == kT1 && t.thr[c] <= 1;
+    switch (kind) {
+      case kT1:
+        if (self1) k_sweep32_group<1, 1, true><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
+        else k_sweep32_group<1, 1, false><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
+        break;
+      case kT4: k_sweep32_group<1, 4, false><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG4: k_sweep32_group<4, 4, false><<<grid_for(cnt * 4, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG16: k_sweep32_group<16, 8, false><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kWarp: k_sweep32_warp<2><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      default: k_sweep32_block<4><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e); break;
+    }
+  }
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+}  // namespace prdf
