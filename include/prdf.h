@@ -79,6 +79,7 @@ typedef struct {
   int prune;           /* DF-P (1, default) or DF (0), for prdf_pagerank_dfp */
   int check_every;     /* sweeps launched between host convergence checks, default 8 */
   int time_sweeps;     /* 1: time every rank sweep with CUDA events (stats->ms_sweep), default 0 */
+  int tile;            /* K-column calls: columns per index fetch (8, 16, 32, 64); 0 = automatic */
   void* stream;        /* cudaStream_t for all work; NULL = legacy default stream */
 } prdf_params;
 
@@ -230,6 +231,25 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
                       int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins,
                       const double* prev_ranks, double* ranks, const prdf_params* p, uint8_t* dV_out,
                       prdf_stats* stats);
+
+/* ------------------------------------------------------ K columns ------ */
+
+/*
+ * Weighted personalised PageRank for K teleport columns at once (extension of
+ * Eq. 1 and Alg. static): R[:, c] = alpha * P^T R[:, c] + (1 - alpha) * S[:, c]
+ * with P_uv = w_uv / sum_k w_uk (the graph must have been created with
+ * weights). S, R: double [n, K] row-major device arrays in vertex-id order;
+ * the iteration starts from R = S.
+ * p->precision = PRDF_FP32_REFINE: FP32 sweeps with compensated products and
+ * sums until max|dR| <= tol_fp32_rel * max|R|, then iterative refinement: an
+ * FP64 Jacobi step gives the residual, an FP32 solve the correction, until
+ * the L-inf change of an FP64 Jacobi step is <= tol (the returned R is that
+ * step's result). p->precision = PRDF_FP64: FP64 Jacobi sweeps until the
+ * L-inf change is <= tol. p->tile: columns handled per index fetch.
+ * stats->iterations counts FP64 steps plus FP32 sweeps (iterations_fp32).
+ * Returns PRDF_ESTATE for an unweighted graph, PRDF_EINVAL for K < 1.
+ */
+int prdf_pagerank_ppr(prdf_graph* g, const double* S, int K, double* R, const prdf_params* p, prdf_stats* stats);
 
 #ifdef __cplusplus
 }

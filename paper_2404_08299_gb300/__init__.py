@@ -35,7 +35,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("tau_f", ctypes.c_double),
                 ("tau_p", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("tol_fp32_rel", ctypes.c_double), ("accumulate", ctypes.c_int), ("prune", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("time_sweeps", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("check_every", ctypes.c_int), ("time_sweeps", ctypes.c_int), ("tile", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class _Stats(ctypes.Structure):
@@ -84,6 +85,7 @@ _SIGNATURES = {
     "prdf_expand_affected": (_INT, [_P, _P, _P, _P]),
     "prdf_pagerank_static": (_INT, [_P, _P, _P, _P, _P]),
     "prdf_pagerank_dfp": (_INT, [_P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
+    "prdf_pagerank_ppr": (_INT, [_P, _P, _INT, _P, _P, _P]),
 }
 
 
@@ -259,3 +261,17 @@ class Graph:
                                        _ptr(prev_ranks, torch.float64, n, "prev_ranks"), _ptr(R), ctypes.byref(p),
                                        _ptr(dV), ctypes.byref(st)))
         return R, _stats(st), dV
+
+    def pagerank_ppr(self, S: torch.Tensor, **kw):
+        """K-column weighted personalised PageRank (prdf_pagerank_ppr). S: float64 [n, K] on the GPU.
+        Returns (R float64 [n, K], Stats)."""
+        n = self.n
+        if S.dim() != 2 or S.shape[0] != n:
+            raise ValueError("S must have shape [n, K]")
+        K = S.shape[1]
+        R = torch.empty((n, K), dtype=torch.float64, device="cuda")
+        st = _Stats()
+        p = params(**kw)
+        _check(lib().prdf_pagerank_ppr(self._h, _ptr(S, torch.float64, name="S"), K, _ptr(R), ctypes.byref(p),
+                                       ctypes.byref(st)))
+        return R, _stats(st)

@@ -72,6 +72,26 @@ __global__ void k_widen(const float* __restrict__ y, int32_t n, double* __restri
     x[i] = (double)y[i];
 }
 
+// dst[i, :] = src[perm[i], :] for [n, K] row-major matrices
+__global__ void k_rows_gather(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t n, int K,
+                              double* __restrict__ dst) {
+  const int64_t cnt = n * K;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / K, c = t - i * K;
+    dst[t] = src[(int64_t)perm[i] * K + c];
+  }
+}
+
+// dst[perm[i], :] = src[i, :]
+__global__ void k_rows_scatter(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t n, int K,
+                               double* __restrict__ dst) {
+  const int64_t cnt = n * K;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / K, c = t - i * K;
+    dst[(int64_t)perm[i] * K + c] = src[t];
+  }
+}
+
 // R[perm[i]] = x[i] * |out(perm[i])|; dV_out[perm[i]] = dV[i]
 __global__ void k_finalize(const double* __restrict__ x, const double* __restrict__ deg,
                            const int32_t* __restrict__ perm, int32_t n, double* __restrict__ R,
@@ -432,6 +452,106 @@ int iterate32(prdf_graph* g, const prdf_params* p, int* iters, int* final_buf, l
   return PRDF_OK;
 }
 
+int auto_tile(int K) { return K >= 32 ? 32 : (K > 8 ? 16 : 8); }
+
+int64_t hub_begin(const Relabel& rl) {
+  const int C = rl.thr.n + 1;
+  int64_t cb[kMaxThr + 2];
+  begins_from_counts(rl.count, C, cb);
+  return C >= 3 ? cb[C - 2] : cb[C - 1];
+}
+
+// FP32 K-column solve of R = alpha P^T R + (1 - alpha) rhs from the start held
+// in *cur; on return *cur holds the result (the other buffer is scratch).
+int ppr32_solve(prdf_graph* g, const prdf_params* p, int K, int tile, const float* rhs, float** cur, float** other,
+                int max_iter, int* iters, long long* kernels, cudaStream_t s) {
+  PRDF_TRY(g->resid32.reserve(2 * ((size_t)max_iter + 1), s));
+  PRDF_CUDA(cudaMemsetAsync(g->resid32.p, 0, sizeof(uint32_t) * 2 * ((size_t)max_iter + 1), s));
+  const Relabel& rl = g->rl;
+  Ppr32Args a;
+  memset(&a, 0, sizeof(a));
+  a.off = rl.in.off.p;
+  a.adj = rl.in.adj.p;
+  a.P = g->pin32.p;
+  a.S = rhs;
+  a.K = K;
+  a.alpha = (float)p->alpha;
+  a.beta = (float)(1.0 - p->alpha);
+  a.tol_rel = (float)p->tol_fp32_rel;
+  const int64_t hb = hub_begin(rl);
+  const int check = p->check_every > 0 ? p->check_every : 8;
+  float* buf[2] = {*cur, *other};
+  int launched = 0;
+  bool done = false;
+  while (launched < max_iter && !done) {
+    const int upto = (launched + check < max_iter) ? launched + check : max_iter;
+    for (int i = launched; i < upto; ++i) {
+      a.R = buf[i & 1];
+      a.Rn = buf[(i + 1) & 1];
+      a.resid = g->resid32.p + 2 * i;
+      a.prev = i > 0 ? g->resid32.p + 2 * (i - 1) : nullptr;
+      PRDF_TRY(launch_ppr32_sweep(a, tile, g->n, hb, s));
+    }
+    launched = upto;
+    PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid32.p + 2 * (launched - 1), 2 * sizeof(uint32_t),
+                              cudaMemcpyDeviceToHost, s));
+    PRDF_CUDA(cudaStreamSynchronize(s));
+    uint32_t h[2];
+    memcpy(h, g->ws.host_i64, sizeof(h));
+    float d, r;
+    memcpy(&d, &h[0], 4);
+    memcpy(&r, &h[1], 4);
+    done = d <= (float)p->tol_fp32_rel * r;
+  }
+  std::vector<uint32_t> hr(2 * (size_t)launched);
+  PRDF_CUDA(cudaMemcpyAsync(hr.data(), g->resid32.p, sizeof(uint32_t) * 2 * launched, cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  int k = launched - 1;
+  for (int i = 0; i < launched; ++i) {
+    float d, r;
+    memcpy(&d, &hr[2 * i], 4);
+    memcpy(&r, &hr[2 * i + 1], 4);
+    if (d <= (float)p->tol_fp32_rel * r) {
+      k = i;
+      break;
+    }
+  }
+  *iters = k + 1;
+  *cur = buf[(k + 1) & 1];
+  *other = buf[k & 1];
+  const int tiles = (K + tile - 1) / tile;
+  *kernels += (long long)launched * tiles * 2;
+  return PRDF_OK;
+}
+
+// one FP64 Jacobi step Rn = T(R); returns max |T(R) - R|
+int ppr64_step(prdf_graph* g, const prdf_params* p, int K, int tile, const double* R, double* Rn, float* res32,
+               double* dmax, long long* kernels, cudaStream_t s) {
+  PRDF_TRY(g->resid.reserve(2, s));
+  PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t), s));
+  const Relabel& rl = g->rl;
+  Ppr64Args a;
+  memset(&a, 0, sizeof(a));
+  a.off = rl.in.off.p;
+  a.adj = rl.in.adj.p;
+  a.P = g->pin64.p;
+  a.R = R;
+  a.Rn = Rn;
+  a.S = g->S64.p;
+  a.res32 = res32;
+  a.K = K;
+  a.alpha = p->alpha;
+  a.beta = 1.0 - p->alpha;
+  a.inv_beta = 1.0 / (1.0 - p->alpha);
+  a.dmax = g->resid.p;
+  PRDF_TRY(launch_ppr64_step(a, tile, g->n, hub_begin(rl), s));
+  PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  memcpy(dmax, g->ws.host_i64, sizeof(double));
+  *kernels += (long long)((K + tile - 1) / tile) * 2;
+  return PRDF_OK;
+}
+
 int alloc_solver(prdf_graph* g, bool dynamic, cudaStream_t s) {
   PRDF_TRY(g->xa.reserve(g->n, s));
   PRDF_TRY(g->xb.reserve(g->n, s));
@@ -464,6 +584,7 @@ void prdf_params_default(prdf_params* p) {
   p->prune = 1;
   p->check_every = 8;
   p->time_sweeps = 0;
+  p->tile = 0;
   p->stream = nullptr;
 }
 
@@ -805,6 +926,112 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
     // out-degree partition + init + initial marking + expand + count + sweeps/expands + finalize
     stats->kernel_launches = 5 + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, g->thr[PRDF_OUT].n + 1) + 1 +
                              it.kernels + 1;
+  }
+  return PRDF_OK;
+}
+
+int prdf_pagerank_ppr(prdf_graph* g, const double* S, int K, double* R, const prdf_params* p, prdf_stats* stats) {
+  if (!g || !S || !R) {
+    set_error("prdf_pagerank_ppr: bad arguments");
+    return PRDF_EINVAL;
+  }
+  if (K < 1) {
+    set_error("prdf_pagerank_ppr: K must be >= 1");
+    return PRDF_EINVAL;
+  }
+  if (!g->weighted) {
+    set_error("prdf_pagerank_ppr: the graph has no edge weights");
+    return PRDF_ESTATE;
+  }
+  PRDF_TRY(check_params(p));
+  if (p->tile != 0 && p->tile != 8 && p->tile != 16 && p->tile != 32 && p->tile != 64) {
+    set_error("prdf_pagerank_ppr: tile must be 0, 8, 16, 32 or 64");
+    return PRDF_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)p->stream;
+  Timer t;
+  PRDF_TRY(t.init());
+  PRDF_CUDA(cudaEventRecord(t.e[0], s));
+  PRDF_TRY(ensure_relabelled(g, false, s));
+  if (!g->ppr_valid) PRDF_TRY(build_ppr_weights(g, s));
+  const int tile = p->tile ? p->tile : auto_tile(K);
+  const int64_t cnt = (int64_t)g->n * K;
+  PRDF_TRY(g->S64.reserve(cnt, s));
+  PRDF_TRY(g->R64a.reserve(cnt, s));
+  PRDF_TRY(g->R64b.reserve(cnt, s));
+  k_rows_gather<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(S, g->rl.perm.p, g->n, K, g->S64.p);
+  PRDF_LAUNCH_CHECK();
+  long long kernels = 1;
+  int iters32 = 0, steps64 = 0, conv = 0;
+  double dmax = 0;
+  double* Rfinal = nullptr;
+  PRDF_CUDA(cudaEventRecord(t.e[1], s));
+  if (p->precision == PRDF_FP64) {
+    // plain FP64 Jacobi from R = S
+    PRDF_CUDA(cudaMemcpyAsync(g->R64a.p, g->S64.p, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s));
+    double* a = g->R64a.p;
+    double* b = g->R64b.p;
+    for (int it = 0; it < p->max_iter; ++it) {
+      PRDF_TRY(ppr64_step(g, p, K, tile, a, b, nullptr, &dmax, &kernels, s));
+      ++steps64;
+      double* tmp = a;
+      a = b;
+      b = tmp;
+      if (dmax <= p->tol) {
+        conv = 1;
+        break;
+      }
+    }
+    Rfinal = a;
+  } else {
+    PRDF_TRY(g->S32.reserve(cnt, s));
+    PRDF_TRY(g->R32a.reserve(cnt, s));
+    PRDF_TRY(g->R32b.reserve(cnt, s));
+    PRDF_TRY(ppr_narrow(g->S64.p, cnt, g->S32.p, s));
+    PRDF_CUDA(cudaMemcpyAsync(g->R32a.p, g->S32.p, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s));
+    float* cur = g->R32a.p;
+    float* oth = g->R32b.p;
+    int it32 = 0;
+    PRDF_TRY(ppr32_solve(g, p, K, tile, g->S32.p, &cur, &oth, p->max_iter, &it32, &kernels, s));
+    iters32 += it32;
+    PRDF_TRY(ppr_widen(cur, cnt, g->R64a.p, s));
+    kernels += 2;
+    // iterative refinement: residual in FP64, correction in FP32
+    const int kRounds = 8;
+    for (int round = 0; round < kRounds; ++round) {
+      PRDF_TRY(ppr64_step(g, p, K, tile, g->R64a.p, g->R64b.p, g->S32.p, &dmax, &kernels, s));
+      ++steps64;
+      if (dmax <= p->tol) {
+        conv = 1;
+        break;
+      }
+      // E = alpha P^T E + (1 - alpha) * res / (1 - alpha), started from the right-hand side
+      PRDF_CUDA(cudaMemcpyAsync(g->R32a.p, g->S32.p, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s));
+      cur = g->R32a.p;
+      oth = g->R32b.p;
+      PRDF_TRY(ppr32_solve(g, p, K, tile, g->S32.p, &cur, &oth, p->max_iter, &it32, &kernels, s));
+      iters32 += it32;
+      PRDF_TRY(ppr_add_correction(g->R64a.p, cur, cnt, s));
+      kernels += 1;
+    }
+    Rfinal = g->R64b.p;  // T(R) of the last step
+  }
+  k_rows_scatter<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(Rfinal, g->rl.perm.p, g->n, K, R);
+  PRDF_LAUNCH_CHECK();
+  kernels += 1;
+  PRDF_CUDA(cudaEventRecord(t.e[2], s));
+  PRDF_CUDA(cudaEventSynchronize(t.e[2]));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations = steps64 + iters32;
+    stats->iterations_fp32 = iters32;
+    stats->converged = conv;
+    stats->final_delta = dmax;
+    cudaEventElapsedTime(&stats->ms_total, t.e[0], t.e[2]);
+    cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
+    cudaEventElapsedTime(&stats->ms_iterate, t.e[1], t.e[2]);
+    stats->edges_processed = (long long)(steps64 + iters32) * g->rl.in.m * K;
+    stats->kernel_launches = kernels;
   }
   return PRDF_OK;
 }

@@ -98,6 +98,38 @@ struct Sweep32Args {
 };
 int launch_sweep32(const Sweep32Args& a, const PartThr& t, const int64_t* class_begin, cudaStream_t s);
 
+// K-column personalised PageRank (ppr.cu), row-major [n, K] in the class-contiguous numbering.
+struct Ppr32Args {
+  const int64_t* off;      // in-CSR of G'
+  const int32_t* adj;
+  const float* P;          // P_uv for the in-edge slot (u -> v)
+  const float* R;          // current [n, K]
+  float* Rn;               // next [n, K]
+  const float* S;          // right-hand side [n, K] (teleport, or residual / (1 - alpha))
+  int K;
+  float alpha, beta;       // alpha, 1 - alpha
+  uint32_t* resid;         // [0] max |R_new - R|, [1] max |R_new| (FP32 bits, atomic max)
+  const uint32_t* prev;    // previous sweep's pair or null
+  float tol_rel;
+};
+struct Ppr64Args {
+  const int64_t* off;
+  const int32_t* adj;
+  const double* P;
+  const double* R;
+  double* Rn;              // T(R)
+  const double* S;
+  float* res32;            // (T(R) - R) / (1 - alpha) in FP32, or null
+  int K;
+  double alpha, beta, inv_beta;
+  uint64_t* dmax;          // max |T(R) - R| (FP64 bits, atomic max)
+};
+int launch_ppr32_sweep(const Ppr32Args& a, int tile, int64_t n, int64_t hub_begin, cudaStream_t s);
+int launch_ppr64_step(const Ppr64Args& a, int tile, int64_t n, int64_t hub_begin, cudaStream_t s);
+int ppr_add_correction(double* R, const float* E, int64_t cnt, cudaStream_t s);
+int ppr_narrow(const double* x, int64_t cnt, float* y, cudaStream_t s);
+int ppr_widen(const float* y, int64_t cnt, double* x, cudaStream_t s);
+
 // Launch one rank sweep (all degree classes) for Static (dynamic = false) or DF/DF-P.
 int launch_sweep(const SweepArgs& a, const PartThr& t, const int64_t* class_begin, bool exact, bool dynamic,
                  cudaStream_t s);
@@ -135,8 +167,19 @@ struct prdf_graph {
   prdf::DBuf<uint8_t> dV, dN, wrote;
   prdf::DBuf<unsigned long long> counter;
   prdf::Relabel rl;                  // class-contiguous copy used by the sweeps
+  // weighted graphs: transition probabilities P_uv = w_uv / sum_k w_uk
+  bool ppr_valid = false;
+  prdf::DBuf<double> wsum;           // sum of out-weights per vertex (original ids)
+  prdf::DBuf<double> pin64;          // P on the in-edge slots of rl.in
+  prdf::DBuf<float> pin32;
+  prdf::DBuf<double> pout64;         // P on the out-edge slots of rl.out (adjoint)
+  prdf::DBuf<float> pout32;
+  // K-column scratch
+  prdf::DBuf<double> S64, R64a, R64b;
+  prdf::DBuf<float> S32, R32a, R32b;
 };
 
 namespace prdf {
 int build_relabelled(prdf_graph* g, cudaStream_t s);
+int build_ppr_weights(prdf_graph* g, cudaStream_t s);
 }

@@ -29,17 +29,63 @@ __global__ void k_perm_rowlen(const int64_t* __restrict__ off, const int32_t* __
   }
 }
 
-// new row i = old row perm[i], neighbour ids mapped through inv; one warp per row
+// new row i = old row perm[i], neighbour ids mapped through inv (weights
+// carried along when present); one warp per row
 __global__ void k_perm_rows(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                            const int32_t* __restrict__ perm, const int32_t* __restrict__ inv, int32_t n,
-                            const int64_t* __restrict__ noff, int32_t* __restrict__ nadj) {
+                            const float* __restrict__ w, const int32_t* __restrict__ perm,
+                            const int32_t* __restrict__ inv, int32_t n, const int64_t* __restrict__ noff,
+                            int32_t* __restrict__ nadj, float* __restrict__ nw) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp; i < n; i += nw) {
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
     const int32_t v = perm[i];
     const int64_t b = off[v], L = off[v + 1] - b, o = noff[i];
-    for (int64_t j = lane; j < L; j += 32) nadj[o + j] = inv[adj[b + j]];
+    for (int64_t j = lane; j < L; j += 32) {
+      nadj[o + j] = inv[adj[b + j]];
+      if (w) nw[o + j] = w[b + j];
+    }
+  }
+}
+
+// sum of out-weights per vertex (original ids), one warp per row
+__global__ void k_row_wsum(const int64_t* __restrict__ off, const float* __restrict__ w, int32_t n,
+                           double* __restrict__ W) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    double s = 0;
+    for (int64_t j = off[v] + lane; j < off[v + 1]; j += 32) s += (double)w[j];
+    s = warp_sum_f64(s);
+    if (lane == 0) W[v] = s;
+  }
+}
+
+// P on the in-slots of the renumbered G': slot (u -> v) gets w_uv / W[u];
+// new_src holds renumbered ids, so W is read through perm
+__global__ void k_pin(const int32_t* __restrict__ new_src, const float* __restrict__ w, const int32_t* __restrict__ perm,
+                      const double* __restrict__ W, int64_t m, double* __restrict__ p64, float* __restrict__ p32) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    const double p = (double)w[j] / W[perm[new_src[j]]];
+    p64[j] = p;
+    p32[j] = (float)p;
+  }
+}
+
+// P on the out-slots of the renumbered G: row i (vertex perm[i]) divides by its own W
+__global__ void k_pout(const int64_t* __restrict__ off, const float* __restrict__ w, const int32_t* __restrict__ perm,
+                       const double* __restrict__ W, int32_t n, double* __restrict__ p64, float* __restrict__ p32) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const double Wi = W[perm[i]];
+    for (int64_t j = off[i] + lane; j < off[i + 1]; j += 32) {
+      const double p = (double)w[j] / Wi;
+      p64[j] = p;
+      p32[j] = (float)p;
+    }
   }
 }
 
@@ -63,8 +109,10 @@ int permute_csr(const Csr& src, const int32_t* perm, const int32_t* inv, int32_t
   PRDF_TRY(exclusive_scan_i64(len.p, n, dst.off.p, ws, s));
   dst.m = src.m;
   PRDF_TRY(dst.adj.alloc(src.m > 0 ? (size_t)src.m : 1, s));
-  k_perm_rows<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(src.off.p, src.adj.p, perm, inv, n, dst.off.p,
-                                                                        dst.adj.p);
+  if (src.w.p) PRDF_TRY(dst.w.alloc(src.m > 0 ? (size_t)src.m : 1, s));
+  else dst.w.release();
+  k_perm_rows<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(src.off.p, src.adj.p, src.w.p, perm, inv, n,
+                                                                        dst.off.p, dst.adj.p, dst.w.p);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }
@@ -90,6 +138,26 @@ int build_relabelled(prdf_graph* g, cudaStream_t s) {
   PRDF_LAUNCH_CHECK();
   r.valid = true;
   r.pout_valid = false;
+  g->ppr_valid = false;
+  return PRDF_OK;
+}
+
+int build_ppr_weights(prdf_graph* g, cudaStream_t s) {
+  const int32_t n = g->n;
+  const Relabel& r = g->rl;
+  const int64_t m = r.in.m;
+  PRDF_TRY(g->wsum.alloc((size_t)n, s));
+  k_row_wsum<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(g->csr[PRDF_OUT].off.p, g->csr[PRDF_OUT].w.p, n,
+                                                                       g->wsum.p);
+  PRDF_TRY(g->pin64.alloc((size_t)m, s));
+  PRDF_TRY(g->pin32.alloc((size_t)m, s));
+  PRDF_TRY(g->pout64.alloc((size_t)m, s));
+  PRDF_TRY(g->pout32.alloc((size_t)m, s));
+  k_pin<<<grid_for(m, kThreads), kThreads, 0, s>>>(r.in.adj.p, r.in.w.p, r.perm.p, g->wsum.p, m, g->pin64.p, g->pin32.p);
+  k_pout<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(r.out.off.p, r.out.w.p, r.perm.p, g->wsum.p, n,
+                                                                   g->pout64.p, g->pout32.p);
+  PRDF_LAUNCH_CHECK();
+  g->ppr_valid = true;
   return PRDF_OK;
 }
 
