@@ -251,6 +251,29 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
  */
 int prdf_pagerank_ppr(prdf_graph* g, const double* S, int K, double* R, const prdf_params* p, prdf_stats* stats);
 
+/*
+ * Replace the edge weights: w is float32[m] in the slot order of the out-CSR
+ * (prdf_graph_export_csr(PRDF_OUT)), every weight finite and > 0 (else
+ * PRDF_EINVAL). Makes an unweighted graph weighted.
+ */
+int prdf_graph_set_weights(prdf_graph* g, const float* w, void* stream);
+
+/*
+ * Adjoint of prdf_pagerank_ppr for the loss L = sum_c G[:, c] . R[:, c]
+ * (extension; gradients of the fixed point R = alpha P^T R + (1 - alpha) S):
+ *   lambda solves lambda = alpha P lambda + G, a pull over the out-edges of G
+ *   (the transposed fixed point; same solver and precision options as the
+ *   forward call);
+ *   grad_S = (1 - alpha) lambda                          (double [n, K]);
+ *   grad_w[j] for out-slot j = (u, v):
+ *     (1 / W_u) sum_c R[u, c] (alpha lambda[v, c] - lambda[u, c] + G[u, c]),
+ *     W_u = sum_k w_uk                                   (double [m]).
+ * R: the forward result (double [n, K], needed for grad_w); G: dL/dR
+ * (double [n, K]); grad_S, grad_w may be NULL. Device arrays, vertex-id order.
+ */
+int prdf_pagerank_backward(prdf_graph* g, const double* R, const double* G, int K, double* grad_S, double* grad_w,
+                           const prdf_params* p, prdf_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,8 @@ _SIGNATURES = {
     "prdf_pagerank_static": (_INT, [_P, _P, _P, _P, _P]),
     "prdf_pagerank_dfp": (_INT, [_P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "prdf_pagerank_ppr": (_INT, [_P, _P, _INT, _P, _P, _P]),
+    "prdf_graph_set_weights": (_INT, [_P, _P, _P]),
+    "prdf_pagerank_backward": (_INT, [_P, _P, _P, _INT, _P, _P, _P, _P]),
 }
 
 
@@ -275,3 +277,48 @@ class Graph:
         _check(lib().prdf_pagerank_ppr(self._h, _ptr(S, torch.float64, name="S"), K, _ptr(R), ctypes.byref(p),
                                        ctypes.byref(st)))
         return R, _stats(st)
+
+    def set_weights(self, w: torch.Tensor):
+        """Edge weights in the out-CSR slot order (float32 [m])."""
+        _check(lib().prdf_graph_set_weights(self._h, _ptr(w, torch.float32, self.m, "w"), _stream()))
+        self.weighted = True
+
+    def pagerank_backward(self, R: torch.Tensor, G: torch.Tensor, want_grad_S: bool = True, want_grad_w: bool = True,
+                          **kw):
+        """Adjoint of pagerank_ppr for L = sum(G * R): returns (grad_S [n, K] or None, grad_w [m] or None, Stats)."""
+        n, m = self.size()
+        K = G.shape[1]
+        gS = torch.empty((n, K), dtype=torch.float64, device="cuda") if want_grad_S else None
+        gw = torch.empty(max(m, 1), dtype=torch.float64, device="cuda") if want_grad_w else None
+        st = _Stats()
+        p = params(**kw)
+        _check(lib().prdf_pagerank_backward(self._h, _ptr(R, torch.float64, n * K, "R"), _ptr(G, torch.float64, n * K, "G"),
+                                            K, _ptr(gS), _ptr(gw), ctypes.byref(p), ctypes.byref(st)))
+        return gS, (gw[:m] if gw is not None else None), _stats(st)
+
+
+class PageRankFn(torch.autograd.Function):
+    """R = PageRankFn.apply(graph, S, w, params): K-column weighted personalised PageRank
+    (forward: prdf_pagerank_ppr) with gradients for S and the edge weights w (out-CSR slot
+    order, float32) from the hand-written adjoint (prdf_pagerank_backward)."""
+
+    @staticmethod
+    def forward(ctx, graph, S, w, kw=None):
+        kw = dict(kw or {})
+        graph.set_weights(w.detach().to(torch.float32).contiguous())
+        R, _ = graph.pagerank_ppr(S.detach().to(torch.float64).contiguous(), **kw)
+        ctx.graph = graph
+        ctx.kw = kw
+        ctx.w_dtype = w.dtype
+        ctx.S_dtype = S.dtype
+        ctx.save_for_backward(R)
+        return R
+
+    @staticmethod
+    def backward(ctx, grad_R):
+        (R,) = ctx.saved_tensors
+        need_S, need_w = ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+        gS, gw, _ = ctx.graph.pagerank_backward(R, grad_R.detach().to(torch.float64).contiguous(), want_grad_S=need_S,
+                                                want_grad_w=need_w, **ctx.kw)
+        return (None, gS.to(ctx.S_dtype) if gS is not None else None, gw.to(ctx.w_dtype) if gw is not None else None,
+                None)

@@ -82,14 +82,49 @@ __global__ void k_rows_gather(const double* __restrict__ src, const int32_t* __r
   }
 }
 
-// dst[perm[i], :] = src[i, :]
+// dst[perm[i], :] = scale * src[i, :]
 __global__ void k_rows_scatter(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t n, int K,
-                               double* __restrict__ dst) {
+                               double* __restrict__ dst, double scale = 1.0) {
   const int64_t cnt = n * K;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / K, c = t - i * K;
-    dst[(int64_t)perm[i] * K + c] = src[t];
+    dst[(int64_t)perm[i] * K + c] = scale * src[t];
   }
+}
+
+// dst[i, :] = scale * src[perm[i], :]
+__global__ void k_rows_gather_scaled(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t n,
+                                     int K, double scale, double* __restrict__ dst) {
+  const int64_t cnt = n * K;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / K, c = t - i * K;
+    dst[t] = scale * src[(int64_t)perm[i] * K + c];
+  }
+}
+
+// in-CSR weights from out-CSR weights: slot (u -> v) of row u holds w; find u in in-row v
+__global__ void k_weights_to_in(const int64_t* __restrict__ ooff, const int32_t* __restrict__ oadj,
+                                const float* __restrict__ w, int32_t n, const int64_t* __restrict__ ioff,
+                                const int32_t* __restrict__ iadj, float* __restrict__ win, int* __restrict__ bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int flag = 0;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    for (int64_t j = ooff[u] + lane; j < ooff[u + 1]; j += 32) {
+      const float x = w[j];
+      if (!(x > 0.f) || !isfinite(x)) flag = 1;
+      const int32_t v = oadj[j];
+      int64_t lo = ioff[v], hi = ioff[v + 1];
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (iadj[mid] < (int32_t)u) lo = mid + 1; else hi = mid;
+      }
+      win[lo] = x;  // (v, u) is in G' because (u, v) is in G
+    }
+  }
+  flag = __reduce_or_sync(0xffffffffu, flag);
+  if (lane == 0 && flag) atomicOr(bad, 1);
 }
 
 // R[perm[i]] = x[i] * |out(perm[i])|; dV_out[perm[i]] = dV[i]
@@ -454,6 +489,17 @@ int iterate32(prdf_graph* g, const prdf_params* p, int* iters, int* final_buf, l
 
 int auto_tile(int K) { return K >= 32 ? 32 : (K > 8 ? 16 : 8); }
 
+// the K-column fixed-point operator: forward pull over G' (P on in-slots) or
+// adjoint pull over G (P on out-slots)
+struct KOp {
+  const int64_t* off;
+  const int32_t* adj;
+  const float* p32;
+  const double* p64;
+  int64_t hub_begin;
+  const double* S64;  // right-hand side of the FP64 step
+};
+
 int64_t hub_begin(const Relabel& rl) {
   const int C = rl.thr.n + 1;
   int64_t cb[kMaxThr + 2];
@@ -463,22 +509,21 @@ int64_t hub_begin(const Relabel& rl) {
 
 // FP32 K-column solve of R = alpha P^T R + (1 - alpha) rhs from the start held
 // in *cur; on return *cur holds the result (the other buffer is scratch).
-int ppr32_solve(prdf_graph* g, const prdf_params* p, int K, int tile, const float* rhs, float** cur, float** other,
-                int max_iter, int* iters, long long* kernels, cudaStream_t s) {
+int ppr32_solve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, const float* rhs, float** cur,
+                float** other, int max_iter, int* iters, long long* kernels, cudaStream_t s) {
   PRDF_TRY(g->resid32.reserve(2 * ((size_t)max_iter + 1), s));
   PRDF_CUDA(cudaMemsetAsync(g->resid32.p, 0, sizeof(uint32_t) * 2 * ((size_t)max_iter + 1), s));
-  const Relabel& rl = g->rl;
   Ppr32Args a;
   memset(&a, 0, sizeof(a));
-  a.off = rl.in.off.p;
-  a.adj = rl.in.adj.p;
-  a.P = g->pin32.p;
+  a.off = op.off;
+  a.adj = op.adj;
+  a.P = op.p32;
   a.S = rhs;
   a.K = K;
   a.alpha = (float)p->alpha;
   a.beta = (float)(1.0 - p->alpha);
   a.tol_rel = (float)p->tol_fp32_rel;
-  const int64_t hb = hub_begin(rl);
+  const int64_t hb = op.hub_begin;
   const int check = p->check_every > 0 ? p->check_every : 8;
   float* buf[2] = {*cur, *other};
   int launched = 0;
@@ -525,30 +570,92 @@ int ppr32_solve(prdf_graph* g, const prdf_params* p, int K, int tile, const floa
 }
 
 // one FP64 Jacobi step Rn = T(R); returns max |T(R) - R|
-int ppr64_step(prdf_graph* g, const prdf_params* p, int K, int tile, const double* R, double* Rn, float* res32,
-               double* dmax, long long* kernels, cudaStream_t s) {
+int ppr64_step(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, const double* R, double* Rn,
+               float* res32, double* dmax, long long* kernels, cudaStream_t s) {
   PRDF_TRY(g->resid.reserve(2, s));
   PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t), s));
-  const Relabel& rl = g->rl;
   Ppr64Args a;
   memset(&a, 0, sizeof(a));
-  a.off = rl.in.off.p;
-  a.adj = rl.in.adj.p;
-  a.P = g->pin64.p;
+  a.off = op.off;
+  a.adj = op.adj;
+  a.P = op.p64;
   a.R = R;
   a.Rn = Rn;
-  a.S = g->S64.p;
+  a.S = op.S64;
   a.res32 = res32;
   a.K = K;
   a.alpha = p->alpha;
   a.beta = 1.0 - p->alpha;
   a.inv_beta = 1.0 / (1.0 - p->alpha);
   a.dmax = g->resid.p;
-  PRDF_TRY(launch_ppr64_step(a, tile, g->n, hub_begin(rl), s));
+  PRDF_TRY(launch_ppr64_step(a, tile, g->n, op.hub_begin, s));
   PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
   memcpy(dmax, g->ws.host_i64, sizeof(double));
   *kernels += (long long)((K + tile - 1) / tile) * 2;
+  return PRDF_OK;
+}
+
+// Solve X = alpha * A X + (1 - alpha) * op.S64 (A = P^T on G' or P on G) from
+// X = S64, K columns in the class-contiguous numbering; result in *out
+// (one of R64a / R64b). Mixed: FP32 solve, then iterative refinement with an
+// FP64 step for the residual and an FP32 solve for the correction.
+struct KSolve {
+  int iters32 = 0, steps64 = 0, converged = 0;
+  double dmax = 0;
+  long long kernels = 0;
+};
+
+int ksolve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, double** out, KSolve* r,
+           cudaStream_t s) {
+  const int64_t cnt = (int64_t)g->n * K;
+  if (p->precision == PRDF_FP64) {
+    PRDF_CUDA(cudaMemcpyAsync(g->R64a.p, op.S64, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s));
+    double* a = g->R64a.p;
+    double* b = g->R64b.p;
+    for (int it = 0; it < p->max_iter; ++it) {
+      PRDF_TRY(ppr64_step(g, op, p, K, tile, a, b, nullptr, &r->dmax, &r->kernels, s));
+      ++r->steps64;
+      double* tmp = a;
+      a = b;
+      b = tmp;
+      if (r->dmax <= p->tol) {
+        r->converged = 1;
+        break;
+      }
+    }
+    *out = a;
+    return PRDF_OK;
+  }
+  PRDF_TRY(g->S32.reserve(cnt, s));
+  PRDF_TRY(g->R32a.reserve(cnt, s));
+  PRDF_TRY(g->R32b.reserve(cnt, s));
+  PRDF_TRY(ppr_narrow(op.S64, cnt, g->S32.p, s));
+  PRDF_CUDA(cudaMemcpyAsync(g->R32a.p, g->S32.p, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s));
+  float* cur = g->R32a.p;
+  float* oth = g->R32b.p;
+  int it32 = 0;
+  PRDF_TRY(ppr32_solve(g, op, p, K, tile, g->S32.p, &cur, &oth, p->max_iter, &it32, &r->kernels, s));
+  r->iters32 += it32;
+  PRDF_TRY(ppr_widen(cur, cnt, g->R64a.p, s));
+  r->kernels += 2;
+  const int kRounds = 8;
+  for (int round = 0; round < kRounds; ++round) {
+    PRDF_TRY(ppr64_step(g, op, p, K, tile, g->R64a.p, g->R64b.p, g->S32.p, &r->dmax, &r->kernels, s));
+    ++r->steps64;
+    if (r->dmax <= p->tol) {
+      r->converged = 1;
+      break;
+    }
+    PRDF_CUDA(cudaMemcpyAsync(g->R32a.p, g->S32.p, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s));
+    cur = g->R32a.p;
+    oth = g->R32b.p;
+    PRDF_TRY(ppr32_solve(g, op, p, K, tile, g->S32.p, &cur, &oth, p->max_iter, &it32, &r->kernels, s));
+    r->iters32 += it32;
+    PRDF_TRY(ppr_add_correction(g->R64a.p, cur, cnt, s));
+    r->kernels += 1;
+  }
+  *out = g->R64b.p;  // T(X) of the last step
   return PRDF_OK;
 }
 
@@ -961,61 +1068,15 @@ int prdf_pagerank_ppr(prdf_graph* g, const double* S, int K, double* R, const pr
   PRDF_TRY(g->R64b.reserve(cnt, s));
   k_rows_gather<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(S, g->rl.perm.p, g->n, K, g->S64.p);
   PRDF_LAUNCH_CHECK();
-  long long kernels = 1;
-  int iters32 = 0, steps64 = 0, conv = 0;
-  double dmax = 0;
-  double* Rfinal = nullptr;
   PRDF_CUDA(cudaEventRecord(t.e[1], s));
-  if (p->precision == PRDF_FP64) {
-    // plain FP64 Jacobi from R = S
-    PRDF_CUDA(cudaMemcpyAsync(g->R64a.p, g->S64.p, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s));
-    double* a = g->R64a.p;
-    double* b = g->R64b.p;
-    for (int it = 0; it < p->max_iter; ++it) {
-      PRDF_TRY(ppr64_step(g, p, K, tile, a, b, nullptr, &dmax, &kernels, s));
-      ++steps64;
-      double* tmp = a;
-      a = b;
-      b = tmp;
-      if (dmax <= p->tol) {
-        conv = 1;
-        break;
-      }
-    }
-    Rfinal = a;
-  } else {
-    PRDF_TRY(g->S32.reserve(cnt, s));
-    PRDF_TRY(g->R32a.reserve(cnt, s));
-    PRDF_TRY(g->R32b.reserve(cnt, s));
-    PRDF_TRY(ppr_narrow(g->S64.p, cnt, g->S32.p, s));
-    PRDF_CUDA(cudaMemcpyAsync(g->R32a.p, g->S32.p, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s));
-    float* cur = g->R32a.p;
-    float* oth = g->R32b.p;
-    int it32 = 0;
-    PRDF_TRY(ppr32_solve(g, p, K, tile, g->S32.p, &cur, &oth, p->max_iter, &it32, &kernels, s));
-    iters32 += it32;
-    PRDF_TRY(ppr_widen(cur, cnt, g->R64a.p, s));
-    kernels += 2;
-    // iterative refinement: residual in FP64, correction in FP32
-    const int kRounds = 8;
-    for (int round = 0; round < kRounds; ++round) {
-      PRDF_TRY(ppr64_step(g, p, K, tile, g->R64a.p, g->R64b.p, g->S32.p, &dmax, &kernels, s));
-      ++steps64;
-      if (dmax <= p->tol) {
-        conv = 1;
-        break;
-      }
-      // E = alpha P^T E + (1 - alpha) * res / (1 - alpha), started from the right-hand side
-      PRDF_CUDA(cudaMemcpyAsync(g->R32a.p, g->S32.p, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s));
-      cur = g->R32a.p;
-      oth = g->R32b.p;
-      PRDF_TRY(ppr32_solve(g, p, K, tile, g->S32.p, &cur, &oth, p->max_iter, &it32, &kernels, s));
-      iters32 += it32;
-      PRDF_TRY(ppr_add_correction(g->R64a.p, cur, cnt, s));
-      kernels += 1;
-    }
-    Rfinal = g->R64b.p;  // T(R) of the last step
-  }
+  const KOp op{g->rl.in.off.p, g->rl.in.adj.p, g->pin32.p, g->pin64.p, hub_begin(g->rl), g->S64.p};
+  KSolve ks;
+  ks.kernels = 1;
+  double* Rfinal = nullptr;
+  PRDF_TRY(ksolve(g, op, p, K, tile, &Rfinal, &ks, s));
+  long long kernels = ks.kernels;
+  const int iters32 = ks.iters32, steps64 = ks.steps64, conv = ks.converged;
+  const double dmax = ks.dmax;
   k_rows_scatter<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(Rfinal, g->rl.perm.p, g->n, K, R);
   PRDF_LAUNCH_CHECK();
   kernels += 1;
@@ -1032,6 +1093,107 @@ int prdf_pagerank_ppr(prdf_graph* g, const double* S, int K, double* R, const pr
     cudaEventElapsedTime(&stats->ms_iterate, t.e[1], t.e[2]);
     stats->edges_processed = (long long)(steps64 + iters32) * g->rl.in.m * K;
     stats->kernel_launches = kernels;
+  }
+  return PRDF_OK;
+}
+
+int prdf_graph_set_weights(prdf_graph* g, const float* w, void* stream) {
+  if (!g || !w) {
+    set_error("prdf_graph_set_weights: bad arguments");
+    return PRDF_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Csr& o = g->csr[PRDF_OUT];
+  Csr& in = g->csr[PRDF_IN];
+  DBuf<float> wo, wi;
+  PRDF_TRY(wo.alloc(o.m > 0 ? (size_t)o.m : 1, s));
+  PRDF_TRY(wi.alloc(in.m > 0 ? (size_t)in.m : 1, s));
+  DBuf<int> bad;
+  PRDF_TRY(bad.alloc(1, s));
+  PRDF_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+  PRDF_CUDA(cudaMemcpyAsync(wo.p, w, sizeof(float) * (size_t)o.m, cudaMemcpyDeviceToDevice, s));
+  k_weights_to_in<<<grid_for((int64_t)g->n * 32, kThreads), kThreads, 0, s>>>(o.off.p, o.adj.p, w, g->n, in.off.p,
+                                                                               in.adj.p, wi.p, bad.p);
+  PRDF_LAUNCH_CHECK();
+  PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  if (*(int*)g->ws.host_i64) {
+    set_error("edge weights must be finite and > 0");
+    return PRDF_EINVAL;
+  }
+  o.w = static_cast<DBuf<float>&&>(wo);
+  in.w = static_cast<DBuf<float>&&>(wi);
+  g->weighted = true;
+  PRDF_TRY(build_relabelled(g, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  return PRDF_OK;
+}
+
+int prdf_pagerank_backward(prdf_graph* g, const double* R, const double* G, int K, double* grad_S, double* grad_w,
+                           const prdf_params* p, prdf_stats* stats) {
+  if (!g || !G || (grad_w && !R)) {
+    set_error("prdf_pagerank_backward: bad arguments");
+    return PRDF_EINVAL;
+  }
+  if (K < 1) {
+    set_error("prdf_pagerank_backward: K must be >= 1");
+    return PRDF_EINVAL;
+  }
+  if (!g->weighted) {
+    set_error("prdf_pagerank_backward: the graph has no edge weights");
+    return PRDF_ESTATE;
+  }
+  PRDF_TRY(check_params(p));
+  if (p->tile != 0 && p->tile != 8 && p->tile != 16 && p->tile != 32 && p->tile != 64) {
+    set_error("prdf_pagerank_backward: tile must be 0, 8, 16, 32 or 64");
+    return PRDF_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)p->stream;
+  Timer t;
+  PRDF_TRY(t.init());
+  PRDF_CUDA(cudaEventRecord(t.e[0], s));
+  PRDF_TRY(ensure_relabelled(g, false, s));
+  if (!g->ppr_valid) PRDF_TRY(build_ppr_weights(g, s));
+  const int tile = p->tile ? p->tile : auto_tile(K);
+  const int64_t cnt = (int64_t)g->n * K;
+  const double beta = 1.0 - p->alpha;
+  PRDF_TRY(g->S64.reserve(cnt, s));
+  PRDF_TRY(g->R64a.reserve(cnt, s));
+  PRDF_TRY(g->R64b.reserve(cnt, s));
+  // lambda = alpha P lambda + G, i.e. X = alpha A X + (1 - alpha) * G / (1 - alpha) over the out-CSR
+  k_rows_gather_scaled<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(G, g->rl.perm.p, g->n, K, 1.0 / beta, g->S64.p);
+  PRDF_LAUNCH_CHECK();
+  PRDF_CUDA(cudaEventRecord(t.e[1], s));
+  const KOp op{g->rl.out.off.p, g->rl.out.adj.p, g->pout32.p, g->pout64.p, hub_begin(g->rl), g->S64.p};
+  KSolve ks;
+  ks.kernels = 1;
+  double* lam = nullptr;
+  PRDF_TRY(ksolve(g, op, p, K, tile, &lam, &ks, s));
+  if (grad_S) {
+    k_rows_scatter<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(lam, g->rl.perm.p, g->n, K, grad_S, beta);
+    PRDF_LAUNCH_CHECK();
+    ks.kernels += 1;
+  }
+  if (grad_w) {
+    double* Rr = (lam == g->R64a.p) ? g->R64b.p : g->R64a.p;
+    k_rows_gather_scaled<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(R, g->rl.perm.p, g->n, K, 1.0, Rr);
+    PRDF_LAUNCH_CHECK();
+    PRDF_TRY(launch_grad_w(g->rl.out.off.p, g->rl.out.adj.p, g->rl.perm.p, g->csr[PRDF_OUT].off.p, lam, g->S64.p, beta,
+                           Rr, g->wsum.p, g->n, K, p->alpha, grad_w, s));
+    ks.kernels += 2;
+  }
+  PRDF_CUDA(cudaEventRecord(t.e[2], s));
+  PRDF_CUDA(cudaEventSynchronize(t.e[2]));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations = ks.steps64 + ks.iters32;
+    stats->iterations_fp32 = ks.iters32;
+    stats->converged = ks.converged;
+    stats->final_delta = ks.dmax;
+    cudaEventElapsedTime(&stats->ms_total, t.e[0], t.e[2]);
+    cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
+    cudaEventElapsedTime(&stats->ms_iterate, t.e[1], t.e[2]);
+    stats->kernel_launches = ks.kernels;
   }
   return PRDF_OK;
 }

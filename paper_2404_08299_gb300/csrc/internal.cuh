@@ -127,6 +127,9 @@ struct Ppr64Args {
 int launch_ppr32_sweep(const Ppr32Args& a, int tile, int64_t n, int64_t hub_begin, cudaStream_t s);
 int launch_ppr64_step(const Ppr64Args& a, int tile, int64_t n, int64_t hub_begin, cudaStream_t s);
 int ppr_add_correction(double* R, const float* E, int64_t cnt, cudaStream_t s);
+int launch_grad_w(const int64_t* off, const int32_t* adj, const int32_t* perm, const int64_t* orig_off,
+                  const double* lam, const double* Gs, double g_scale, const double* Rr, const double* W, int32_t n,
+                  int K, double alpha, double* grad_w, cudaStream_t s);
 int ppr_narrow(const double* x, int64_t cnt, float* y, cudaStream_t s);
 int ppr_widen(const float* y, int64_t cnt, double* x, cudaStream_t s);
 

@@ -256,6 +256,38 @@ __global__ void __launch_bounds__(kThreads) k_ppr64_step(const Ppr64Args a, int6
   }
 }
 
+// Edge gradient of L = sum_c G_c . R_c with respect to w_uv (out-slot j of
+// renumbered row i, vertex u = perm[i], target v = adj[j]):
+//   dL/dw_uv = (1 / W_u) * sum_c R[u, c] * (alpha * lambda[v, c] - (lambda[u, c] - G[u, c]))
+// using sum_k P_uk lambda[k] = (lambda[u] - G[u]) / alpha. The per-row constant
+// b_u = sum_c R[u, c] * (lambda[u, c] - G[u, c]) is formed once per row; one
+// warp per row, lanes over edges; written to the original out-slot order.
+__global__ void k_grad_w(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                         const int32_t* __restrict__ perm, const int64_t* __restrict__ orig_off,
+                         const double* __restrict__ lam, const double* __restrict__ Gs, double g_scale,
+                         const double* __restrict__ Rr, const double* __restrict__ W, int32_t n, int K, double alpha,
+                         double* __restrict__ grad_w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const double* Ri = Rr + i * K;
+    // b = sum_c R[i, c] * (lambda[i, c] - G[i, c]), lanes over columns
+    double b = 0;
+    for (int c = lane; c < K; c += 32) b = fma(Ri[c], lam[i * K + c] - g_scale * Gs[i * K + c], b);
+    b = warp_sum_f64(b);
+    const int32_t u = perm[i];
+    const double invW = 1.0 / W[u];
+    const int64_t rb = off[i], re = off[i + 1], ob = orig_off[u];
+    for (int64_t j = rb + lane; j < re; j += 32) {
+      const double* Lv = lam + (int64_t)adj[j] * K;
+      double d = 0;
+      for (int c = 0; c < K; ++c) d = fma(Ri[c], __ldg(Lv + c), d);
+      grad_w[ob + (j - rb)] = (alpha * d - b) * invW;
+    }
+  }
+}
+
 // R64 += (double) E32
 __global__ void k_add_correction(double* __restrict__ R, const float* __restrict__ E, int64_t cnt) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
@@ -310,6 +342,15 @@ int launch_ppr64_step(const Ppr64Args& a, int tile, int64_t n, int64_t hub_begin
       default: launch64_tile<32>(a, 0, hub_begin, n, c0, s); break;
     }
   }
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+int launch_grad_w(const int64_t* off, const int32_t* adj, const int32_t* perm, const int64_t* orig_off,
+                  const double* lam, const double* Gs, double g_scale, const double* Rr, const double* W, int32_t n,
+                  int K, double alpha, double* grad_w, cudaStream_t s) {
+  k_grad_w<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(off, adj, perm, orig_off, lam, Gs, g_scale, Rr, W, n,
+                                                                     K, alpha, grad_w);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }
