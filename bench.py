@@ -195,6 +195,47 @@ def measure_dfp(g, n, m, args):
     return out
 
 
+def measure_ppr(args):
+    """Weighted personalised PageRank and its adjoint on the 2^22-vertex R-MAT (2^26 samples, weights
+    U[0.5, 1.5) on every edge and self-loop, row-normalised), K = 64 teleport columns each on 16 seed
+    vertices with Dirichlet(1) weights, loss sum_c g_c . r_c with g ~ N(0, 1): time to tolerance of the
+    mixed-precision and FP64 forms (same 1e-10 L-inf stop rule) and of the backward pass."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2404_08299_gb300 as prdf
+    n, s, d = synth.rmat(22, 1 << 26, seed=1)
+    loops = np.arange(n, dtype=np.int32)
+    s2, d2 = np.concatenate([s, loops]), np.concatenate([d, loops])
+    w = synth.edge_weights(s2, d2, seed=1)
+    g = prdf.Graph(n, torch.from_numpy(s2).cuda(), torch.from_numpy(d2).cuda(), torch.from_numpy(w).cuda())
+    m = g.m
+    K = 64
+    S = torch.from_numpy(synth.ppr_seeds(n, K, n_seed=16, seed=2)).cuda()
+    Gw = torch.from_numpy(synth.normal((n, K), seed=3)).cuda()
+    out = {"n": n, "m": m, "K": K}
+    res = {}
+    for name, prec in (("fp32_refined", prdf.PRDF_FP32_REFINE), ("fp64", prdf.PRDF_FP64)):
+        g.pagerank_ppr(S, precision=prec)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.time()
+        R, st = g.pagerank_ppr(S, precision=prec)
+        torch.cuda.synchronize()
+        res[name] = R
+        out[name] = {"ms": st.ms_total, "wall_ms": (time.time() - t0) * 1e3, "sweeps_fp32": st.iterations_fp32,
+                     "steps_fp64": st.iterations - st.iterations_fp32, "converged": bool(st.converged),
+                     "column_gteps": st.iterations * m * K / (st.ms_total * 1e-3) / 1e9}
+    out["linf_mixed_vs_fp64"] = float((res["fp32_refined"] - res["fp64"]).abs().max())
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["fp32_refined"]["ms"]
+    g.pagerank_backward(res["fp32_refined"], Gw, precision=prdf.PRDF_FP32_REFINE)
+    gS, gw, stb = g.pagerank_backward(res["fp32_refined"], Gw, precision=prdf.PRDF_FP32_REFINE)
+    out["backward"] = {"ms": stb.ms_total, "sweeps_fp32": stb.iterations_fp32,
+                       "steps_fp64": stb.iterations - stb.iterations_fp32, "converged": bool(stb.converged)}
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(n, src, dst, m, target_s):
     """The FP64 oracle (as it stands) on the host cores: a bounded sample of sweeps
     of the same Static iteration on the same graph."""
@@ -382,6 +423,10 @@ def main():
 
     if not args.no_extras and args.dfp_sizes:
         extras["dfp"] = measure_dfp(g, n, m, args)
+    if not args.no_extras:
+        del g
+        torch.cuda.empty_cache()
+        extras["ppr_adjoint"] = measure_ppr(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
