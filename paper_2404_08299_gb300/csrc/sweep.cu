@@ -35,6 +35,23 @@ template <>
 struct Acc<true> {
   Fix4 v;
   __device__ __forceinline__ void add(uint64_t xb) { v.add(xb); }
+  __device__ __forceinline__ void merge(const Acc& o) { v.add4(o.v.w0, o.v.w1, o.v.w2, o.v.w3); }
+  __device__ __forceinline__ Acc shfl_up(int o) const {
+    Acc r;
+    r.v.w0 = __shfl_up_sync(0xffffffffu, v.w0, o);
+    r.v.w1 = __shfl_up_sync(0xffffffffu, v.w1, o);
+    r.v.w2 = __shfl_up_sync(0xffffffffu, v.w2, o);
+    r.v.w3 = __shfl_up_sync(0xffffffffu, v.w3, o);
+    return r;
+  }
+  __device__ __forceinline__ Acc shfl_idx(int l) const {
+    Acc r;
+    r.v.w0 = __shfl_sync(0xffffffffu, v.w0, l);
+    r.v.w1 = __shfl_sync(0xffffffffu, v.w1, l);
+    r.v.w2 = __shfl_sync(0xffffffffu, v.w2, l);
+    r.v.w3 = __shfl_sync(0xffffffffu, v.w3, l);
+    return r;
+  }
   template <int G>
   __device__ __forceinline__ void group_reduce() { v.template group_reduce<G>(); }
   __device__ __forceinline__ double value() const { return v.to_double(); }
@@ -46,6 +63,17 @@ template <>
 struct Acc<false> {
   double v = 0;
   __device__ __forceinline__ void add(uint64_t xb) { v += bitsd(xb); }
+  __device__ __forceinline__ void merge(const Acc& o) { v += o.v; }
+  __device__ __forceinline__ Acc shfl_up(int o) const {
+    Acc r;
+    r.v = __shfl_up_sync(0xffffffffu, v, o);
+    return r;
+  }
+  __device__ __forceinline__ Acc shfl_idx(int l) const {
+    Acc r;
+    r.v = __shfl_sync(0xffffffffu, v, l);
+    return r;
+  }
   template <int G>
   __device__ __forceinline__ void group_reduce() {
 #pragma unroll
@@ -104,13 +132,16 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
       xself = (u == v) ? xv : xself;
     }
   }
-  for (int64_t q0 = ba + 4 * (int64_t)lane; q0 < ea; q0 += 4 * (int64_t)NT * KV) {
-    int4 u4[KV];
+  // body: the next chunk's indices are loaded while this chunk's gathers are in flight
+  const int64_t step = 4 * (int64_t)NT * KV;
+  int64_t q0 = ba + 4 * (int64_t)lane;
+  int4 u4[KV];
 #pragma unroll
-    for (int k = 0; k < KV; ++k) {
-      const int64_t q = q0 + 4 * (int64_t)NT * k;
-      u4[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
-    }
+  for (int k = 0; k < KV; ++k) {
+    const int64_t q = q0 + 4 * (int64_t)NT * k;
+    u4[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
+  }
+  for (; q0 < ea; q0 += step) {
     uint64_t xv[4 * KV];
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
@@ -118,6 +149,12 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
       xv[4 * k + 1] = u4[k].y >= 0 ? ld_gather_b64(a.x + u4[k].y, pl) : 0ull;
       xv[4 * k + 2] = u4[k].z >= 0 ? ld_gather_b64(a.x + u4[k].z, pl) : 0ull;
       xv[4 * k + 3] = u4[k].w >= 0 ? ld_gather_b64(a.x + u4[k].w, pl) : 0ull;
+    }
+    int4 nx[KV];
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      const int64_t q = q0 + step + 4 * (int64_t)NT * k;
+      nx[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
     }
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
@@ -131,6 +168,8 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
       xself = (u4[k].z == v) ? xv[4 * k + 2] : xself;
       xself = (u4[k].w == v) ? xv[4 * k + 3] : xself;
     }
+#pragma unroll
+    for (int k = 0; k < KV; ++k) u4[k] = nx[k];
   }
 }
 
