@@ -78,7 +78,9 @@ typedef struct {
   int accumulate;      /* PRDF_ACC_EXACT (default) or PRDF_ACC_FP64 */
   int prune;           /* DF-P (1, default) or DF (0), for prdf_pagerank_dfp */
   int check_every;     /* sweeps launched between host convergence checks, default 8 */
-  int time_sweeps;     /* 1: time every rank sweep with CUDA events (stats->ms_sweep), default 0 */
+  int time_sweeps;     /* 1: time every rank sweep with CUDA events (stats->ms_sweep) from a host-driven
+                          loop; 0 (default): the Static FP64 loop runs as one CUDA graph (device-side
+                          convergence test, no host round trips) */
   int tile;            /* K-column calls: columns per index fetch (8, 16, 32, 64); 0 = automatic */
   void* stream;        /* cudaStream_t for all work; NULL = legacy default stream */
 } prdf_params;
@@ -231,6 +233,26 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
                       int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins,
                       const double* prev_ranks, double* ranks, const prdf_params* p, uint8_t* dV_out,
                       prdf_stats* stats);
+
+/* ------------------------------------------------------------ tuning -- */
+
+/*
+ * Choose the in-degree class thresholds of the rank sweep for this graph
+ * (the paper leaves D_P and the kernel shapes open, Appendix A.2): each of a
+ * fixed list of candidates is applied, `sweeps` FP64 sweeps are timed with
+ * CUDA events, and the fastest candidate stays applied. best_index (host,
+ * nullable) receives the winner's index, best_ms_per_sweep (host, nullable)
+ * its time per sweep. Uses p->alpha, p->accumulate and p->stream.
+ */
+int prdf_autotune(prdf_graph* g, const prdf_params* p, int sweeps, int* best_index, float* best_ms_per_sweep);
+
+/*
+ * Choose the column tile width (8, 16, 32 or 64) of the K-column calls for
+ * this graph and K by timing `sweeps` FP64 sweeps of prdf_pagerank_ppr with
+ * teleport S (double [n, K] device). best_tile: host output; pass it as
+ * prdf_params.tile.
+ */
+int prdf_autotune_tile(prdf_graph* g, const double* S, int K, const prdf_params* p, int sweeps, int* best_tile);
 
 /* ------------------------------------------------------ K columns ------ */
 

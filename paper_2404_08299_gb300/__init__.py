@@ -87,6 +87,8 @@ _SIGNATURES = {
     "prdf_pagerank_dfp": (_INT, [_P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "prdf_pagerank_ppr": (_INT, [_P, _P, _INT, _P, _P, _P]),
     "prdf_graph_set_weights": (_INT, [_P, _P, _P]),
+    "prdf_autotune": (_INT, [_P, _P, _INT, _P, _P]),
+    "prdf_autotune_tile": (_INT, [_P, _P, _INT, _P, _INT, _P]),
     "prdf_pagerank_backward": (_INT, [_P, _P, _P, _INT, _P, _P, _P, _P]),
 }
 
@@ -217,6 +219,23 @@ class Graph:
                                             _ptr(ins_w, torch.float32, ni, "ins_w"), ni, _ptr(de), _ptr(ie),
                                             _stream()))
         return de[:nd], ie[:ni]
+
+    def autotune(self, sweeps: int = 8, **kw):
+        """Pick the fastest in-degree class thresholds for this graph (prdf_autotune).
+        Returns (candidate index, ms per sweep)."""
+        idx = ctypes.c_int()
+        ms = ctypes.c_float()
+        p = params(**kw)
+        _check(lib().prdf_autotune(self._h, ctypes.byref(p), sweeps, ctypes.byref(idx), ctypes.byref(ms)))
+        return idx.value, ms.value
+
+    def autotune_tile(self, S: torch.Tensor, sweeps: int = 3, **kw) -> int:
+        """Fastest column tile width for K-column calls with teleport S (prdf_autotune_tile)."""
+        tile = ctypes.c_int()
+        p = params(**kw)
+        _check(lib().prdf_autotune_tile(self._h, _ptr(S, torch.float64, name="S"), S.shape[1], ctypes.byref(p), sweeps,
+                                        ctypes.byref(tile)))
+        return tile.value
 
     def set_thresholds(self, which: int, thresholds):
         arr = (ctypes.c_int64 * len(thresholds))(*[int(t) for t in thresholds])

@@ -659,6 +659,107 @@ int ksolve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, 
   return PRDF_OK;
 }
 
+// Static FP64 loop as one CUDA graph: a while node whose body is one sweep
+// (all classes) and a one-thread check that advances the device iteration
+// counter and stops at L-inf <= tol or max_iter. One launch per solve, no host
+// round trips. The instantiated graph is cached on the graph handle and rebuilt
+// when its buffers, numbering or parameters change.
+int iterate_graph(prdf_graph* g, const prdf_params* p, IterResult* res, cudaStream_t s) {
+  const int max_iter = p->max_iter;
+  const bool exact = p->accumulate == PRDF_ACC_EXACT;
+  PRDF_TRY(g->resid.reserve((size_t)max_iter + 1, s));
+  PRDF_TRY(g->ctl.reserve(2, s));
+  PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t) * ((size_t)max_iter + 1), s));
+  PRDF_CUDA(cudaMemsetAsync(g->ctl.p, 0, 2 * sizeof(int), s));
+  const Relabel& rl = g->rl;
+  int64_t cb[kMaxThr + 2];
+  const int nci = rl.thr.n + 1;
+  begins_from_counts(rl.count, nci, cb);
+  uint64_t key[8];
+  key[0] = (uint64_t)(uintptr_t)g->xa.p ^ ((uint64_t)(uintptr_t)g->xb.p << 1);
+  key[1] = (uint64_t)(uintptr_t)g->resid.p ^ ((uint64_t)(uintptr_t)g->ctl.p << 1);
+  key[2] = rl.version;
+  memcpy(&key[3], &p->alpha, 8);
+  memcpy(&key[4], &p->tol, 8);
+  key[5] = (uint64_t)max_iter;
+  key[6] = exact ? 1 : 0;
+  key[7] = (uint64_t)(uintptr_t)g->rl.in.adj.p;
+  if (!g->static_exec || memcmp(key, g->static_key, sizeof(key)) != 0) {
+    if (g->static_exec) {
+      cudaGraphExecDestroy(g->static_exec);
+      g->static_exec = nullptr;
+    }
+    if (!g->cap_stream) PRDF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.off = rl.in.off.p;
+    a.adj = rl.in.adj.p;
+    a.degd = rl.degd.p;
+    a.inv_deg = rl.inv_deg.p;
+    a.alpha = p->alpha;
+    a.c0 = (1.0 - p->alpha) / (double)g->n;
+    a.self_loops = g->self_loops ? 1 : 0;
+    a.tol = p->tol;
+    a.ctl = g->ctl.p;
+    a.xa = g->xa.p;
+    a.xb = g->xb.p;
+    a.resid_base = g->resid.p;
+    cudaGraph_t graph = nullptr;
+    PRDF_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    alignas(cudaGraphNodeParams) unsigned char np_storage[sizeof(cudaGraphNodeParams)];
+    memset(np_storage, 0, sizeof(np_storage));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_storage);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(g->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    int rc = PRDF_OK;
+    if (e == cudaSuccess) {
+      rc = launch_sweep(a, rl.thr, cb, exact, false, g->cap_stream);
+      if (rc == PRDF_OK) rc = launch_iter_check(g->ctl.p, g->resid.p, p->tol, max_iter, h, g->cap_stream);
+      cudaGraph_t captured = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &captured);
+      if (e == cudaSuccess) e = e2;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && rc == PRDF_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (rc != PRDF_OK) return rc;
+    if (e != cudaSuccess) {
+      set_error("building the iteration graph: %s", cudaGetErrorString(e));
+      return PRDF_ECUDA;
+    }
+    g->static_exec = exec;
+    memcpy(g->static_key, key, sizeof(key));
+  }
+  PRDF_CUDA(cudaGraphLaunch(g->static_exec, s));
+  int hit = 0;
+  PRDF_CUDA(cudaMemcpyAsync(&hit, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  if (hit < 1 || hit > max_iter) {
+    set_error("iteration graph ran %d sweeps", hit);
+    return PRDF_ECUDA;
+  }
+  uint64_t last = 0;
+  PRDF_CUDA(cudaMemcpy(&last, g->resid.p + hit - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  memcpy(&res->final_delta, &last, sizeof(double));
+  res->iters = hit;
+  res->converged = res->final_delta <= p->tol ? 1 : 0;
+  const int k = hit - 1;
+  res->final_buf = (k & 1) ? 0 : 1;
+  res->launched = hit;
+  res->kernels = (long long)hit * (nonempty_classes(cb, nci) + 1);
+  res->ms_sweep = 0;
+  return PRDF_OK;
+}
+
 int alloc_solver(prdf_graph* g, bool dynamic, cudaStream_t s) {
   PRDF_TRY(g->xa.reserve(g->n, s));
   PRDF_TRY(g->xb.reserve(g->n, s));
@@ -758,6 +859,9 @@ int prdf_graph_create(int32_t n, const int32_t* src, const int32_t* dst, const f
 void prdf_graph_destroy(prdf_graph* g) {
   if (!g) return;
   cudaStreamSynchronize(g->stream);
+  cudaDeviceSynchronize();
+  if (g->static_exec) cudaGraphExecDestroy(g->static_exec);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   delete g;
 }
 
@@ -946,7 +1050,8 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
     PRDF_CUDA(cudaEventRecord(t.e[1], s));
   }
   IterResult it;
-  PRDF_TRY(iterate(g, &p64, false, &it, s));
+  if (p64.time_sweeps) PRDF_TRY(iterate(g, &p64, false, &it, s));
+  else PRDF_TRY(iterate_graph(g, &p64, &it, s));
   k_finalize<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, g->rl.degd.p,
                                                            g->rl.perm.p, g->n, ranks, nullptr, nullptr);
   PRDF_LAUNCH_CHECK();
@@ -962,7 +1067,7 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
     cudaEventElapsedTime(&stats->ms_total, t.e[0], t.e[2]);
     cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
     cudaEventElapsedTime(&stats->ms_iterate, t.e[1], t.e[2]);
-    stats->ms_sweep = it.ms_sweep;
+    stats->ms_sweep = it.ms_sweep > 0 ? it.ms_sweep : 0.f;
     stats->edges_processed = (long long)(it.iters + iters32) * g->csr[PRDF_IN].m;
     // init + sweeps + finalize
     stats->kernel_launches = 1 + kernels32 + it.kernels + 1;
@@ -1194,6 +1299,80 @@ int prdf_pagerank_backward(prdf_graph* g, const double* R, const double* G, int 
     cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
     cudaEventElapsedTime(&stats->ms_iterate, t.e[1], t.e[2]);
     stats->kernel_launches = ks.kernels;
+  }
+  return PRDF_OK;
+}
+
+int prdf_autotune(prdf_graph* g, const prdf_params* p, int sweeps, int* best_index, float* best_ms_per_sweep) {
+  if (!g || sweeps < 1) {
+    set_error("prdf_autotune: bad arguments");
+    return PRDF_EINVAL;
+  }
+  PRDF_TRY(check_params(p));
+  // candidate in-degree class thresholds (the sweep numbering is rebuilt for each)
+  static const int64_t cand[][6] = {
+      {5, 1, 4, 16, 128, 4096}, {3, 1, 16, 4096},   {4, 1, 4, 32, 1024}, {4, 1, 8, 64, 2048},
+      {3, 4, 128, 4096},        {2, 16, 2048},      {1, 4096, 0},         {5, 1, 4, 16, 256, 8192}};
+  const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
+  cudaStream_t s = (cudaStream_t)p->stream;
+  DBuf<double> R;
+  PRDF_TRY(R.alloc((size_t)g->n, s));
+  prdf_params q = *p;
+  q.max_iter = sweeps;
+  q.tol = 1e-300;  // run exactly `sweeps` sweeps
+  q.precision = PRDF_FP64;
+  q.time_sweeps = 0;
+  int best = 0;
+  float best_ms = 0;
+  for (int c = 0; c < ncand; ++c) {
+    PRDF_TRY(prdf_graph_set_thresholds(g, PRDF_IN, (int)cand[c][0], &cand[c][1]));
+    prdf_stats st;
+    PRDF_TRY(prdf_pagerank_static(g, &q, nullptr, R.p, &st));  // builds numbering and graph
+    PRDF_TRY(prdf_pagerank_static(g, &q, nullptr, R.p, &st));  // timed
+    const float ms = st.ms_iterate / (float)st.iterations;
+    if (c == 0 || ms < best_ms) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  PRDF_TRY(prdf_graph_set_thresholds(g, PRDF_IN, (int)cand[best][0], &cand[best][1]));
+  PRDF_TRY(ensure_relabelled(g, false, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  if (best_index) *best_index = best;
+  if (best_ms_per_sweep) *best_ms_per_sweep = best_ms;
+  return PRDF_OK;
+}
+
+int prdf_autotune_tile(prdf_graph* g, const double* S, int K, const prdf_params* p, int sweeps, int* best_tile) {
+  if (!g || !S || K < 1 || sweeps < 1 || !best_tile) {
+    set_error("prdf_autotune_tile: bad arguments");
+    return PRDF_EINVAL;
+  }
+  if (!g->weighted) {
+    set_error("prdf_autotune_tile: the graph has no edge weights");
+    return PRDF_ESTATE;
+  }
+  PRDF_TRY(check_params(p));
+  cudaStream_t s = (cudaStream_t)p->stream;
+  DBuf<double> R;
+  PRDF_TRY(R.alloc((size_t)g->n * K, s));
+  prdf_params q = *p;
+  q.precision = PRDF_FP64;
+  q.max_iter = sweeps;
+  q.tol = 1e-300;
+  const int tiles[4] = {8, 16, 32, 64};
+  float best_ms = 0;
+  *best_tile = 32;
+  for (int i = 0; i < 4; ++i) {
+    if (tiles[i] > 2 * K && i > 0) break;
+    q.tile = tiles[i];
+    prdf_stats st;
+    PRDF_TRY(prdf_pagerank_ppr(g, S, K, R.p, &q, &st));
+    PRDF_TRY(prdf_pagerank_ppr(g, S, K, R.p, &q, &st));
+    if (i == 0 || st.ms_iterate < best_ms) {
+      best_ms = st.ms_iterate;
+      *best_tile = tiles[i];
+    }
   }
   return PRDF_OK;
 }

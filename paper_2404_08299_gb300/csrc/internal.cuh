@@ -59,6 +59,7 @@ struct Relabel {
   DBuf<int32_t> pout;                // out-degree partition of `out` (new ids), for marking
   int64_t pout_count[kMaxThr + 1] = {};
   bool pout_valid = false;
+  uint64_t version = 0;              // bumped on every rebuild
 };
 
 // Per-sweep arguments of the pull rank kernels (Alg. update).
@@ -75,6 +76,12 @@ struct SweepArgs {
   const uint64_t* prev;    // L-inf change of the previous sweep, or null on the first sweep
   double tol;              // the sweep exits at once if *prev <= tol (already converged)
   // DF / DF-P only
+  // device-driven iteration (CUDA graph): when ctl is set the kernel takes
+  // x/xn/resid/prev for iteration it = ctl[0] from xa/xb/resid_base instead
+  const int* ctl;
+  const double* xa;
+  double* xb;
+  uint64_t* resid_base;
   uint8_t* dV;             // affected flags (read; cleared on prune)
   uint8_t* dN;             // expand flags (set when the change exceeds tau_f)
   uint8_t* wrote;          // 1 where this vertex's slot in xn was written by the previous sweep
@@ -133,6 +140,11 @@ int launch_grad_w(const int64_t* off, const int32_t* adj, const int32_t* perm, c
 int ppr_narrow(const double* x, int64_t cnt, float* y, cudaStream_t s);
 int ppr_widen(const float* y, int64_t cnt, double* x, cudaStream_t s);
 
+// One-thread iteration check of the graph-driven loop: it = ctl[0]; stop when
+// resid[it] <= tol or it + 1 >= max_iter; ctl[0] = it + 1; sets the while condition.
+int launch_iter_check(int* ctl, const uint64_t* resid_base, double tol, int max_iter,
+                      cudaGraphConditionalHandle h, cudaStream_t s);
+
 // Launch one rank sweep (all degree classes) for Static (dynamic = false) or DF/DF-P.
 int launch_sweep(const SweepArgs& a, const PartThr& t, const int64_t* class_begin, bool exact, bool dynamic,
                  cudaStream_t s);
@@ -169,6 +181,10 @@ struct prdf_graph {
   prdf::DBuf<uint64_t> resid;
   prdf::DBuf<uint8_t> dV, dN, wrote;
   prdf::DBuf<unsigned long long> counter;
+  prdf::DBuf<int> ctl;               // device iteration counter of the graph-driven loop
+  cudaStream_t cap_stream = nullptr; // private stream used to capture graph bodies
+  cudaGraphExec_t static_exec = nullptr;
+  uint64_t static_key[8] = {};       // what static_exec was built for
   prdf::Relabel rl;                  // class-contiguous copy used by the sweeps
   // weighted graphs: transition probabilities P_uv = w_uv / sum_k w_uk
   bool ppr_valid = false;

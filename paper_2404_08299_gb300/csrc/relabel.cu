@@ -138,6 +138,7 @@ int build_relabelled(prdf_graph* g, cudaStream_t s) {
   PRDF_LAUNCH_CHECK();
   r.valid = true;
   r.pout_valid = false;
+  ++r.version;
   g->ppr_valid = false;
   return PRDF_OK;
 }

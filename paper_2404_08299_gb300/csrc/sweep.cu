@@ -201,6 +201,26 @@ __device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v,
   return dbits(dr);
 }
 
+// per-iteration pointers of the graph-driven loop
+__device__ __forceinline__ SweepArgs resolve(const SweepArgs& in) {
+  if (!in.ctl) return in;
+  SweepArgs a = in;
+  const int it = in.ctl[0];
+  a.x = (it & 1) ? in.xb : in.xa;
+  a.xn = (it & 1) ? const_cast<double*>(in.xa) : in.xb;
+  a.resid = in.resid_base + it;
+  a.prev = it > 0 ? in.resid_base + it - 1 : nullptr;
+  return a;
+}
+
+__global__ void k_iter_check(int* ctl, const uint64_t* resid_base, double tol, int max_iter,
+                             cudaGraphConditionalHandle h) {
+  const int it = ctl[0];
+  const bool done = bitsd(resid_base[it]) <= tol || it + 1 >= max_iter;
+  ctl[0] = it + 1;
+  cudaGraphSetConditional(h, done ? 0u : 1u);
+}
+
 // DF / DF-P: an unaffected vertex keeps its rank; its slot in xn is stale
 // only if the previous sweep wrote it (then copy it through).
 __device__ __forceinline__ bool skip_unaffected(const SweepArgs& a, int32_t v) {
@@ -243,7 +263,8 @@ struct Item {
 // With self-loops on every vertex, a row of length 1 is [v] itself and needs
 // no offsets or indices.
 template <int G, int U, bool EXACT, bool DYN, bool SELF1>
-__global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a, int64_t begin, int64_t end) {
+__global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, int64_t begin, int64_t end) {
+  const SweepArgs a = resolve(a_in);
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
   constexpr int kGroupsPerWarp = 32 / G;
@@ -324,7 +345,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a, int
 // one warp per vertex, 16-byte index loads; the next vertex's list entry and
 // row offsets are loaded while the current row is gathered
 template <int KV, bool EXACT, bool DYN>
-__global__ void __launch_bounds__(kThreads) k_sweep_warp(const SweepArgs a, int64_t begin, int64_t end) {
+__global__ void __launch_bounds__(kThreads) k_sweep_warp(const SweepArgs a_in, int64_t begin, int64_t end) {
+  const SweepArgs a = resolve(a_in);
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
   const int lane = threadIdx.x & 31;
@@ -358,7 +380,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep_warp(const SweepArgs a, int6
 
 // one block per vertex (high in-degree)
 template <int KV, bool EXACT, bool DYN>
-__global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a, int64_t begin, int64_t end) {
+__global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a_in, int64_t begin, int64_t end) {
+  const SweepArgs a = resolve(a_in);
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
   __shared__ uint32_t s_acc[kThreads / 32][4];
@@ -445,6 +468,13 @@ int launch_all(const SweepArgs& a, const PartThr& t, const int64_t* cb, cudaStre
 }
 
 }  // namespace
+
+int launch_iter_check(int* ctl, const uint64_t* resid_base, double tol, int max_iter,
+                      cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_iter_check<<<1, 1, 0, s>>>(ctl, resid_base, tol, max_iter, h);
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
 
 int launch_sweep(const SweepArgs& a, const PartThr& t, const int64_t* class_begin, bool exact, bool dynamic,
                  cudaStream_t s) {

@@ -84,3 +84,13 @@ def test_ppr_needs_weights_and_columns():
     gw = prdf().Graph(n, dev(s), dev(d), dev(np.ones(len(s), np.float32)))
     with pytest.raises(prdf().PrdfError):
         gw.pagerank_ppr(torch.zeros((n, 2), dtype=torch.float64, device="cuda"), tile=12)
+
+
+def test_autotune_tile_is_valid_and_consistent():
+    n, g, og, w_out = weighted_case(10, 12000, seed=8, hub=False)
+    S = dev(synth.ppr_seeds(n, 24, n_seed=16, seed=9))
+    tile = g.autotune_tile(S, sweeps=2)
+    assert tile in (8, 16, 32, 64)
+    R0, _ = g.pagerank_ppr(S, precision=0, tile=8)
+    R1, _ = g.pagerank_ppr(S, precision=0, tile=tile)
+    assert float((R1 - R0).abs().max()) <= 1e-12

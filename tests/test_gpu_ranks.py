@@ -183,3 +183,14 @@ def test_dfp_all_affected_df_equals_naive_dynamic():
     Rn, stn = oracle.pagerank_static(og, R0=R0)
     assert st.iterations == stn.iterations
     assert np.max(np.abs(host(R) - Rn)) <= 1e-13
+
+
+def test_autotune_keeps_ranks_bit_identical():
+    """The tuner only changes kernel shapes and the vertex numbering; exact accumulation keeps every bit."""
+    n, s, d = synth.rmat(13, 150000, seed=12)
+    g = gpu_graph(n, s, d)
+    R0, st0 = g.pagerank_static()
+    idx, ms = g.autotune(sweeps=3)
+    assert 0 <= idx < 8 and ms > 0
+    R1, st1 = g.pagerank_static()
+    assert torch.equal(R0, R1) and st0.iterations == st1.iterations
