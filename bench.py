@@ -38,6 +38,19 @@ WORKLOADS = {
 }
 
 
+def aggregate_ranks(ms_local, units_local, dist=None):
+    """Replicas: every rank solves its own copy. Returns (max time over ranks, units summed over ranks)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms_local, units_local
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    u = torch.tensor([units_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def make_edges(name):
     import synth
     kind, prm, _ = WORKLOADS[name]
@@ -383,13 +396,9 @@ def main():
     ms_total = e0.elapsed_time(e1)
     clk = clocks.stop()
     iters = sts[-1].iterations
-    ms_step = ms_total / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
     edges_per_step = sum(s.iterations for s in sts) / len(sts) * m
-    value = world * edges_per_step / (ms_step * 1e-3) / 1e9
+    ms_step, edges_all = aggregate_ranks(ms_total / args.steps, edges_per_step, dist)
+    value = edges_all / (ms_step * 1e-3) / 1e9
 
     # roofline of the dominant kernel: the rank sweep. The solve runs as one CUDA graph (a while node
     # around one sweep and a 1-thread convergence check); its event-timed iteration phase divided by the
@@ -422,12 +431,8 @@ def main():
         if k > 0:
             e2e_ms.append(a0.elapsed_time(a1))
         del g2, s_d, d_d, R2
-    e2e_step = sum(e2e_ms) / len(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
-    e2e_val = world * st2.iterations * m / (e2e_step * 1e-3) / 1e9
+    e2e_step, e2e_edges = aggregate_ranks(sum(e2e_ms) / len(e2e_ms), st2.iterations * m, dist)
+    e2e_val = e2e_edges / (e2e_step * 1e-3) / 1e9
 
     if not args.no_extras and args.dfp_sizes:
         extras["dfp"] = measure_dfp(g, n, m, args)
