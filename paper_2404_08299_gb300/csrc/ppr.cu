@@ -160,13 +160,31 @@ __global__ void __launch_bounds__(kThreads) k_ppr32_block(const Ppr32Args a, int
     const int32_t v = (int32_t)i;
     const int64_t b = a.off[v], e = a.off[v + 1];
     Dot2 s0, s1;
-    for (int64_t j = b + slot; j < e; j += kSlots) {
-      const int32_t u = __ldg(a.adj + j);
-      const float p = __ldg(a.P + j);
-      if (colok) {
-        const float* src = a.R + (int64_t)u * a.K + col;
-        s0.add_prod(p, __ldg(src));
-        if (two) s1.add_prod(p, __ldg(src + 1));
+    constexpr int U = 4;  // edges in flight per slot
+    for (int64_t j0 = b + slot; j0 < e; j0 += (int64_t)kSlots * U) {
+      int32_t u[U];
+      float p[U], r0[U], r1[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int64_t j = j0 + (int64_t)k * kSlots;
+        u[k] = j < e ? __ldg(a.adj + j) : -1;
+        p[k] = j < e ? __ldg(a.P + j) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        r0[k] = 0.f;
+        r1[k] = 0.f;
+        if (u[k] >= 0 && colok) {
+          const float* src = a.R + (int64_t)u[k] * a.K + col;
+          r0[k] = __ldg(src);
+          if (two) r1[k] = __ldg(src + 1);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (u[k] < 0) continue;
+        s0.add_prod(p[k], r0[k]);
+        s1.add_prod(p[k], r1[k]);
       }
     }
     ss[slot][2 * lane] = s0.value();
@@ -205,13 +223,32 @@ __global__ void __launch_bounds__(kThreads) k_ppr64_step(const Ppr64Args a, int6
     const int32_t v = (int32_t)i;
     const int64_t b = a.off[v], e = a.off[v + 1];
     double s0 = 0, s1 = 0;
-    for (int64_t j = b + slot; j < e; j += (HUB ? kSlots : 1)) {
-      const int32_t u = __ldg(a.adj + j);
-      const double p = __ldg(a.P + j);
-      if (colok) {
-        const double* src = a.R + (int64_t)u * a.K + col;
-        s0 = fma(p, __ldg(src), s0);
-        if (two) s1 = fma(p, __ldg(src + 1), s1);
+    constexpr int U = 4;  // edges in flight per slot
+    const int64_t stride = HUB ? kSlots : 1;
+    for (int64_t j0 = b + slot; j0 < e; j0 += stride * U) {
+      int32_t u[U];
+      double p[U], r0[U], r1[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int64_t j = j0 + (int64_t)k * stride;
+        u[k] = j < e ? __ldg(a.adj + j) : -1;
+        p[k] = j < e ? __ldg(a.P + j) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        r0[k] = 0.0;
+        r1[k] = 0.0;
+        if (u[k] >= 0 && colok) {
+          const double* src = a.R + (int64_t)u[k] * a.K + col;
+          r0[k] = __ldg(src);
+          if (two) r1[k] = __ldg(src + 1);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (u[k] < 0) continue;
+        s0 = fma(p[k], r0[k], s0);
+        s1 = fma(p[k], r1[k], s1);
       }
     }
     if (HUB) {
