@@ -114,7 +114,7 @@ __device__ __forceinline__ void gather_row(const SweepArgs& a, int64_t b, int64_
 
 // Vectorised variant for a row handled by NT lanes: 16-byte index loads for
 // the aligned body (KV of them in flight per lane), scalar head and tail.
-template <int NT, int KV, bool EXACT>
+template <int NT, int KV, bool EXACT, bool SELF = true>
 __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, int64_t e, int lane, int32_t v,
                                                Acc<EXACT>& acc, uint64_t& xself, uint64_t pf, uint64_t pl) {
   int64_t ba = (b + 3) & ~(int64_t)3;
@@ -129,7 +129,7 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
       const int32_t u = ld_stream_i32(a.adj + j, pf);
       const uint64_t xv = ld_gather_b64(a.x + u, pl);
       acc.add(xv);
-      xself = (u == v) ? xv : xself;
+      if (SELF) xself = (u == v) ? xv : xself;
     }
   }
   // body: the next chunk's indices are loaded while this chunk's gathers are in flight
@@ -163,10 +163,12 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
       acc.add(xv[4 * k + 1]);
       acc.add(xv[4 * k + 2]);
       acc.add(xv[4 * k + 3]);
-      xself = (u4[k].x == v) ? xv[4 * k + 0] : xself;
-      xself = (u4[k].y == v) ? xv[4 * k + 1] : xself;
-      xself = (u4[k].z == v) ? xv[4 * k + 2] : xself;
-      xself = (u4[k].w == v) ? xv[4 * k + 3] : xself;
+      if (SELF) {
+        xself = (u4[k].x == v) ? xv[4 * k + 0] : xself;
+        xself = (u4[k].y == v) ? xv[4 * k + 1] : xself;
+        xself = (u4[k].z == v) ? xv[4 * k + 2] : xself;
+        xself = (u4[k].w == v) ? xv[4 * k + 3] : xself;
+      }
     }
 #pragma unroll
     for (int k = 0; k < KV; ++k) u4[k] = nx[k];
@@ -181,7 +183,6 @@ __device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v,
                                                   uint64_t pf) {
   const double xself = bitsd(xself_b);
   const double d = ld_stream_f64(a.degd + v, pf);
-  const double rold = xself * d;  // R[v] of the previous iteration
   double r;
   if (DYN && a.prune) {
     // Eq. 2: the self-loop term is solved in closed form
@@ -190,8 +191,10 @@ __device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v,
   } else {
     r = fma(a.alpha, c, a.c0);  // Eq. 1
   }
-  const double dr = fabs(r - rold);
+  // |r - R[v]| with R[v] = x[v] * |out(v)| of the previous iteration, one rounding
+  const double dr = fabs(fma(xself, -d, r));
   if (DYN) {
+    const double rold = xself * d;
     const double m = fmax(r, rold);
     if (a.prune && dr <= a.tau_p * m) a.dV[v] = 0;
     if (dr > a.tau_f * m) a.dN[v] = 1;
@@ -362,11 +365,11 @@ __global__ void __launch_bounds__(kThreads) k_sweep_warp(const SweepArgs a_in, i
     bool active = true;
     if (DYN && skip_unaffected(a, v)) active = false;
     Acc<EXACT> acc;
-    uint64_t xself = 0;
-    if (active) gather_row_vec<32, KV, EXACT>(a, b, e, lane, v, acc, xself, pf, pl);
+    // x[v], for R[v] of the previous iteration = x[v] * |out(v)|, issued ahead of the gathers
+    uint64_t xself = (active && lane == 0) ? ld_gather_b64(a.x + v, pl) : 0ull;
+    if (active) gather_row_vec<32, KV, EXACT, false>(a, b, e, lane, v, acc, xself, pf, pl);
     const int64_t bn = vn >= 0 ? ld_stream_i64(a.off + vn, pf) : 0, en = vn >= 0 ? ld_stream_i64(a.off + vn + 1, pf) : 0;
     acc.template group_reduce<32>();
-    xself = warp_max_u64(xself);
     if (active && lane == 0) {
       const uint64_t db = finish_vertex<DYN>(a, v, acc.value(), xself, pf);
       dmax = db > dmax ? db : dmax;
@@ -385,7 +388,6 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a_in, 
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
   __shared__ uint32_t s_acc[kThreads / 32][4];
-  __shared__ uint64_t s_x[kThreads / 32];
   __shared__ int s_skip;
   uint64_t dmax = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -400,23 +402,16 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a_in, 
     }
     const int64_t b = a.off[v], e = a.off[v + 1];
     Acc<EXACT> acc;
-    uint64_t xself = 0;
-    gather_row_vec<kThreads, KV, EXACT>(a, b, e, threadIdx.x, v, acc, xself, pf, pl);
+    // x[v] for R[v] of the previous iteration, read by the thread that finishes the vertex
+    uint64_t xb = (threadIdx.x == 0) ? ld_gather_b64(a.x + v, pl) : 0ull;
+    gather_row_vec<kThreads, KV, EXACT, false>(a, b, e, threadIdx.x, v, acc, xb, pf, pl);
     acc.template group_reduce<32>();
-    const uint64_t xb = warp_max_u64(xself);
-    if (lane == 0) {
-      acc.to_shared(s_acc[wid]);
-      s_x[wid] = xb;
-    }
+    if (lane == 0) acc.to_shared(s_acc[wid]);
     __syncthreads();
     if (threadIdx.x == 0) {
       Acc<EXACT> tot;
-      uint64_t xm = 0;
-      for (int k = 0; k < kThreads / 32; ++k) {
-        tot.from_shared(s_acc[k]);
-        xm = s_x[k] > xm ? s_x[k] : xm;
-      }
-      const uint64_t db = finish_vertex<DYN>(a, v, tot.value(), xm, pf);
+      for (int k = 0; k < kThreads / 32; ++k) tot.from_shared(s_acc[k]);
+      const uint64_t db = finish_vertex<DYN>(a, v, tot.value(), xb, pf);
       dmax = db > dmax ? db : dmax;
     }
     __syncthreads();
