@@ -154,8 +154,8 @@ int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t*
  * degree <= thr[0], class c holds thr[c-1] < degree <= thr[c], the last class
  * degree > thr[n_thr-1]; 1 <= n_thr <= 7. For PRDF_IN the classes select the
  * rank-sweep kernels (the last class one block per vertex, the one before it
- * one warp per vertex, lower classes 1, 4 or 16 lanes per vertex by their
- * upper bound; default thresholds 1, 4, 16, 128, 4096); for PRDF_OUT the
+ * one warp per vertex, lower classes 1, 4, 8 or 16 lanes per vertex by their
+ * upper bound; default thresholds 1, 4, 16, 32, 128, 4096); for PRDF_OUT the
  * marking kernels (thread, 8 lanes, warp, block; default 8, 64, 2048).
  * thr_host: host int64[n_thr], strictly increasing, thr[0] >= 0.
  */

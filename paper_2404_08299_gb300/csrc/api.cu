@@ -827,12 +827,13 @@ int prdf_graph_create(int32_t n, const int32_t* src, const int32_t* dst, const f
   g->weighted = w != nullptr;
   g->stream = s;
   // default class thresholds. In-degree (rank sweep): self-loop only, <= 4,
-  // <= 16 (4 lanes), <= 128 (16 lanes), <= 4096 (warp), block above.
-  // Out-degree (marking): thread <= 8, 8 lanes <= 64, warp <= 2048, block above.
+  // <= 16 (4 lanes), <= 32 (8 lanes), <= 128 (16 lanes), <= 4096 (warp),
+  // block above. Out-degree (marking): thread <= 8, 8 lanes <= 64, warp <=
+  // 2048, block above.
   {
-    const int64_t tin[5] = {1, 4, 16, 128, 4096};
-    g->thr[PRDF_IN].n = 5;
-    for (int i = 0; i < 5; ++i) g->thr[PRDF_IN].thr[i] = tin[i];
+    const int64_t tin[6] = {1, 4, 16, 32, 128, 4096};
+    g->thr[PRDF_IN].n = 6;
+    for (int i = 0; i < 6; ++i) g->thr[PRDF_IN].thr[i] = tin[i];
     const int64_t tout[3] = {8, 64, 2048};
     g->thr[PRDF_OUT].n = 3;
     for (int i = 0; i < 3; ++i) g->thr[PRDF_OUT].thr[i] = tout[i];
@@ -1310,9 +1311,10 @@ int prdf_autotune(prdf_graph* g, const prdf_params* p, int sweeps, int* best_ind
   }
   PRDF_TRY(check_params(p));
   // candidate in-degree class thresholds (the sweep numbering is rebuilt for each)
-  static const int64_t cand[][6] = {
-      {5, 1, 4, 16, 128, 4096}, {3, 1, 16, 4096},   {4, 1, 4, 32, 1024}, {4, 1, 8, 64, 2048},
-      {3, 4, 128, 4096},        {2, 16, 2048},      {1, 4096, 0},         {5, 1, 4, 16, 256, 8192}};
+  static const int64_t cand[][8] = {
+      {6, 1, 4, 16, 32, 128, 4096}, {5, 1, 4, 16, 128, 4096},   {6, 1, 4, 16, 64, 128, 4096},
+      {6, 1, 4, 8, 32, 128, 2048},  {6, 1, 4, 16, 32, 256, 8192}, {4, 1, 4, 32, 1024},
+      {3, 1, 16, 4096},             {2, 16, 2048}};
   const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
   cudaStream_t s = (cudaStream_t)p->stream;
   DBuf<double> R;

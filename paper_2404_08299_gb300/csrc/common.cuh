@@ -161,12 +161,32 @@ struct Fix4 {
     const uint32_t t0 = lo << b;
     const uint32_t t1 = __funnelshift_l(lo, mh, b);
     const uint32_t t2 = __funnelshift_l(mh, 0u, b);
-    uint32_t a0 = w == 0 ? t0 : 0u;
-    uint32_t a1 = w == 0 ? t1 : (w == 1 ? t0 : 0u);
-    uint32_t a2 = w == 0 ? t2 : (w == 1 ? t1 : t0);
-    uint32_t a3 = w == 0 ? 0u : (w == 1 ? t2 : t1);
-    if (!ok) a0 = a1 = a2 = a3 = 0u;
+    const uint32_t ww = ok ? w : 3u;  // 3: a dropped term, every word zero
+    const uint32_t a0 = ww == 0 ? t0 : 0u;
+    const uint32_t a1 = ww == 0 ? t1 : (ww == 1 ? t0 : 0u);
+    const uint32_t a2 = ww == 0 ? t2 : (ww == 1 ? t1 : (ww == 2 ? t0 : 0u));
+    const uint32_t a3 = ww == 1 ? t2 : (ww == 2 ? t1 : 0u);
     add4(a0, a1, a2, a3);
+  }
+
+  // Terms in [2^-40, 2^-8) (biased exponent 983..1014) have their mantissa's
+  // lowest bit in word 1 (w = 1 above): the image is (0, t0, t1, t2) with
+  // b = e - 983, so the word selection and the dropped-term test fall away.
+  // PageRank values of graphs with 2^8 .. 2^36 vertices divided by their
+  // out-degree land in this window.
+  __device__ __forceinline__ static bool in_w1(uint64_t xb) { return (uint32_t)(xb >> 52) - 983u < 32u; }
+  __device__ __forceinline__ void add_w1(uint64_t xb) {
+    const uint32_t hi = (uint32_t)(xb >> 32), lo = (uint32_t)xb;
+    const uint32_t b = (hi >> 20) - 983u;
+    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+    const uint32_t t0 = lo << b;
+    const uint32_t t1 = __funnelshift_l(lo, mh, b);
+    const uint32_t t2 = __funnelshift_l(mh, 0u, b);
+    asm("add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, %2, %5;"
+        : "+r"(w1), "+r"(w2), "+r"(w3)
+        : "r"(t0), "r"(t1), "r"(t2));
   }
 
   __device__ __forceinline__ void add_words(const uint32_t* s) { add4(s[0], s[1], s[2], s[3]); }

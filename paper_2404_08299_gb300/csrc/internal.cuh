@@ -30,6 +30,10 @@ int exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, Workspace& ws
 // Alg. partition over the rows of a CSR (degree = off[v+1] - off[v]).
 int partition_by_degree(const int64_t* off, int64_t n, const PartThr& t, int32_t* P, int64_t* counts_host,
                         Workspace& ws, cudaStream_t s);
+// Stable partition of a list of vertex ids (in = NULL: 0..n-1) by the degree
+// classes of off; desc puts the highest class first. P may not alias in.
+int partition_list(const int64_t* off, const int32_t* in, int64_t n, const PartThr& t, bool desc, int32_t* P,
+                   int64_t* counts_host, Workspace& ws, cudaStream_t s);
 
 // A device CSR with optional float weights.
 struct Csr {

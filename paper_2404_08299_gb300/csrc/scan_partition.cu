@@ -123,14 +123,24 @@ struct Packed2 {
   __device__ __forceinline__ int64_t get(int c) const { return (int64_t)((p[c >> 2] >> (16 * (c & 3))) & 0xFFFF); }
 };
 
-// count[c * ntiles + tile] = number of vertices of class c in the tile
-__global__ void k_part_count(const int64_t* __restrict__ off, int64_t n, PartThr t, int64_t* __restrict__ count) {
+// Class of list entry i: vertex v = in[i] (in = NULL: v = i) classed by its
+// degree; desc reverses the class order (highest degrees first).
+__device__ __forceinline__ int entry_class(const int64_t* __restrict__ off, const int32_t* __restrict__ in, int64_t i,
+                                           const PartThr& t, bool desc) {
+  const int64_t v = in ? in[i] : i;
+  const int c = degree_class(off[v + 1] - off[v], t);
+  return desc ? t.n - c : c;
+}
+
+// count[c * ntiles + tile] = number of list entries of class c in the tile
+__global__ void k_part_count(const int64_t* __restrict__ off, const int32_t* __restrict__ in, int64_t n, PartThr t,
+                             bool desc, int64_t* __restrict__ count) {
   const int64_t base = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartItems;
   Packed2 pk;
 #pragma unroll
   for (int k = 0; k < kPartItems; ++k) {
-    const int64_t v = base + k;
-    if (v < n) pk.add(degree_class(off[v + 1] - off[v], t));
+    const int64_t i = base + k;
+    if (i < n) pk.add(entry_class(off, in, i, t, desc));
   }
   __shared__ uint64_t tot0, tot1;
   block_exclusive_scan<uint64_t>(pk.p[0], &tot0);
@@ -143,16 +153,16 @@ __global__ void k_part_count(const int64_t* __restrict__ off, int64_t n, PartThr
   }
 }
 
-// P[base[c][tile] + rank within tile] = v, ranks in ascending vertex order (stable).
-__global__ void k_part_scatter(const int64_t* __restrict__ off, int64_t n, PartThr t, const int64_t* __restrict__ base,
-                               int32_t* __restrict__ P) {
+// P[base[c][tile] + rank within tile] = entry, ranks in list order (stable).
+__global__ void k_part_scatter(const int64_t* __restrict__ off, const int32_t* __restrict__ in, int64_t n, PartThr t,
+                               bool desc, const int64_t* __restrict__ base, int32_t* __restrict__ P) {
   const int64_t first = (int64_t)blockIdx.x * kPartTile + (int64_t)threadIdx.x * kPartItems;
   int cls[kPartItems];
   Packed2 pk;
 #pragma unroll
   for (int k = 0; k < kPartItems; ++k) {
-    const int64_t v = first + k;
-    cls[k] = v < n ? degree_class(off[v + 1] - off[v], t) : -1;
+    const int64_t i = first + k;
+    cls[k] = i < n ? entry_class(off, in, i, t, desc) : -1;
     if (cls[k] >= 0) pk.add(cls[k]);
   }
   __shared__ uint64_t tot0, tot1;
@@ -164,7 +174,7 @@ __global__ void k_part_scatter(const int64_t* __restrict__ off, int64_t n, PartT
     if (cls[k] < 0) continue;
     const int c = cls[k];
     const int64_t pos = base[(int64_t)c * gridDim.x + blockIdx.x] + ex.get(c);
-    P[pos] = (int32_t)(first + k);
+    P[pos] = in ? in[first + k] : (int32_t)(first + k);
     ex.add(c);
   }
 }
@@ -201,6 +211,11 @@ int exclusive_scan_i64(const int64_t* in, int64_t n, int64_t* out, Workspace& ws
 
 int partition_by_degree(const int64_t* off, int64_t n, const PartThr& t, int32_t* P, int64_t* counts_host,
                         Workspace& ws, cudaStream_t s) {
+  return partition_list(off, nullptr, n, t, false, P, counts_host, ws, s);
+}
+
+int partition_list(const int64_t* off, const int32_t* in, int64_t n, const PartThr& t, bool desc, int32_t* P,
+                   int64_t* counts_host, Workspace& ws, cudaStream_t s) {
   const int64_t nt = (n + kPartTile - 1) / kPartTile;
   const int C = t.n + 1;
   if (nt == 0) {
@@ -209,10 +224,10 @@ int partition_by_degree(const int64_t* off, int64_t n, const PartThr& t, int32_t
   }
   PRDF_TRY(ws.part_cnt.reserve((size_t)C * nt, s));
   PRDF_TRY(ws.part_base.reserve((size_t)C * nt + 1, s));
-  k_part_count<<<(unsigned)nt, kScanThreads, 0, s>>>(off, n, t, ws.part_cnt.p);
+  k_part_count<<<(unsigned)nt, kScanThreads, 0, s>>>(off, in, n, t, desc, ws.part_cnt.p);
   PRDF_LAUNCH_CHECK();
   PRDF_TRY(exclusive_scan_i64(ws.part_cnt.p, C * nt, ws.part_base.p, ws, s));
-  k_part_scatter<<<(unsigned)nt, kScanThreads, 0, s>>>(off, n, t, ws.part_base.p, P);
+  k_part_scatter<<<(unsigned)nt, kScanThreads, 0, s>>>(off, in, n, t, desc, ws.part_base.p, P);
   PRDF_LAUNCH_CHECK();
   // class sizes from the class boundaries of the flattened scan
   int64_t* hb = ws.host_i64;
@@ -310,11 +325,11 @@ extern "C" int prdf_partition_noalloc(const int64_t* off, int32_t n, int n_thr, 
   int64_t* base = scratch + kNoAllocCnt;
   int64_t* sums = base + kNoAllocCnt + 1;
   const int64_t nt2 = (cn + kScanTile - 1) / kScanTile;
-  k_part_count<<<(unsigned)nt, kScanThreads, 0, s>>>(off, n, t, cnt);
+  k_part_count<<<(unsigned)nt, kScanThreads, 0, s>>>(off, nullptr, n, t, false, cnt);
   k_tile_sums<int64_t><<<(unsigned)nt2, kScanThreads, 0, s>>>(cnt, cn, sums);
   k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(sums, nt2);
   k_scan_apply<int64_t><<<(unsigned)nt2, kScanThreads, 0, s>>>(cnt, cn, sums, base);
-  k_part_scatter<<<(unsigned)nt, kScanThreads, 0, s>>>(off, n, t, base, P);
+  k_part_scatter<<<(unsigned)nt, kScanThreads, 0, s>>>(off, nullptr, n, t, false, base, P);
   PRDF_LAUNCH_CHECK();
   int64_t hb[kNoAllocMaxThr + 2];
   for (int c = 0; c <= C; ++c)

@@ -35,6 +35,9 @@ template <>
 struct Acc<true> {
   Fix4 v;
   __device__ __forceinline__ void add(uint64_t xb) { v.add(xb); }
+  // add_w1: only for terms with in_w1 (the common window, three-word add)
+  __device__ __forceinline__ static bool in_w1(uint64_t xb) { return Fix4::in_w1(xb); }
+  __device__ __forceinline__ void add_w1(uint64_t xb) { v.add_w1(xb); }
   __device__ __forceinline__ void merge(const Acc& o) { v.add4(o.v.w0, o.v.w1, o.v.w2, o.v.w3); }
   __device__ __forceinline__ Acc shfl_up(int o) const {
     Acc r;
@@ -63,6 +66,8 @@ template <>
 struct Acc<false> {
   double v = 0;
   __device__ __forceinline__ void add(uint64_t xb) { v += bitsd(xb); }
+  __device__ __forceinline__ static bool in_w1(uint64_t) { return true; }
+  __device__ __forceinline__ void add_w1(uint64_t xb) { v += bitsd(xb); }
   __device__ __forceinline__ void merge(const Acc& o) { v += o.v; }
   __device__ __forceinline__ Acc shfl_up(int o) const {
     Acc r;
@@ -132,16 +137,18 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
       if (SELF) xself = (u == v) ? xv : xself;
     }
   }
-  // body: the next chunk's indices are loaded while this chunk's gathers are in flight
+  // body: the next chunk's indices are loaded while this chunk's gathers are
+  // in flight. The loop runs the same trip count on all NT lanes, so each
+  // warp is converged at the vote below.
   const int64_t step = 4 * (int64_t)NT * KV;
-  int64_t q0 = ba + 4 * (int64_t)lane;
   int4 u4[KV];
 #pragma unroll
   for (int k = 0; k < KV; ++k) {
-    const int64_t q = q0 + 4 * (int64_t)NT * k;
+    const int64_t q = ba + 4 * (int64_t)lane + 4 * (int64_t)NT * k;
     u4[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
   }
-  for (; q0 < ea; q0 += step) {
+  for (int64_t base = ba; base < ea; base += step) {
+    const int64_t q0 = base + 4 * (int64_t)lane;
     uint64_t xv[4 * KV];
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
@@ -156,13 +163,29 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
       const int64_t q = q0 + step + 4 * (int64_t)NT * k;
       nx[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
     }
+    bool w1 = true;
+#pragma unroll
+    for (int k = 0; k < KV; ++k)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w1 = w1 && (u4[k].x < 0 || Acc<EXACT>::in_w1(xv[4 * k + q]));
+    if (__all_sync(0xffffffffu, w1)) {
+#pragma unroll
+      for (int k = 0; k < KV; ++k) {
+        if (u4[k].x < 0) continue;  // a whole int4 is valid or not
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc.add_w1(xv[4 * k + q]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < KV; ++k) {
+        if (u4[k].x < 0) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc.add(xv[4 * k + q]);
+      }
+    }
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
-      if (u4[k].x < 0) continue;  // a whole int4 is valid or not
-      acc.add(xv[4 * k + 0]);
-      acc.add(xv[4 * k + 1]);
-      acc.add(xv[4 * k + 2]);
-      acc.add(xv[4 * k + 3]);
+      if (u4[k].x < 0) continue;
       if (SELF) {
         xself = (u4[k].x == v) ? xv[4 * k + 0] : xself;
         xself = (u4[k].y == v) ? xv[4 * k + 1] : xself;
@@ -314,16 +337,28 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, 
     load_item(v_next, nxt);
     v_next = load_v(base + 2 * step + gw);
 
+    // the warp is converged here (uniform loop): one vote picks the
+    // three-word add when every gathered term of the step is in the common window
+    bool w1 = true;
+#pragma unroll
+    for (int k = 0; k < U; ++k) w1 = w1 && (cur.u[k] < 0 || Acc<EXACT>::in_w1(xv[k]));
+    const bool all_w1 = __all_sync(0xffffffffu, w1);
     bool active = cur.v >= 0;
     if (DYN && active && skip_unaffected(a, cur.v)) active = false;
     Acc<EXACT> acc;
     uint64_t xself = 0;
     if (active) {
+      if (all_w1) {
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        if (cur.u[k] >= 0) acc.add(xv[k]);
-        xself = (cur.u[k] == cur.v) ? xv[k] : xself;
+        for (int k = 0; k < U; ++k)
+          if (cur.u[k] >= 0) acc.add_w1(xv[k]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+          if (cur.u[k] >= 0) acc.add(xv[k]);
       }
+#pragma unroll
+      for (int k = 0; k < U; ++k) xself = (cur.u[k] == cur.v) ? xv[k] : xself;
       // rest of a row longer than G*U (not reached with the default classes)
       if (!SELF1 && cur.e - cur.b > (int64_t)G * U)
         gather_row<G, U, EXACT>(a, cur.b + (int64_t)G * U, cur.e, lane, cur.v, acc, xself, pf, pl);
@@ -421,7 +456,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a_in, 
 
 // Kernel shape of class c: the last class is block-per-vertex, the one before
 // it warp-per-vertex; lower classes by their upper degree bound.
-enum Kind { kT1 = 0, kT4, kG4, kG16, kWarp, kBlock };
+enum Kind { kT1 = 0, kT4, kG4, kG8, kG16, kG16U8, kWarp, kBlock };
 
 Kind class_kind(const PartThr& t, int c) {
   const int C = t.n + 1;
@@ -431,12 +466,38 @@ Kind class_kind(const PartThr& t, int c) {
   if (hi <= 1) return kT1;
   if (hi <= 4) return kT4;
   if (hi <= 16) return kG4;
-  if (hi <= 128) return kG16;
+  if (hi <= 32) return kG8;
+  // 16 lanes; 8 indices per lane only when every row of the class is longer than 64
+  if (hi <= 128) return (c > 0 && t.thr[c - 1] >= 64) ? kG16U8 : kG16;
   return kWarp;
+}
+
+// The sweep kernels use almost no shared memory: give the unified L1 /
+// shared storage to L1, which holds the gathered x of the hottest sources.
+template <typename K>
+void prefer_l1(K k) {
+  // a preference the driver declines is not an error: clear what this call set
+  if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 0) != cudaSuccess) cudaGetLastError();
+}
+
+template <bool EXACT, bool DYN>
+bool prefer_l1_all() {
+  prefer_l1(k_sweep_group<1, 1, EXACT, DYN, true>);
+  prefer_l1(k_sweep_group<1, 1, EXACT, DYN, false>);
+  prefer_l1(k_sweep_group<1, 4, EXACT, DYN, false>);
+  prefer_l1(k_sweep_group<4, 4, EXACT, DYN, false>);
+  prefer_l1(k_sweep_group<8, 4, EXACT, DYN, false>);
+  prefer_l1(k_sweep_group<16, 4, EXACT, DYN, false>);
+  prefer_l1(k_sweep_group<16, 8, EXACT, DYN, false>);
+  prefer_l1(k_sweep_warp<2, EXACT, DYN>);
+  prefer_l1(k_sweep_block<4, EXACT, DYN>);
+  return true;
 }
 
 template <bool EXACT, bool DYN>
 int launch_all(const SweepArgs& a, const PartThr& t, const int64_t* cb, cudaStream_t s) {
+  static const bool carveout_set = prefer_l1_all<EXACT, DYN>();
+  (void)carveout_set;
   const int maxg = kSMs * 8;
   const int C = t.n + 1;
   for (int c = 0; c < C; ++c) {
@@ -453,7 +514,9 @@ int launch_all(const SweepArgs& a, const PartThr& t, const int64_t* cb, cudaStre
         break;
       case kT4: k_sweep_group<1, 4, EXACT, DYN, false><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kG4: k_sweep_group<4, 4, EXACT, DYN, false><<<grid_for(cnt * 4, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      case kG16: k_sweep_group<16, 8, EXACT, DYN, false><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG8: k_sweep_group<8, 4, EXACT, DYN, false><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG16: k_sweep_group<16, 4, EXACT, DYN, false><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG16U8: k_sweep_group<16, 8, EXACT, DYN, false><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kWarp: k_sweep_warp<2, EXACT, DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       default: k_sweep_block<4, EXACT, DYN><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e); break;
     }
