@@ -54,6 +54,12 @@ __global__ void k_init_x(const double* __restrict__ R0, const int32_t* __restric
   }
 }
 
+// Eq. 2 factor per vertex, 1 / (1 - alpha / |out(i)|)
+__global__ void k_eq2_factor(const double* __restrict__ deg, int32_t n, double alpha, double* __restrict__ kf) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    kf[i] = 1.0 / (1.0 - alpha / deg[i]);
+}
+
 // FP32 stage set-up: y[i] = R0[perm[i]] / |out| (R0 = NULL: 1/n) and FP32 degrees
 __global__ void k_init_y(const double* __restrict__ R0, const int32_t* __restrict__ perm, int32_t n,
                          const double* __restrict__ deg, const double* __restrict__ inv, float* __restrict__ y,
@@ -345,6 +351,7 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
   a.adj = rl.in.adj.p;
   a.degd = rl.degd.p;
   a.inv_deg = rl.inv_deg.p;
+  a.kf = rl.kf.p;
   a.alpha = p->alpha;
   a.c0 = (1.0 - p->alpha) / (double)n;
   a.self_loops = g->self_loops ? 1 : 0;
@@ -1098,7 +1105,14 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
   // partitions: G' by in-degree is the sweep numbering; G by out-degree (for marking) per call
   g->rl.pout_valid = false;
   PRDF_TRY(ensure_relabelled(g, true, s));
-  const Relabel& rl = g->rl;
+  Relabel& rl = g->rl;
+  if (p->prune && rl.kf_alpha != p->alpha) {
+    // Eq. 2's per-vertex factor, kept until the numbering or alpha changes
+    PRDF_TRY(rl.kf.reserve((size_t)n, s));
+    k_eq2_factor<<<grid_for(n, kThreads), kThreads, 0, s>>>(rl.degd.p, n, p->alpha, rl.kf.p);
+    PRDF_LAUNCH_CHECK();
+    rl.kf_alpha = p->alpha;
+  }
   k_init_x<<<grid_for(n, kThreads), kThreads, 0, s>>>(prev_ranks, rl.perm.p, n, rl.inv_deg.p, g->xa.p, g->xb.p);
   PRDF_LAUNCH_CHECK();
   PRDF_CUDA(cudaEventRecord(t.e[1], s));

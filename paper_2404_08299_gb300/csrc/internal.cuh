@@ -60,6 +60,8 @@ struct Relabel {
   DBuf<int32_t> inv;                 // old -> new
   Csr in, out;                       // G' and G in the new numbering
   DBuf<double> degd, inv_deg;        // |out(i)| and 1/|out(i)| in the new numbering
+  DBuf<double> kf;                   // Eq. 2 factor 1 / (1 - alpha / |out(i)|) for kf_alpha
+  double kf_alpha = -1;              // alpha kf was made for (< 0: none)
   DBuf<int32_t> pout;                // out-degree partition of `out` (new ids), for marking
   int64_t pout_count[kMaxThr + 1] = {};
   bool pout_valid = false;
@@ -74,6 +76,7 @@ struct SweepArgs {
   double* xn;              // next x
   const double* degd;      // |out(v)| (self-loop included), as a double
   const double* inv_deg;   // 1 / |out(v)|
+  const double* kf;        // DF-P: 1 / (1 - alpha / |out(v)|) (Eq. 2's self-loop factor)
   double alpha, c0;        // damping, (1 - alpha) / n
   int self_loops;          // every vertex has exactly one self-loop (graph built with PRDF_ADD_SELF_LOOPS)
   uint64_t* resid;         // L-inf change of this sweep (bits of a non-negative double), atomic max

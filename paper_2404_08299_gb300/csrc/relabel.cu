@@ -151,6 +151,7 @@ int build_relabelled(prdf_graph* g, cudaStream_t s) {
   k_perm_degrees<<<grid_for(n, kThreads), kThreads, 0, s>>>(g->outdeg.p, g->inv_outdeg.p, r.perm.p, n, r.degd.p,
                                                             r.inv_deg.p);
   PRDF_LAUNCH_CHECK();
+  r.kf_alpha = -1;
   r.valid = true;
   r.pout_valid = false;
   ++r.version;

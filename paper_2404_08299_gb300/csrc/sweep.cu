@@ -208,9 +208,8 @@ __device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v,
   const double d = ld_stream_f64(a.degd + v, pf);
   double r;
   if (DYN && a.prune) {
-    // Eq. 2: the self-loop term is solved in closed form
-    const double kf = 1.0 / (1.0 - a.alpha / d);
-    r = kf * (a.c0 + a.alpha * (c - xself));
+    // Eq. 2: the self-loop term is solved in closed form (factor precomputed per vertex)
+    r = ld_stream_f64(a.kf + v, pf) * (a.c0 + a.alpha * (c - xself));
   } else {
     r = fma(a.alpha, c, a.c0);  // Eq. 1
   }
