@@ -319,6 +319,7 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="build the graph and run one solve capped at --max-iter sweeps (for ncu captures)")
     ap.add_argument("--max-iter", type=int, default=500)
+    ap.add_argument("--tile", type=int, default=0, help="column tile of the K-column calls (0: default)")
     ap.add_argument("--profile-ppr", action="store_true",
                     help="build the 2^22 weighted graph and run a few K=64 PPR sweeps (for ncu captures)")
     args = ap.parse_args()
@@ -344,7 +345,8 @@ def main():
         w = synth.edge_weights(s2, d2, seed=1)
         g = prdf.Graph(n, torch.from_numpy(s2).cuda(), torch.from_numpy(d2).cuda(), torch.from_numpy(w).cuda())
         S = torch.from_numpy(synth.ppr_seeds(n, 64, n_seed=16, seed=2)).cuda()
-        R, st = g.pagerank_ppr(S, precision=prdf.PRDF_FP32_REFINE, max_iter=args.max_iter, check_every=args.max_iter)
+        R, st = g.pagerank_ppr(S, precision=prdf.PRDF_FP32_REFINE, max_iter=args.max_iter, check_every=args.max_iter,
+                               tile=args.tile)
         torch.cuda.synchronize()
         print(json.dumps({"profile_ppr": True, "n": n, "m": g.m, "sweeps": st.iterations}), flush=True)
         return 0

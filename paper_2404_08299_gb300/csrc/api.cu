@@ -494,7 +494,7 @@ int iterate32(prdf_graph* g, const prdf_params* p, int* iters, int* final_buf, l
   return PRDF_OK;
 }
 
-int auto_tile(int K) { return K >= 32 ? 32 : (K > 8 ? 16 : 8); }
+int auto_tile(int K) { return K >= 64 ? 64 : (K >= 32 ? 32 : (K > 8 ? 16 : 8)); }
 
 // the K-column fixed-point operator: forward pull over G' (P on in-slots) or
 // adjoint pull over G (P on out-slots)
@@ -503,7 +503,8 @@ struct KOp {
   const int32_t* adj;
   const float* p32;
   const double* p64;
-  int64_t hub_begin;
+  int64_t hub_begin;  // first vertex of the two highest in-degree classes
+  const PprHubTable* hub;  // chunks of the highest class's rows of this CSR
   const double* S64;  // right-hand side of the FP64 step
 };
 
@@ -514,12 +515,34 @@ int64_t hub_begin(const Relabel& rl) {
   return C >= 3 ? cb[C - 2] : cb[C - 1];
 }
 
+int64_t blk_begin(const Relabel& rl) {
+  const int C = rl.thr.n + 1;
+  int64_t cb[kMaxThr + 2];
+  begins_from_counts(rl.count, C, cb);
+  return cb[C - 1];
+}
+
+// kernels of one K-column FP32 tile: groups, warps, hub partials and hub finish
+int ppr32_kernels(int64_t hub_b, int64_t blk_b, int64_t n) {
+  return (hub_b > 0 ? 1 : 0) + (blk_b > hub_b ? 1 : 0) + (n > blk_b ? 2 : 0);
+}
+
+// chunk table of the highest in-degree class's rows of one CSR, rebuilt when the numbering changes
+int ensure_hub(prdf_graph* g, const Csr& c, PprHubTable& t, cudaStream_t s) {
+  if (t.valid && t.version == g->rl.version) return PRDF_OK;
+  PRDF_TRY(build_ppr_hub(c.off.p, blk_begin(g->rl), g->n, t, g->ws, s));
+  t.version = g->rl.version;
+  t.valid = true;
+  return PRDF_OK;
+}
+
 // FP32 K-column solve of R = alpha P^T R + (1 - alpha) rhs from the start held
 // in *cur; on return *cur holds the result (the other buffer is scratch).
 int ppr32_solve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, const float* rhs, float** cur,
                 float** other, int max_iter, int* iters, long long* kernels, cudaStream_t s) {
   PRDF_TRY(g->resid32.reserve(2 * ((size_t)max_iter + 1), s));
   PRDF_CUDA(cudaMemsetAsync(g->resid32.p, 0, sizeof(uint32_t) * 2 * ((size_t)max_iter + 1), s));
+  PRDF_TRY(g->ppr_part.reserve((size_t)(op.hub->nchunk > 0 ? op.hub->nchunk : 1) * (size_t)tile, s));
   Ppr32Args a;
   memset(&a, 0, sizeof(a));
   a.off = op.off;
@@ -542,7 +565,7 @@ int ppr32_solve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int t
       a.Rn = buf[(i + 1) & 1];
       a.resid = g->resid32.p + 2 * i;
       a.prev = i > 0 ? g->resid32.p + 2 * (i - 1) : nullptr;
-      PRDF_TRY(launch_ppr32_sweep(a, tile, g->n, hb, s));
+      PRDF_TRY(launch_ppr32_sweep(a, tile, g->n, hb, op.hub->view(), g->ppr_part.p, s));
     }
     launched = upto;
     PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid32.p + 2 * (launched - 1), 2 * sizeof(uint32_t),
@@ -572,7 +595,7 @@ int ppr32_solve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int t
   *cur = buf[(k + 1) & 1];
   *other = buf[k & 1];
   const int tiles = (K + tile - 1) / tile;
-  *kernels += (long long)launched * tiles * 2;
+  *kernels += (long long)launched * tiles * ppr32_kernels(hb, op.hub->begin, g->n);
   return PRDF_OK;
 }
 
@@ -1189,7 +1212,8 @@ int prdf_pagerank_ppr(prdf_graph* g, const double* S, int K, double* R, const pr
   k_rows_gather<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(S, g->rl.perm.p, g->n, K, g->S64.p);
   PRDF_LAUNCH_CHECK();
   PRDF_CUDA(cudaEventRecord(t.e[1], s));
-  const KOp op{g->rl.in.off.p, g->rl.in.adj.p, g->pin32.p, g->pin64.p, hub_begin(g->rl), g->S64.p};
+  PRDF_TRY(ensure_hub(g, g->rl.in, g->hub_in, s));
+  const KOp op{g->rl.in.off.p, g->rl.in.adj.p, g->pin32.p, g->pin64.p, hub_begin(g->rl), &g->hub_in, g->S64.p};
   KSolve ks;
   ks.kernels = 1;
   double* Rfinal = nullptr;
@@ -1284,7 +1308,8 @@ int prdf_pagerank_backward(prdf_graph* g, const double* R, const double* G, int 
   k_rows_gather_scaled<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(G, g->rl.perm.p, g->n, K, 1.0 / beta, g->S64.p);
   PRDF_LAUNCH_CHECK();
   PRDF_CUDA(cudaEventRecord(t.e[1], s));
-  const KOp op{g->rl.out.off.p, g->rl.out.adj.p, g->pout32.p, g->pout64.p, hub_begin(g->rl), g->S64.p};
+  PRDF_TRY(ensure_hub(g, g->rl.out, g->hub_out, s));
+  const KOp op{g->rl.out.off.p, g->rl.out.adj.p, g->pout32.p, g->pout64.p, hub_begin(g->rl), &g->hub_out, g->S64.p};
   KSolve ks;
   ks.kernels = 1;
   double* lam = nullptr;

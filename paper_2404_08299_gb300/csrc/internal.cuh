@@ -138,7 +138,32 @@ struct Ppr64Args {
   double alpha, beta, inv_beta;
   uint64_t* dmax;          // max |T(R) - R| (FP64 bits, atomic max)
 };
-int launch_ppr32_sweep(const Ppr32Args& a, int tile, int64_t n, int64_t hub_begin, cudaStream_t s);
+// Rows of the highest in-degree class of the K-column calls are cut into
+// chunks of kHubChunk edges: chunk c covers edges [chunk_j0[c], +kHubChunk)
+// of vertex begin + chunk_hub[c]; the chunks of hub i are
+// [hub_first[i], hub_first[i + 1]) in row order.
+constexpr int64_t kHubChunk = 1024;
+struct PprHub {
+  int64_t begin, nhub, nchunk;
+  const int32_t* chunk_hub;
+  const int64_t* chunk_j0;
+  const int64_t* hub_first;
+};
+struct PprHubTable {
+  int64_t begin = 0, nhub = 0, nchunk = 0;
+  DBuf<int32_t> chunk_hub;
+  DBuf<int64_t> chunk_j0, hub_first;
+  uint64_t version = 0;  // numbering version it was built for
+  bool valid = false;
+  PprHub view() const { return PprHub{begin, nhub, nchunk, chunk_hub.p, chunk_j0.p, hub_first.p}; }
+};
+int build_ppr_hub(const int64_t* off, int64_t begin, int64_t n, PprHubTable& t, Workspace& ws, cudaStream_t s);
+
+// FP32 sweep over tiles of `tile` columns: vertices [0, hub_begin) one per
+// slot, [hub_begin, h.begin) a warp each, the hub rows in chunks (part:
+// h.nchunk * tile float2 scratch).
+int launch_ppr32_sweep(const Ppr32Args& a, int tile, int64_t n, int64_t hub_begin, const PprHub& h, float2* part,
+                       cudaStream_t s);
 int launch_ppr64_step(const Ppr64Args& a, int tile, int64_t n, int64_t hub_begin, cudaStream_t s);
 int ppr_add_correction(double* R, const float* E, int64_t cnt, cudaStream_t s);
 int launch_grad_w(const int64_t* off, const int32_t* adj, const int32_t* perm, const int64_t* orig_off,
@@ -183,6 +208,8 @@ struct prdf_graph {
   prdf::Workspace ws;
   // solver scratch
   prdf::DBuf<double> xa, xb;
+  prdf::PprHubTable hub_in, hub_out;  // chunk tables of the K-column calls (G' and G)
+  prdf::DBuf<float2> ppr_part;        // chunk partial sums of one column tile
   prdf::DBuf<float> ya, yb, degf, invf;  // FP32 stage state and degrees (class-contiguous numbering)
   prdf::DBuf<uint32_t> resid32;
   prdf::DBuf<uint64_t> resid;

@@ -19,25 +19,43 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// compensated FP32 dot product accumulator
+// Compensated FP32 sum (s + e): TwoSum folds each term's rounding error into e.
 struct Dot2 {
   float s = 0.f, e = 0.f;
-  __device__ __forceinline__ void add_prod(float p, float r) {
-    const float h = p * r;
-    const float eh = fmaf(p, r, -h);
-    const float t = s + h;
-    const float bp = t - s;
-    e += ((s - (t - bp)) + (h - bp)) + eh;
-    s = t;
-  }
   __device__ __forceinline__ void add(float y) {
     const float t = s + y;
     const float bp = t - s;
     e += (s - (t - bp)) + (y - bp);
     s = t;
   }
+  __device__ __forceinline__ void merge(const Dot2& o) {
+    add(o.s);
+    e += o.e;
+  }
   __device__ __forceinline__ float value() const { return s + e; }
 };
+
+// Column accumulator of the FP32 sweeps: the products of a block of up to U
+// edges are summed with FMAs in b, and each block sum is folded into a
+// compensated pair, so the rounding error does not grow with the row length
+// (about two FP32 instructions per edge and column instead of ten for a
+// compensated product per edge).
+struct BlockSum {
+  Dot2 d;
+  float b = 0.f;
+  __device__ __forceinline__ void prod(float p, float r) { b = fmaf(p, r, b); }
+  __device__ __forceinline__ void fold() {
+    d.add(b);
+    b = 0.f;
+  }
+};
+
+// the two columns (col, col + 1) of row u; K even: one 8-byte load
+__device__ __forceinline__ float2 ld_pair(const float* R, int64_t u, int K, int col, bool two) {
+  const float* src = R + u * K + col;
+  if (two && (K & 1) == 0) return __ldg(reinterpret_cast<const float2*>(src));
+  return make_float2(__ldg(src), two ? __ldg(src + 1) : 0.f);
+}
 
 __device__ __forceinline__ void block_max2_u32(uint32_t dmax, uint32_t rmax, uint32_t* out) {
   __shared__ uint32_t sd[32], sr[32];
@@ -72,135 +90,272 @@ __device__ __forceinline__ bool ppr32_converged(const Ppr32Args& a) {
   return __uint_as_float(a.prev[0]) <= a.tol_rel * __uint_as_float(a.prev[1]);
 }
 
-// new values of 2 columns of vertex v from their accumulated sums
-__device__ __forceinline__ void ppr32_finish(const Ppr32Args& a, int32_t v, int col, float acc0, float acc1,
-                                             uint32_t& dmax, uint32_t& rmax) {
+// ------------------------------------------------- FP32 K-column sweep ----
+// A lane owns 4 consecutive columns of a tile (one 16-byte load per gathered
+// row when K % 4 == 0), so LPE = tile / 4 lanes cover one edge and a warp
+// load serves 32 / LPE edges ("slots").
+
+struct Col4 {
+  float v[4];
+};
+
+__device__ __forceinline__ Col4 zero4() {
+  Col4 c;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) c.v[q] = 0.f;
+  return c;
+}
+
+// columns col .. col + 3 of row u (zero past K)
+__device__ __forceinline__ Col4 ld_cols(const float* R, int64_t u, int K, int col) {
+  Col4 c;
+  const float* src = R + u * K + col;
+  if ((K & 3) == 0) {  // col is a multiple of 4: 16-byte aligned
+    const float4 f = __ldg(reinterpret_cast<const float4*>(src));
+    c.v[0] = f.x;
+    c.v[1] = f.y;
+    c.v[2] = f.z;
+    c.v[3] = f.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c.v[q] = col + q < K ? __ldg(src + q) : 0.f;
+  }
+  return c;
+}
+
+// S and the previous R of the 4 columns of vertex v, loaded before the row's
+// gathers so their latency overlaps
+struct Own4 {
+  float s[4], o[4];
+};
+__device__ __forceinline__ Own4 ppr32_own(const Ppr32Args& a, int32_t v, int col) {
+  Own4 w;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) w.s[q] = w.o[q] = 0.f;
+  if (col >= a.K) return w;
   const int64_t o = (int64_t)v * a.K + col;
+  if ((a.K & 3) == 0) {
+    const float4 s4 = *reinterpret_cast<const float4*>(a.S + o);
+    const float4 o4 = *reinterpret_cast<const float4*>(a.R + o);
+    w.s[0] = s4.x; w.s[1] = s4.y; w.s[2] = s4.z; w.s[3] = s4.w;
+    w.o[0] = o4.x; w.o[1] = o4.y; w.o[2] = o4.z; w.o[3] = o4.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      w.s[q] = col + q < a.K ? a.S[o + q] : 0.f;
+      w.o[q] = col + q < a.K ? a.R[o + q] : 0.f;
+    }
+  }
+  return w;
+}
+
+// new values of the 4 columns of vertex v from their accumulated sums
+__device__ __forceinline__ void ppr32_finish4(const Ppr32Args& a, int32_t v, int col, const float* acc, const Own4& w,
+                                              uint32_t& dmax, uint32_t& rmax) {
   if (col >= a.K) return;
-  const bool two = col + 1 < a.K;
-  const float s0 = a.S[o], s1 = two ? a.S[o + 1] : 0.f;
-  const float r0 = fmaf(a.alpha, acc0, a.beta * s0), r1 = fmaf(a.alpha, acc1, a.beta * s1);
-  const float o0 = a.R[o], o1 = two ? a.R[o + 1] : 0.f;
-  a.Rn[o] = r0;
-  if (two) a.Rn[o + 1] = r1;
-  dmax = max(dmax, __float_as_uint(fabsf(r0 - o0)));
-  rmax = max(rmax, __float_as_uint(fabsf(r0)));
-  if (two) {
-    dmax = max(dmax, __float_as_uint(fabsf(r1 - o1)));
-    rmax = max(rmax, __float_as_uint(fabsf(r1)));
+  const int64_t o = (int64_t)v * a.K + col;
+  float r[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    r[q] = fmaf(a.alpha, acc[q], a.beta * w.s[q]);
+    if (col + q < a.K) {
+      dmax = max(dmax, __float_as_uint(fabsf(r[q] - w.o[q])));
+      rmax = max(rmax, __float_as_uint(fabsf(r[q])));
+    }
+  }
+  if ((a.K & 3) == 0) {
+    *reinterpret_cast<float4*>(a.Rn + o) = make_float4(r[0], r[1], r[2], r[3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (col + q < a.K) a.Rn[o + q] = r[q];
   }
 }
 
-// G lanes per vertex, 2 columns per lane (tile of 2G columns starting at c0)
-template <int G, int U>
+// U edges of one slot in flight: edges j0 + k * stride (k < U) below e
+template <int U>
+__device__ __forceinline__ void ppr32_edges(const Ppr32Args& a, int64_t j0, int64_t stride, int64_t e, int col,
+                                            bool colok, BlockSum* acc) {
+  int32_t u[U];
+  float p[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    const int64_t j = j0 + (int64_t)k * stride;
+    u[k] = j < e ? __ldg(a.adj + j) : -1;
+    p[k] = j < e ? __ldg(a.P + j) : 0.f;
+  }
+  Col4 r[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) r[k] = (u[k] >= 0 && colok) ? ld_cols(a.R, u[k], a.K, col) : zero4();
+#pragma unroll
+  for (int k = 0; k < U; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q].prod(p[k], r[k].v[q]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q].fold();
+}
+
+// merge the compensated sums of the slots of a warp (slot 0 ends with the total)
+template <int LPE>
+__device__ __forceinline__ void merge_slots(Dot2* t) {
+#pragma unroll
+  for (int o = LPE; o < 32; o <<= 1) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Dot2 x;
+      x.s = __shfl_xor_sync(0xffffffffu, t[q].s, o);
+      x.e = __shfl_xor_sync(0xffffffffu, t[q].e, o);
+      t[q].merge(x);
+    }
+  }
+}
+
+// One vertex per slot (rows of at most a few hundred edges), U edges in flight.
+template <int LPE, int U>
 __global__ void __launch_bounds__(kThreads) k_ppr32_group(const Ppr32Args a, int64_t begin, int64_t end, int c0) {
   if (ppr32_converged(a)) return;
-  constexpr int kGroupsPerWarp = 32 / G;
-  const int lane = threadIdx.x & (G - 1);
-  const int gw = (threadIdx.x & 31) / G;
+  constexpr int kSlots = 32 / LPE;
+  const int sub = threadIdx.x & (LPE - 1);
+  const int slot = (threadIdx.x & 31) / LPE;
   const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-  const int col = c0 + 2 * lane;
-  const bool colok = col < a.K, two = col + 1 < a.K;
+  const int col = c0 + 4 * sub;
+  const bool colok = col < a.K;
   uint32_t dmax = 0, rmax = 0;
-  for (int64_t base = begin + warp * kGroupsPerWarp; base < end; base += nwarps * kGroupsPerWarp) {
-    const int64_t i = base + gw;
+  for (int64_t base = begin + warp * kSlots; base < end; base += nwarps * kSlots) {
+    const int64_t i = base + slot;
     if (i >= end) continue;
     const int32_t v = (int32_t)i;
     const int64_t b = a.off[v], e = a.off[v + 1];
-    Dot2 s0, s1;
-    for (int64_t j0 = b; j0 < e; j0 += U) {
-      int32_t u[U];
-      float p[U];
+    const Own4 w = ppr32_own(a, v, col);
+    BlockSum acc[4];
+    for (int64_t j0 = b; j0 < e; j0 += U) ppr32_edges<U>(a, j0, 1, e, col, colok, acc);
+    float c[4];
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const bool ok = j0 + k < e;
-        u[k] = ok ? __ldg(a.adj + j0 + k) : -1;
-        p[k] = ok ? __ldg(a.P + j0 + k) : 0.f;
-      }
-      float r0[U], r1[U];
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        r0[k] = 0.f;
-        r1[k] = 0.f;
-        if (u[k] >= 0 && colok) {
-          const float* src = a.R + (int64_t)u[k] * a.K + col;
-          if (two) {
-            r0[k] = __ldg(src);
-            r1[k] = __ldg(src + 1);
-          } else {
-            r0[k] = __ldg(src);
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        if (u[k] < 0) continue;
-        s0.add_prod(p[k], r0[k]);
-        s1.add_prod(p[k], r1[k]);
-      }
-    }
-    ppr32_finish(a, v, col, s0.value(), s1.value(), dmax, rmax);
+    for (int q = 0; q < 4; ++q) c[q] = acc[q].d.value();
+    ppr32_finish4(a, v, col, c, w, dmax, rmax);
   }
   block_max2_u32(dmax, rmax, a.resid);
 }
 
-// block per vertex for rows above kHubDeg edges: the block's edge slots
-// (kThreads / G of them) stride over the row, partial sums meet in shared memory
-template <int G>
-__global__ void __launch_bounds__(kThreads) k_ppr32_block(const Ppr32Args a, int64_t begin, int64_t end, int c0) {
+// One warp per vertex (mid-degree rows): the slots stride over the row, U
+// edges in flight each, and meet by shuffles.
+template <int LPE, int U>
+__global__ void __launch_bounds__(kThreads) k_ppr32_warp(const Ppr32Args a, int64_t begin, int64_t end, int c0) {
   if (ppr32_converged(a)) return;
-  constexpr int kSlots = kThreads / G;
-  __shared__ float ss[kSlots][2 * G];
-  const int lane = threadIdx.x % G, slot = threadIdx.x / G;
-  const int col = c0 + 2 * lane;
-  const bool colok = col < a.K, two = col + 1 < a.K;
+  constexpr int kSlots = 32 / LPE;
+  const int sub = threadIdx.x & (LPE - 1);
+  const int slot = (threadIdx.x & 31) / LPE;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const int col = c0 + 4 * sub;
+  const bool colok = col < a.K;
   uint32_t dmax = 0, rmax = 0;
-  for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
+  for (int64_t i = begin + warp; i < end; i += nwarps) {
     const int32_t v = (int32_t)i;
     const int64_t b = a.off[v], e = a.off[v + 1];
-    Dot2 s0, s1;
-    constexpr int U = 4;  // edges in flight per slot
-    for (int64_t j0 = b + slot; j0 < e; j0 += (int64_t)kSlots * U) {
-      int32_t u[U];
-      float p[U], r0[U], r1[U];
+    Own4 w;
+    if (slot == 0) w = ppr32_own(a, v, col);
+    BlockSum acc[4];
+    for (int64_t j0 = b + slot; j0 < e; j0 += (int64_t)kSlots * U) ppr32_edges<U>(a, j0, kSlots, e, col, colok, acc);
+    Dot2 t[4];
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const int64_t j = j0 + (int64_t)k * kSlots;
-        u[k] = j < e ? __ldg(a.adj + j) : -1;
-        p[k] = j < e ? __ldg(a.P + j) : 0.f;
-      }
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        r0[k] = 0.f;
-        r1[k] = 0.f;
-        if (u[k] >= 0 && colok) {
-          const float* src = a.R + (int64_t)u[k] * a.K + col;
-          r0[k] = __ldg(src);
-          if (two) r1[k] = __ldg(src + 1);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        if (u[k] < 0) continue;
-        s0.add_prod(p[k], r0[k]);
-        s1.add_prod(p[k], r1[k]);
-      }
-    }
-    ss[slot][2 * lane] = s0.value();
-    ss[slot][2 * lane + 1] = s1.value();
-    __syncthreads();
+    for (int q = 0; q < 4; ++q) t[q] = acc[q].d;
+    merge_slots<LPE>(t);
     if (slot == 0) {
-      Dot2 t0, t1;
-      for (int k = 0; k < kSlots; ++k) {
-        t0.add(ss[k][2 * lane]);
-        t1.add(ss[k][2 * lane + 1]);
-      }
-      ppr32_finish(a, v, col, t0.value(), t1.value(), dmax, rmax);
+      float c[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[q] = t[q].value();
+      ppr32_finish4(a, v, col, c, w, dmax, rmax);
     }
-    __syncthreads();
   }
   block_max2_u32(dmax, rmax, a.resid);
+}
+
+// Rows of the highest in-degree class are cut into chunks of kHubChunk edges
+// handled by different warps; each chunk's compensated partial sums go to
+// part[chunk][column] and a second kernel merges them in chunk order.
+template <int LPE, int U>
+__global__ void __launch_bounds__(kThreads) k_ppr32_hub_part(const Ppr32Args a, PprHub h, int c0, int tile,
+                                                             float2* __restrict__ part) {
+  if (ppr32_converged(a)) return;
+  constexpr int kSlots = 32 / LPE;
+  const int sub = threadIdx.x & (LPE - 1);
+  const int slot = (threadIdx.x & 31) / LPE;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const int col = c0 + 4 * sub;
+  const bool colok = col < a.K;
+  for (int64_t c = warp; c < h.nchunk; c += nwarps) {
+    const int32_t v = (int32_t)(h.begin + h.chunk_hub[c]);
+    const int64_t j_begin = h.chunk_j0[c];
+    const int64_t row_end = a.off[v + 1];
+    const int64_t e = j_begin + kHubChunk < row_end ? j_begin + kHubChunk : row_end;
+    BlockSum acc[4];
+    for (int64_t j0 = j_begin + slot; j0 < e; j0 += (int64_t)kSlots * U) ppr32_edges<U>(a, j0, kSlots, e, col, colok, acc);
+    Dot2 t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] = acc[q].d;
+    merge_slots<LPE>(t);
+    if (slot == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) part[c * tile + 4 * sub + q] = make_float2(t[q].s, t[q].e);
+    }
+  }
+}
+
+template <int LPE>
+__global__ void __launch_bounds__(kThreads) k_ppr32_hub_finish(const Ppr32Args a, PprHub h, int c0, int tile,
+                                                               const float2* __restrict__ part) {
+  if (ppr32_converged(a)) return;
+  constexpr int kSlots = 32 / LPE;
+  const int sub = threadIdx.x & (LPE - 1);
+  const int slot = (threadIdx.x & 31) / LPE;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const int col = c0 + 4 * sub;
+  uint32_t dmax = 0, rmax = 0;
+  for (int64_t base = warp * kSlots; base < h.nhub; base += nwarps * kSlots) {
+    const int64_t hi = base + slot;
+    if (hi >= h.nhub) continue;
+    Dot2 t[4];
+    for (int64_t c = h.hub_first[hi]; c < h.hub_first[hi + 1]; ++c) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 x = part[c * tile + 4 * sub + q];
+        Dot2 y;
+        y.s = x.x;
+        y.e = x.y;
+        t[q].merge(y);
+      }
+    }
+    float cv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cv[q] = t[q].value();
+    const int32_t v = (int32_t)(h.begin + hi);
+    ppr32_finish4(a, v, col, cv, ppr32_own(a, v, col), dmax, rmax);
+  }
+  block_max2_u32(dmax, rmax, a.resid);
+}
+
+// hub chunk table: count, then fill (hub_first is the scan of the counts)
+__global__ void k_hub_count(const int64_t* __restrict__ off, int64_t begin, int64_t nhub, int64_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nhub; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = off[begin + i + 1] - off[begin + i];
+    cnt[i] = d > 0 ? (d + kHubChunk - 1) / kHubChunk : 0;
+  }
+}
+
+__global__ void k_hub_fill(const int64_t* __restrict__ off, int64_t begin, int64_t nhub,
+                           const int64_t* __restrict__ first, int32_t* __restrict__ chunk_hub,
+                           int64_t* __restrict__ chunk_j0) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nhub; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = off[begin + i];
+    for (int64_t c = first[i]; c < first[i + 1]; ++c) {
+      chunk_hub[c] = (int32_t)i;
+      chunk_j0[c] = b + (c - first[i]) * kHubChunk;
+    }
+  }
 }
 
 // FP64 Jacobi step T(R) = alpha P^T R + (1 - alpha) S for a tile of 2G columns:
@@ -341,11 +496,19 @@ __global__ void k_widen_n(const float* __restrict__ y, int64_t cnt, double* __re
     x[i] = (double)y[i];
 }
 
-template <int G>
-void launch32_tile(const Ppr32Args& a, int64_t lo_b, int64_t lo_e, int64_t hi_e, int c0, cudaStream_t s) {
+template <int LPE>
+void launch32_tile(const Ppr32Args& a, const PprHub& h, float2* part, int64_t hub_b, int64_t n, int c0, int tile,
+                   cudaStream_t s) {
   const int maxg = kSMs * 8;
-  if (lo_e > lo_b) k_ppr32_group<G, 4><<<grid_for((lo_e - lo_b) * G, kThreads, maxg), kThreads, 0, s>>>(a, lo_b, lo_e, c0);
-  if (hi_e > lo_e) k_ppr32_block<G><<<grid_for(hi_e - lo_e, 1, maxg), kThreads, 0, s>>>(a, lo_e, hi_e, c0);
+  constexpr int kSlots = 32 / LPE;
+  if (hub_b > 0) k_ppr32_group<LPE, 4><<<grid_for(hub_b * LPE, kThreads, maxg), kThreads, 0, s>>>(a, 0, hub_b, c0);
+  if (h.begin > hub_b)
+    k_ppr32_warp<LPE, 8><<<grid_for((h.begin - hub_b) * 32, kThreads, maxg), kThreads, 0, s>>>(a, hub_b, h.begin, c0);
+  if (n > h.begin) {
+    k_ppr32_hub_part<LPE, 8><<<grid_for(h.nchunk * 32, kThreads, maxg), kThreads, 0, s>>>(a, h, c0, tile, part);
+    k_ppr32_hub_finish<LPE><<<grid_for(h.nhub * LPE, kThreads, maxg), kThreads, 0, s>>>(a, h, c0, tile, part);
+  }
+  (void)kSlots;
 }
 
 template <int G>
@@ -357,15 +520,39 @@ void launch64_tile(const Ppr64Args& a, int64_t lo_b, int64_t lo_e, int64_t hi_e,
 
 }  // namespace
 
-int launch_ppr32_sweep(const Ppr32Args& a, int tile, int64_t n, int64_t hub_begin, cudaStream_t s) {
+int launch_ppr32_sweep(const Ppr32Args& a, int tile, int64_t n, int64_t hub_begin, const PprHub& h, float2* part,
+                       cudaStream_t s) {
   for (int c0 = 0; c0 < a.K; c0 += tile) {
     switch (tile) {
-      case 8: launch32_tile<4>(a, 0, hub_begin, n, c0, s); break;
-      case 16: launch32_tile<8>(a, 0, hub_begin, n, c0, s); break;
-      case 32: launch32_tile<16>(a, 0, hub_begin, n, c0, s); break;
-      default: launch32_tile<32>(a, 0, hub_begin, n, c0, s); break;
+      case 8: launch32_tile<2>(a, h, part, hub_begin, n, c0, tile, s); break;
+      case 16: launch32_tile<4>(a, h, part, hub_begin, n, c0, tile, s); break;
+      case 32: launch32_tile<8>(a, h, part, hub_begin, n, c0, tile, s); break;
+      default: launch32_tile<16>(a, h, part, hub_begin, n, c0, tile, s); break;
     }
   }
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+int build_ppr_hub(const int64_t* off, int64_t begin, int64_t n, PprHubTable& t, Workspace& ws, cudaStream_t s) {
+  const int64_t nhub = n - begin;
+  t.begin = begin;
+  t.nhub = nhub > 0 ? nhub : 0;
+  t.nchunk = 0;
+  if (t.nhub == 0) return PRDF_OK;
+  DBuf<int64_t> cnt;
+  PRDF_TRY(cnt.alloc((size_t)t.nhub, s));
+  PRDF_TRY(t.hub_first.alloc((size_t)t.nhub + 1, s));
+  k_hub_count<<<grid_for(t.nhub, kThreads), kThreads, 0, s>>>(off, begin, t.nhub, cnt.p);
+  PRDF_LAUNCH_CHECK();
+  PRDF_TRY(exclusive_scan_i64(cnt.p, t.nhub, t.hub_first.p, ws, s));
+  PRDF_CUDA(cudaMemcpyAsync(ws.host_i64, t.hub_first.p + t.nhub, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  t.nchunk = ws.host_i64[0];
+  PRDF_TRY(t.chunk_hub.alloc((size_t)(t.nchunk > 0 ? t.nchunk : 1), s));
+  PRDF_TRY(t.chunk_j0.alloc((size_t)(t.nchunk > 0 ? t.nchunk : 1), s));
+  k_hub_fill<<<grid_for(t.nhub, kThreads), kThreads, 0, s>>>(off, begin, t.nhub, t.hub_first.p, t.chunk_hub.p,
+                                                              t.chunk_j0.p);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }
