@@ -26,8 +26,13 @@ def prdf():
     return p
 
 
-def case(scale, nsamp, seed, K):
+def case(scale, nsamp, seed, K, hub=False):
     n, s, d = synth.rmat(scale, nsamp, seed=seed)
+    if hub:  # vertex 0 with 6000 in- and out-neighbours: its rows span several 1024-edge chunks
+        k = min(n - 1, 6000)
+        ks = np.arange(1, k + 1, dtype=np.int32)
+        s = np.concatenate([s, ks, np.zeros(k, np.int32)])
+        d = np.concatenate([d, np.zeros(k, np.int32), ks])
     loops = np.arange(n, dtype=np.int32)
     s2, d2 = np.concatenate([s, loops]), np.concatenate([d, loops])
     w = synth.edge_weights(s2, d2, seed=seed)
@@ -48,8 +53,9 @@ def dense_P(og, w_out):
 
 
 @pytest.mark.parametrize("precision", [1, 0])
-def test_backward_matches_oracle_adjoint(precision):
-    n, g, og, w_out, S, Gw = case(10, 1 << 14, 3, 6)
+@pytest.mark.parametrize("scale,nsamp,hub", [(10, 1 << 14, False), (13, 60000, True)])
+def test_backward_matches_oracle_adjoint(precision, scale, nsamp, hub):
+    n, g, og, w_out, S, Gw = case(scale, nsamp, 3, 6, hub=hub)
     # the graph's out-CSR order is the oracle's (both sorted), so weights line up
     off, adj, wg = g.export_csr(prdf().PRDF_OUT)
     assert np.array_equal(host(adj), og.out_adj)

@@ -27,10 +27,10 @@ def prdf():
 
 def weighted_case(scale, nsamp, seed, hub=False):
     n, s, d = synth.rmat(scale, nsamp, seed=seed)
-    if hub:  # one vertex with a large in-row (block-per-vertex kernels)
-        k = min(n - 1, 3000)
-        s = np.concatenate([s, np.arange(1, k + 1, dtype=np.int32)])
-        d = np.concatenate([d, np.zeros(k, np.int32)])
+    if hub:  # large in-rows: vertex 0 gets up to 6000 sources, vertex 1 up to 5120
+        k0, k1 = min(n - 1, 6000), min(n - 2, 5120)
+        s = np.concatenate([s, np.arange(1, k0 + 1, dtype=np.int32), np.arange(2, k1 + 2, dtype=np.int32)])
+        d = np.concatenate([d, np.zeros(k0, np.int32), np.ones(k1, np.int32)])
     loops = np.arange(n, dtype=np.int32)
     s2, d2 = np.concatenate([s, loops]), np.concatenate([d, loops])
     w = synth.edge_weights(s2, d2, seed=seed)
@@ -42,7 +42,10 @@ def weighted_case(scale, nsamp, seed, hub=False):
 
 
 @pytest.mark.parametrize("precision", [1, 0])
-@pytest.mark.parametrize("scale,nsamp,K,hub", [(8, 3000, 5, False), (10, 12000, 64, False), (11, 20000, 17, True)])
+# (11, .., hub): rows of about 2000 in-edges (warp-per-vertex class); (13, .., hub):
+# rows above 4096 in-edges, cut into several 1024-edge chunks
+@pytest.mark.parametrize("scale,nsamp,K,hub", [(8, 3000, 5, False), (10, 12000, 64, False), (11, 20000, 17, True),
+                                               (13, 60000, 12, True)])
 def test_ppr_matches_oracle(precision, scale, nsamp, K, hub):
     n, g, og, w_out = weighted_case(scale, nsamp, seed=scale, hub=hub)
     S = synth.ppr_seeds(n, K, n_seed=16 if n > 100 else 4, seed=3)
