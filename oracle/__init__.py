@@ -77,6 +77,7 @@ def _l():
         lib.oracle_pagerank_static.argtypes = [i32, P, P, P, f64, f64, ci, P, P, P]
         lib.oracle_pagerank_dfp.argtypes = [i32, P, P, P, P, P, P, P, i64, P, P, i64, P, f64, f64, f64, f64, ci,
                                             ci, P, P, P, P]
+        lib.oracle_pagerank_dt.argtypes = [i32, P, P, P, P, P, P, P, i64, P, P, i64, P, f64, f64, ci, P, P, P, P, P]
         lib.oracle_row_normalise.argtypes = [i32, P, P, P]
         lib.oracle_ppr.argtypes = [i32, ci, P, P, P, P, f64, f64, ci, P, P, P]
         lib.oracle_ppr_adjoint.argtypes = [i32, ci, P, P, P, P, P, P, f64, f64, ci, P, P, P, P]
@@ -236,6 +237,27 @@ def pagerank_dfp(g: Graph, del_src, del_dst, ins_src, Rprev, del_mask=None, ins_
                              len(ds), _p(is_), _p(im), len(is_), _p(_c(Rprev, np.float64)), alpha, tol, tau_f, tau_p,
                              max_iter, int(prune), _p(R), _p(dV), _p(trace), ctypes.byref(st))
     return R, Stats(st.iterations, bool(st.converged), st.final_delta), dV, trace[:st.iterations].copy()
+
+
+def pagerank_dt(g: Graph, del_src, del_dst, ins_src, Rprev, del_mask=None, ins_mask=None, alpha=ALPHA, tol=TOL,
+                max_iter=MAX_ITER):
+    """Alg. traversal (Dynamic Traversal): reachability closure of the affected set, then Eq. 1 on it.
+
+    Returns (R, Stats, deltaV after the closure, |deltaV|, closure rounds).
+    """
+    n = g.n
+    ds, dd, is_ = _c(del_src, np.int32), _c(del_dst, np.int32), _c(ins_src, np.int32)
+    dm = None if del_mask is None else _c(del_mask, np.uint8)
+    im = None if ins_mask is None else _c(ins_mask, np.uint8)
+    R = np.empty(n, np.float64)
+    dV = np.empty(n, np.uint8)
+    na = ctypes.c_int64()
+    nr = ctypes.c_int64()
+    st = _Stats()
+    _l().oracle_pagerank_dt(n, _p(g.out_off), _p(g.out_adj), _p(g.in_off), _p(g.in_adj), _p(ds), _p(dd), _p(dm),
+                            len(ds), _p(is_), _p(im), len(is_), _p(_c(Rprev, np.float64)), alpha, tol, max_iter,
+                            _p(R), _p(dV), ctypes.byref(na), ctypes.byref(nr), ctypes.byref(st))
+    return R, Stats(st.iterations, bool(st.converged), st.final_delta), dV, na.value, nr.value
 
 
 # ------------------------------------------------- weighted PPR + adjoint ----

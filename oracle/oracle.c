@@ -31,7 +31,11 @@
  *     expand; the iteration count includes the final sweep;
  *  R10 duplicates are removed, then exactly one self-loop per vertex;
  *  R11 batch updates have set semantics: E^t = (E^{t-1} \ D) u I, self-loops
- *     are never deleted.
+ *     are never deleted;
+ *  R12 Dynamic Traversal closes the marked set under reachability along the
+ *     out-edges of G^t (Alg. traversal passes G^t; a vertex reachable in
+ *     G^{t-1} only through deleted edges is reached from their targets, which
+ *     initialAffected marks).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -339,6 +343,78 @@ int oracle_pagerank_dfp(int32_t n, const int64_t* out_off, const int32_t* out_ad
   if (dV_out) memcpy(dV_out, dV, (size_t)n);
   if (st) { st->iterations = it; st->converged = conv; st->final_delta = dR; }
   free(Ra); free(Rb); free(dV); free(dN); free(deg);
+  return 0;
+}
+
+/*
+ * Dynamic Traversal (Alg. traversal). Marking: initialAffected over the batch
+ * and one expandAffected, as in DF. Then the affected set is closed under
+ * reachability along the out-edges of G^t: the frontier (at first every
+ * affected vertex) is replaced by its out-neighbours, which join deltaV, until
+ * countOnes(deltaV) stops changing. Iterations: Eq. 1 on the affected vertices
+ * only (unaffected vertices keep R^{t-1}), no prune and no further expansion,
+ * until the L-inf change is <= tol. n_affected (nullable): |deltaV| after the
+ * closure; rounds (nullable): expansion rounds of the closure loop.
+ */
+int oracle_pagerank_dt(int32_t n, const int64_t* out_off, const int32_t* out_adj, const int64_t* in_off,
+                       const int32_t* in_adj, const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask,
+                       int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins,
+                       const double* Rprev, double alpha, double tol, int max_iter, double* R, uint8_t* dV_out,
+                       int64_t* n_affected, int64_t* rounds, oracle_stats* st) {
+  double* Ra = (double*)malloc((size_t)n * sizeof(double));
+  double* Rb = (double*)malloc((size_t)n * sizeof(double));
+  uint8_t* dV = (uint8_t*)calloc((size_t)n, 1);
+  uint8_t* dN = (uint8_t*)calloc((size_t)n, 1);
+  uint8_t* dF = (uint8_t*)calloc((size_t)n, 1);
+  int64_t* deg = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  for (int32_t v = 0; v < n; ++v) deg[v] = out_off[v + 1] - out_off[v];
+  for (int32_t v = 0; v < n; ++v) Ra[v] = Rb[v] = Rprev[v];
+  /* mark */
+  oracle_initial_affected(n, del_src, del_dst, del_mask, n_del, ins_src, ins_mask, n_ins, dV, dN);
+  oracle_expand_affected(n, out_off, out_adj, dN, dV);
+  int64_t na = 0;
+  for (int32_t v = 0; v < n; ++v) na += dV[v];
+  memcpy(dN, dV, (size_t)n);
+  int64_t nr = 0;
+  for (;;) {
+    memset(dF, 0, (size_t)n);
+    oracle_expand_affected(n, out_off, out_adj, dN, dF);
+    for (int32_t v = 0; v < n; ++v) dV[v] |= dF[v];
+    uint8_t* t = dN; dN = dF; dF = t;
+    ++nr;
+    int64_t na2 = 0;
+    for (int32_t v = 0; v < n; ++v) na2 += dV[v];
+    if (na2 == na) break;
+    na = na2;
+  }
+  /* Eq. 1 over the affected vertices */
+  const double C0 = (1.0 - alpha) / (double)n;
+  double* cur = Ra;
+  double* nxt = Rb;
+  int it = 0, conv = 0;
+  double dR = 0;
+  for (int i = 0; i < max_iter; ++i) {
+#pragma omp parallel for schedule(dynamic, 2048)
+    for (int32_t v = 0; v < n; ++v) {
+      if (!dV[v]) { nxt[v] = cur[v]; continue; }
+      double c = 0;
+      for (int64_t j = in_off[v]; j < in_off[v + 1]; ++j) {
+        int32_t u = in_adj[j];
+        c += cur[u] / (double)deg[u];
+      }
+      nxt[v] = C0 + alpha * c;
+    }
+    dR = linf_delta(n, nxt, cur);
+    double* t = cur; cur = nxt; nxt = t;
+    it = i + 1;
+    if (dR <= tol) { conv = 1; break; }
+  }
+  memcpy(R, cur, (size_t)n * sizeof(double));
+  if (dV_out) memcpy(dV_out, dV, (size_t)n);
+  if (n_affected) *n_affected = na;
+  if (rounds) *rounds = nr;
+  if (st) { st->iterations = it; st->converged = conv; st->final_delta = dR; }
+  free(Ra); free(Rb); free(dV); free(dN); free(dF); free(deg);
   return 0;
 }
 

@@ -351,6 +351,83 @@ def test_dfp_unaffected_vertices_keep_their_rank():
     assert trace[0] == aff.sum()
 
 
+# ------------------------------------------------------ Dynamic Traversal ----
+
+def _reachable(g, seeds):
+    """Brute-force breadth-first search along out-edges from a set of seed vertices."""
+    seen = np.zeros(g.n, bool)
+    stack = [int(v) for v in seeds]
+    for v in stack:
+        seen[v] = True
+    while stack:
+        u = stack.pop()
+        for w in g.out_adj[g.out_off[u]:g.out_off[u + 1]]:
+            if not seen[w]:
+                seen[w] = True
+                stack.append(int(w))
+    return seen
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_dt_affected_set_is_the_reachable_set(seed):
+    """Alg. traversal marks every vertex reachable in G^t from the batch: the targets of effective deletions and
+    the out-neighbours of the sources of effective deletions and insertions, then everything they reach."""
+    g0, g1, (ds, dd, is_, id_, dm, im) = _batch_graphs(seed, scale=7, nsamp=300, size=6)
+    R0, _ = oracle.pagerank_static(g0)
+    R, st, dV, na, rounds = oracle.pagerank_dt(g1, ds, dd, is_, R0, del_mask=dm, ins_mask=im)
+    dm, im = dm.astype(bool), im.astype(bool)
+    seeds = set(np.asarray(dd)[dm].tolist())
+    for u in list(np.asarray(ds)[dm]) + list(np.asarray(is_)[im]):
+        seeds.update(g1.out_adj[g1.out_off[u]:g1.out_off[u + 1]].tolist())
+    reach = _reachable(g1, sorted(seeds))
+    assert np.array_equal(dV.astype(bool), reach)
+    assert na == reach.sum()
+    assert 0 < reach.sum() < g1.n  # a sparse random graph: the closure is a proper subset
+
+
+def test_dt_reaches_the_exact_ranks_and_keeps_the_rest():
+    """Vertices not reachable from the batch keep their exact rank (PageRank of v depends only on the vertices
+    that reach v), so from the exact ranks of G^{t-1} DT converges to the exact ranks of G^t, and every
+    unaffected vertex is left bit-for-bit unchanged."""
+    g0, g1, (ds, dd, is_, id_, dm, im) = _batch_graphs(4, scale=7, nsamp=300, size=6)
+    r0 = dense_pagerank(g0)
+    R, st, dV, na, rounds = oracle.pagerank_dt(g1, ds, dd, is_, r0, del_mask=dm, ins_mask=im, tol=1e-15)
+    aff = dV.astype(bool)
+    assert np.array_equal(R[~aff], r0[~aff])
+    assert np.max(np.abs(R - dense_pagerank(g1))) <= 1e-13
+
+
+def test_dt_on_a_strongly_connected_graph_is_naive_dynamic():
+    """When every vertex reaches every other, the closure is all of V and DT runs Eq. 1 on every vertex, which
+    is Alg. naive."""
+    n, s, d = synth.rmat(7, 500, seed=5)
+    ring = np.arange(n)
+    s = np.concatenate([s, ring])
+    d = np.concatenate([d, (ring + 1) % n])
+    g0 = oracle.graph(n, s, d)
+    ds, dd, is_, id_ = synth.batch(n, g0.out_off, g0.out_adj, 8, seed=5, s1=1)
+    g1, dm, im = oracle.apply_batch(g0, ds, dd, is_, id_)
+    # keep the ring: the batch's deletions must not break strong connectivity
+    keep = ~((np.asarray(dd) == (np.asarray(ds) + 1) % n))
+    ds, dd, dm = np.asarray(ds)[keep], np.asarray(dd)[keep], np.asarray(dm)[keep]
+    g1, dm2, im = oracle.apply_batch(g0, ds, dd, is_, id_)
+    R0, _ = oracle.pagerank_static(g0)
+    R, st, dV, na, rounds = oracle.pagerank_dt(g1, ds, dd, is_, R0, del_mask=dm2, ins_mask=im)
+    Rn, stn = oracle.pagerank_static(g1, R0=R0)
+    assert na == n
+    assert st.iterations == stn.iterations
+    assert np.array_equal(R, Rn)
+
+
+def test_dt_empty_batch_is_identity():
+    g0, g1, _ = _batch_graphs(2)
+    R1, _ = oracle.pagerank_static(g1)
+    R, st, dV, na, rounds = oracle.pagerank_dt(g1, [], [], [], R1)
+    assert na == 0 and dV.sum() == 0
+    assert st.iterations == 1 and st.final_delta == 0
+    assert np.array_equal(R, R1)
+
+
 # ------------------------------------------------------- PPR + adjoint ----
 
 def _weighted(seed=1, scale=6, nsamp=500):
