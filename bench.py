@@ -174,8 +174,9 @@ def measure_dfp(g, n, m, args):
     """DF-P after random batches (80% uniform insertions, 20% deletions of existing non-self-loop edges)
     of size f*|E|, consecutive batches per size, each starting from the previous DF-P ranks. Reports
     DF-P time (partition + marking + sweeps + expansion, batch application excluded as in the paper),
-    GPU Static time from scratch on the same snapshot, and the L1 error of DF-P against a GPU Static
-    solve at L-inf 1e-13 (the oracle pins the same path on smaller graphs)."""
+    Dynamic Traversal time from the same previous ranks, GPU Static time from scratch on the same
+    snapshot, and the L1 errors against a GPU Static solve at L-inf 1e-13 (the oracle pins the same
+    path on smaller graphs)."""
     import numpy as np
     import torch
     import synth
@@ -184,6 +185,7 @@ def measure_dfp(g, n, m, args):
     out = []
     for fi, f in enumerate(args.dfp_sizes):
         t_dfp, t_static, errs, iters, aff = [], [], [], [], []
+        t_dt, errs_dt, aff_dt = [], [], []
         for b in range(args.dfp_batches):
             off, adj, _ = g.export_csr(prdf.PRDF_OUT)
             size = max(1, int(round(f * m)))
@@ -192,8 +194,12 @@ def measure_dfp(g, n, m, args):
             de, ie = g.apply_batch(t(ds), t(dd), t(is_), t(id_))
             torch.cuda.synchronize()
             R, st, _ = g.pagerank_dfp(t(ds), t(dd), t(is_), R_prev, del_mask=de, ins_mask=ie)
+            Rd, std, _ = g.pagerank_dt(t(ds), t(dd), t(is_), R_prev, del_mask=de, ins_mask=ie)
             Rs, sts = g.pagerank_static()
             Rt, _ = g.pagerank_static(tol=1e-13)
+            t_dt.append(std.ms_total)
+            errs_dt.append(float((Rd - Rt).abs().sum()))
+            aff_dt.append(std.affected_initial)
             t_dfp.append(st.ms_total)
             t_static.append(sts.ms_total)
             errs.append(float((R - Rt).abs().sum()))
@@ -204,7 +210,10 @@ def measure_dfp(g, n, m, args):
                     "dfp_ms": statistics.median(t_dfp), "static_ms": statistics.median(t_static),
                     "speedup_vs_static": statistics.median(t_static) / statistics.median(t_dfp),
                     "dfp_sweeps": statistics.median(iters), "affected_initial": int(statistics.median(aff)),
-                    "l1_err_max": max(errs)})
+                    "l1_err_max": max(errs),
+                    "dt_ms": statistics.median(t_dt), "dt_affected": int(statistics.median(aff_dt)),
+                    "dt_l1_err_max": max(errs_dt),
+                    "dfp_speedup_vs_dt": statistics.median(t_dt) / statistics.median(t_dfp)})
     return out
 
 

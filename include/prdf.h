@@ -234,6 +234,23 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
                       const double* prev_ranks, double* ranks, const prdf_params* p, uint8_t* dV_out,
                       prdf_stats* stats);
 
+/*
+ * Dynamic Traversal PageRank (Alg. traversal), the paper's traversal-based
+ * baseline for dynamic graphs. Marking as in prdf_pagerank_dfp
+ * (initialAffected over the batch, then expandAffected); then deltaV is
+ * closed under reachability along the out-edges of G^t (rounds that mark the
+ * not-yet-affected out-neighbours of the last round's new vertices, until a
+ * round adds none, i.e. until the affected count stops changing); then Eq. 1
+ * sweeps on the affected vertices only, with no prune and no expansion (p->prune
+ * and p->tau_f are ignored), until ||R_new - R||_inf <= p->tol or p->max_iter.
+ * Unaffected vertices keep prev_ranks. Arguments as for prdf_pagerank_dfp;
+ * dV_out receives the closed affected set, stats->affected_initial its size.
+ */
+int prdf_pagerank_dt(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask,
+                     int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins,
+                     const double* prev_ranks, double* ranks, const prdf_params* p, uint8_t* dV_out,
+                     prdf_stats* stats);
+
 /* ------------------------------------------------------------ tuning -- */
 
 /*

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "prdf_expand_affected": (_INT, [_P, _P, _P, _P]),
     "prdf_pagerank_static": (_INT, [_P, _P, _P, _P, _P]),
     "prdf_pagerank_dfp": (_INT, [_P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
+    "prdf_pagerank_dt": (_INT, [_P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "prdf_pagerank_ppr": (_INT, [_P, _P, _INT, _P, _P, _P]),
     "prdf_graph_set_weights": (_INT, [_P, _P, _P]),
     "prdf_autotune": (_INT, [_P, _P, _INT, _P, _P]),
@@ -281,6 +282,21 @@ class Graph:
                                        _ptr(ins_mask, torch.uint8, ni), ni,
                                        _ptr(prev_ranks, torch.float64, n, "prev_ranks"), _ptr(R), ctypes.byref(p),
                                        _ptr(dV), ctypes.byref(st)))
+        return R, _stats(st), dV
+
+    def pagerank_dt(self, del_src, del_dst, ins_src, prev_ranks, del_mask=None, ins_mask=None, want_dV=False, **kw):
+        """Alg. traversal (Dynamic Traversal). Returns (ranks, Stats, closed deltaV or None)."""
+        n = self.n
+        nd, ni = del_src.numel(), ins_src.numel()
+        R = torch.empty(n, dtype=torch.float64, device="cuda")
+        dV = torch.empty(n, dtype=torch.uint8, device="cuda") if want_dV else None
+        st = _Stats()
+        p = params(**kw)
+        _check(lib().prdf_pagerank_dt(self._h, _ptr(del_src, torch.int32), _ptr(del_dst, torch.int32, nd),
+                                      _ptr(del_mask, torch.uint8, nd), nd, _ptr(ins_src, torch.int32),
+                                      _ptr(ins_mask, torch.uint8, ni), ni,
+                                      _ptr(prev_ranks, torch.float64, n, "prev_ranks"), _ptr(R), ctypes.byref(p),
+                                      _ptr(dV), ctypes.byref(st)))
         return R, _stats(st), dV
 
     def pagerank_ppr(self, S: torch.Tensor, **kw):

@@ -334,7 +334,7 @@ int nonempty_classes(const int64_t* cb, int nclass) {
 // change of a sweep is <= tol or max_iter sweeps ran. The host reads the
 // residual every check_every sweeps; sweeps launched past convergence exit at
 // once on the device.
-int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, cudaStream_t s) {
+int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, cudaStream_t s, bool expand = true) {
   const int n = g->n;
   const int max_iter = p->max_iter;
   PRDF_TRY(g->resid.reserve((size_t)max_iter + 1, s));
@@ -344,7 +344,8 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
   const int nci = rl.thr.n + 1, nco = g->thr[PRDF_OUT].n + 1;
   begins_from_counts(rl.count, nci, cb);
   if (dynamic) begins_from_counts(rl.pout_count, nco, cbo);
-  const int kps = nonempty_classes(cb, nci) + (dynamic ? nonempty_classes(cbo, nco) : 0);
+  const bool expanding = dynamic && expand;
+  const int kps = nonempty_classes(cb, nci) + (expanding ? nonempty_classes(cbo, nco) : 0);
   SweepArgs a;
   memset(&a, 0, sizeof(a));
   a.off = rl.in.off.p;
@@ -381,7 +382,7 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
       a.xn = (i & 1) ? g->xa.p : g->xb.p;
       a.resid = g->resid.p + i;
       a.prev = i > 0 ? g->resid.p + i - 1 : nullptr;
-      if (dynamic) PRDF_CUDA(cudaMemsetAsync(g->dN.p, 0, (size_t)n, s));
+      if (expanding) PRDF_CUDA(cudaMemsetAsync(g->dN.p, 0, (size_t)n, s));
       if (timed) {
         cudaEvent_t e0, e1;
         PRDF_CUDA(cudaEventCreate(&e0));
@@ -392,8 +393,8 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
       }
       PRDF_TRY(launch_sweep(a, rl.thr, cb, exact, dynamic, s));
       if (timed) PRDF_CUDA(cudaEventRecord(ev.back(), s));
-      if (dynamic)
-        PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, g->resid.p + i,
+      if (expanding)
+        PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, nullptr, g->resid.p + i,
                                p->tol, s));
     }
     launched = upto;
@@ -1036,7 +1037,7 @@ int prdf_expand_affected(prdf_graph* g, const uint8_t* dN, uint8_t* dV, void* st
   int64_t cb[kMaxThr + 2];
   class_begins(g, PRDF_OUT, cb);
   PRDF_TRY(launch_expand(g->csr[PRDF_OUT].off.p, g->csr[PRDF_OUT].adj.p, g->P[PRDF_OUT].p, cb, g->thr[PRDF_OUT].n + 1,
-                         dN, dV, nullptr, 0.0, s));
+                         dN, dV, nullptr, nullptr, 0.0, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
   return PRDF_OK;
 }
@@ -1147,7 +1148,7 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
   int64_t cbo[kMaxThr + 2];
   begins_from_counts(rl.pout_count, g->thr[PRDF_OUT].n + 1, cbo);
   PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, g->thr[PRDF_OUT].n + 1, g->dN.p, g->dV.p,
-                         nullptr, 0.0, s));
+                         nullptr, nullptr, 0.0, s));
   PRDF_TRY(count_flags(g->dV.p, n, g->counter.p, s));
   PRDF_CUDA(cudaEventRecord(t.e[2], s));
   PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64 + 8, g->counter.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -1176,6 +1177,94 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
     // out-degree partition + init + initial marking + expand + count + sweeps/expands + finalize
     stats->kernel_launches = 5 + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, g->thr[PRDF_OUT].n + 1) + 1 +
                              it.kernels + 1;
+  }
+  return PRDF_OK;
+}
+
+int prdf_pagerank_dt(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask,
+                     int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins,
+                     const double* prev_ranks, double* ranks, const prdf_params* p, uint8_t* dV_out,
+                     prdf_stats* stats) {
+  if (!g || !prev_ranks || !ranks || n_del < 0 || n_ins < 0 || (n_del && (!del_src || !del_dst)) ||
+      (n_ins && !ins_src)) {
+    set_error("prdf_pagerank_dt: bad arguments");
+    return PRDF_EINVAL;
+  }
+  PRDF_TRY(check_params(p));
+  cudaStream_t s = (cudaStream_t)p->stream;
+  PRDF_TRY(check_ids(g, del_src, del_dst, n_del, s));
+  PRDF_TRY(check_ids(g, ins_src, nullptr, n_ins, s));
+  Timer t;
+  PRDF_TRY(t.init());
+  PRDF_TRY(alloc_solver(g, true, s));
+  const int n = g->n;
+  PRDF_TRY(g->dF.reserve(n, s));
+  PRDF_CUDA(cudaEventRecord(t.e[0], s));
+  // Alg. traversal: R = Rnew = R^{t-1}; partition G and G'; mark; close; iterate
+  g->rl.pout_valid = false;
+  PRDF_TRY(ensure_relabelled(g, true, s));
+  const Relabel& rl = g->rl;
+  k_init_x<<<grid_for(n, kThreads), kThreads, 0, s>>>(prev_ranks, rl.perm.p, n, rl.inv_deg.p, g->xa.p, g->xb.p);
+  PRDF_LAUNCH_CHECK();
+  PRDF_CUDA(cudaEventRecord(t.e[1], s));
+  PRDF_CUDA(cudaMemsetAsync(g->dV.p, 0, (size_t)n, s));
+  PRDF_CUDA(cudaMemsetAsync(g->dN.p, 0, (size_t)n, s));
+  PRDF_CUDA(cudaMemsetAsync(g->wrote.p, 0, (size_t)n, s));
+  PRDF_TRY(launch_initial_affected(del_src, del_dst, del_mask, n_del, ins_src, ins_mask, n_ins, rl.inv.p, g->dV.p,
+                                   g->dN.p, s));
+  const int nco = g->thr[PRDF_OUT].n + 1;
+  int64_t cbo[kMaxThr + 2];
+  begins_from_counts(rl.pout_count, nco, cbo);
+  PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, nullptr, nullptr, 0.0, s));
+  // reachability closure over G^t: the frontier starts as every affected vertex; each
+  // round marks the vertices it reaches that were not yet affected, which form the
+  // next frontier, until a round adds none (the affected count stops changing)
+  long long kernels = 5 + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, nco);
+  PRDF_CUDA(cudaMemcpyAsync(g->dN.p, g->dV.p, (size_t)n, cudaMemcpyDeviceToDevice, s));
+  uint8_t* front = g->dN.p;
+  uint8_t* next = g->dF.p;
+  for (int round = 0; round < n; ++round) {
+    PRDF_CUDA(cudaMemsetAsync(next, 0, (size_t)n, s));
+    PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, front, g->dV.p, next, nullptr, 0.0, s));
+    PRDF_TRY(count_flags(next, n, g->counter.p, s));
+    kernels += nonempty_classes(cbo, nco) + 1;
+    unsigned long long added = 0;
+    PRDF_CUDA(cudaMemcpyAsync(&added, g->counter.p, sizeof(added), cudaMemcpyDeviceToHost, s));
+    PRDF_CUDA(cudaStreamSynchronize(s));
+    if (added == 0) break;
+    uint8_t* tmp = front;
+    front = next;
+    next = tmp;
+  }
+  PRDF_TRY(count_flags(g->dV.p, n, g->counter.p, s));
+  PRDF_CUDA(cudaEventRecord(t.e[2], s));
+  PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64 + 8, g->counter.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  // Eq. 1 on the affected vertices, no prune and no expansion
+  prdf_params q = *p;
+  q.prune = 0;
+  q.tau_f = INFINITY;
+  IterResult it;
+  PRDF_TRY(iterate(g, &q, true, &it, s, false));  // synchronises the stream
+  const long long aff = (long long)g->ws.host_i64[8];
+  k_finalize<<<grid_for(n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, rl.degd.p, rl.perm.p, n,
+                                                       ranks, g->dV.p, dV_out);
+  PRDF_LAUNCH_CHECK();
+  PRDF_CUDA(cudaEventRecord(t.e[3], s));
+  PRDF_CUDA(cudaEventSynchronize(t.e[3]));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations = it.iters;
+    stats->converged = it.converged;
+    stats->final_delta = it.final_delta;
+    stats->sweeps_launched = it.launched;
+    cudaEventElapsedTime(&stats->ms_total, t.e[0], t.e[3]);
+    cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
+    cudaEventElapsedTime(&stats->ms_mark, t.e[1], t.e[2]);
+    cudaEventElapsedTime(&stats->ms_iterate, t.e[2], t.e[3]);
+    stats->ms_sweep = it.ms_sweep;
+    stats->edges_processed = -1;
+    stats->affected_initial = aff;
+    stats->kernel_launches = kernels + 1 + it.kernels + 1;
   }
   return PRDF_OK;
 }

@@ -3,6 +3,9 @@
 // partition of G with thread-, sub-warp-, warp- and block-per-vertex
 // kernels. Flags are uint8; every store writes 1, so concurrent marks of the
 // same vertex need no atomics, and a flag already set is not stored again.
+// With a third flag array dF the same kernels are one round of the
+// reachability closure of Dynamic Traversal (Alg. traversal): a vertex that
+// was not yet affected is marked in dV and in dF (the next frontier).
 #include "internal.cuh"
 
 namespace prdf {
@@ -39,7 +42,7 @@ __global__ void __launch_bounds__(kThreads) k_expand_group(const int64_t* __rest
                                                            const int32_t* __restrict__ adj,
                                                            const int32_t* __restrict__ P, int64_t begin, int64_t end,
                                                            const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
-                                                           const uint64_t* resid, double tol) {
+                                                           uint8_t* __restrict__ dF, const uint64_t* resid, double tol) {
   if (converged(resid, tol)) return;
   const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
   const int64_t gid = (blockIdx.x * (int64_t)kThreads + threadIdx.x) / G;
@@ -50,7 +53,10 @@ __global__ void __launch_bounds__(kThreads) k_expand_group(const int64_t* __rest
     const int64_t b = off[u], e = off[u + 1];
     for (int64_t j = b + lane; j < e; j += G) {
       const int32_t w = adj[j];
-      if (!dV[w]) dV[w] = 1;  // most targets are already marked when the frontier is large
+      if (!dV[w]) {  // most targets are already marked when the frontier is large
+        dV[w] = 1;
+        if (dF) dF[w] = 1;
+      }
     }
   }
 }
@@ -59,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_expand_block(const int64_t* __rest
                                                            const int32_t* __restrict__ adj,
                                                            const int32_t* __restrict__ P, int64_t begin, int64_t end,
                                                            const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
-                                                           const uint64_t* resid, double tol) {
+                                                           uint8_t* __restrict__ dF, const uint64_t* resid, double tol) {
   if (converged(resid, tol)) return;
   for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
     const int32_t u = P[i];
@@ -67,7 +73,10 @@ __global__ void __launch_bounds__(kThreads) k_expand_block(const int64_t* __rest
     const int64_t b = off[u], e = off[u + 1];
     for (int64_t j = b + threadIdx.x; j < e; j += kThreads) {
       const int32_t w = adj[j];
-      if (!dV[w]) dV[w] = 1;
+      if (!dV[w]) {
+        dV[w] = 1;
+        if (dF) dF[w] = 1;
+      }
     }
   }
 }
@@ -93,7 +102,7 @@ int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, cons
 }
 
 int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, const int64_t* cb, int nclass,
-                  const uint8_t* dN, uint8_t* dV, const uint64_t* resid, double tol, cudaStream_t s) {
+                  const uint8_t* dN, uint8_t* dV, uint8_t* dF, const uint64_t* resid, double tol, cudaStream_t s) {
   const int maxg = kSMs * 8;
   for (int c = 0; c < nclass; ++c) {
     const int64_t b = cb[c], e = cb[c + 1];
@@ -101,10 +110,10 @@ int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, cons
     const int64_t cnt = e - b;
     const int kind = (nclass == 4) ? c : (c == nclass - 1 ? 3 : c);
     switch (kind) {
-      case 0: k_expand_group<1><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, resid, tol); break;
-      case 1: k_expand_group<8><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, resid, tol); break;
-      case 2: k_expand_group<32><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, resid, tol); break;
-      default: k_expand_block<<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, resid, tol); break;
+      case 0: k_expand_group<1><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
+      case 1: k_expand_group<8><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
+      case 2: k_expand_group<32><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
+      default: k_expand_block<<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
     }
   }
   PRDF_LAUNCH_CHECK();

@@ -185,6 +185,37 @@ def test_dfp_all_affected_df_equals_naive_dynamic():
     assert np.max(np.abs(host(R) - Rn)) <= 1e-13
 
 
+# ------------------------------------------------------ Dynamic Traversal ----
+
+@pytest.mark.parametrize("seed,scale,nsamp,size", [(1, 8, 3000, 20), (5, 12, 3000, 8), (6, 12, 50000, 5),
+                                                   (7, 14, 20000, 40)])
+def test_dt_matches_oracle(seed, scale, nsamp, size):
+    """Closure bit-exact (sparse graphs leave unreachable vertices out), same sweep count, ranks to 1e-12."""
+    g, og1, R0, (ds, dd, is_, id_, de, ie, dmo, imo) = _dynamic_case(seed, scale, nsamp, size)
+    R, st, dV = g.pagerank_dt(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True)
+    Ro, sto, dVo, na, rounds = oracle.pagerank_dt(og1, ds, dd, is_, host(R0), del_mask=dmo, ins_mask=imo)
+    assert np.array_equal(host(dV), dVo)
+    assert st.affected_initial == na
+    assert st.iterations == sto.iterations and st.converged
+    assert np.max(np.abs(host(R) - Ro) / Ro) <= 1e-12
+    unaffected = dVo == 0
+    if unaffected.any():  # unaffected vertices keep R^{t-1} up to the x = R/|out| round trip
+        r0 = host(R0)[unaffected]
+        assert np.max(np.abs(host(R)[unaffected] - r0) / r0) <= 4.5e-16
+
+
+def test_dt_empty_batch_is_identity():
+    n, s, d = synth.rmat(10, 12000, seed=5)
+    g = gpu_graph(n, s, d)
+    R0o, _ = oracle.pagerank_static(oracle.graph(n, s, d))
+    R0 = dev(R0o)
+    e = torch.zeros(0, dtype=torch.int32, device="cuda")
+    R, st, dV = g.pagerank_dt(e, e, e, R0, want_dV=True)
+    assert st.iterations == 1 and st.affected_initial == 0
+    assert int(dV.sum()) == 0
+    assert float(((R - R0).abs() / R0).max()) <= 4.5e-16
+
+
 def test_autotune_keeps_ranks_bit_identical():
     """The tuner only changes kernel shapes and the vertex numbering; exact accumulation keeps every bit."""
     n, s, d = synth.rmat(13, 150000, seed=12)
