@@ -74,6 +74,21 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def sweep_source_hash():
+    """sha256 over what the rank-sweep kernels are compiled from: sweep.cu, common.cuh and the SweepArgs
+    declaration in internal.cuh (other declarations there do not change the sweep)."""
+    csrc = os.path.join(ROOT, "paper_2404_08299_gb300", "csrc")
+    h = hashlib.sha256()
+    for fn in ("sweep.cu", "common.cuh"):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
+    with open(os.path.join(csrc, "internal.cuh")) as f:
+        text = f.read()
+    i = text.index("struct SweepArgs {")
+    h.update(text[i:text.index("};", i) + 2].encode())
+    return h.hexdigest()
+
+
 def recorded_traffic():
     """DRAM bytes per sweep from the committed ncu summary, valid only while the
     sweep sources are unchanged (sha256 recorded beside the number)."""
@@ -85,11 +100,7 @@ def recorded_traffic():
                 parts = line.split()
                 if len(parts) == 2:
                     rec[parts[0]] = parts[1]
-        h = hashlib.sha256()
-        for fn in ("sweep.cu", "common.cuh", "internal.cuh"):
-            with open(os.path.join(ROOT, "paper_2404_08299_gb300", "csrc", fn), "rb") as f:
-                h.update(f.read())
-        if rec.get("source_sha256") == h.hexdigest():
+        if rec.get("source_sha256") == sweep_source_hash():
             return float(rec["dram_bytes_per_sweep"])
     except Exception:
         pass
@@ -174,7 +185,7 @@ def measure_dfp(g, n, m, args):
     """DF-P after random batches (80% uniform insertions, 20% deletions of existing non-self-loop edges)
     of size f*|E|, consecutive batches per size, each starting from the previous DF-P ranks. Reports
     DF-P time (partition + marking + sweeps + expansion, batch application excluded as in the paper),
-    Dynamic Traversal time from the same previous ranks, GPU Static time from scratch on the same
+    Dynamic Traversal, Naive-dynamic and DF times from the same previous ranks, GPU Static time from scratch on the same
     snapshot, and the L1 errors against a GPU Static solve at L-inf 1e-13 (the oracle pins the same
     path on smaller graphs)."""
     import numpy as np
@@ -186,6 +197,7 @@ def measure_dfp(g, n, m, args):
     for fi, f in enumerate(args.dfp_sizes):
         t_dfp, t_static, errs, iters, aff = [], [], [], [], []
         t_dt, errs_dt, aff_dt = [], [], []
+        t_nd, t_df, errs_nd, errs_df = [], [], [], []
         for b in range(args.dfp_batches):
             off, adj, _ = g.export_csr(prdf.PRDF_OUT)
             size = max(1, int(round(f * m)))
@@ -195,9 +207,15 @@ def measure_dfp(g, n, m, args):
             torch.cuda.synchronize()
             R, st, _ = g.pagerank_dfp(t(ds), t(dd), t(is_), R_prev, del_mask=de, ins_mask=ie)
             Rd, std, _ = g.pagerank_dt(t(ds), t(dd), t(is_), R_prev, del_mask=de, ins_mask=ie)
+            Rn, stn = g.pagerank_static(R0=R_prev)  # Naive-dynamic (Alg. naive)
+            Rf, stf, _ = g.pagerank_dfp(t(ds), t(dd), t(is_), R_prev, del_mask=de, ins_mask=ie, prune=0)  # DF
             Rs, sts = g.pagerank_static()
             Rt, _ = g.pagerank_static(tol=1e-13)
             t_dt.append(std.ms_total)
+            t_nd.append(stn.ms_total)
+            t_df.append(stf.ms_total)
+            errs_nd.append(float((Rn - Rt).abs().sum()))
+            errs_df.append(float((Rf - Rt).abs().sum()))
             errs_dt.append(float((Rd - Rt).abs().sum()))
             aff_dt.append(std.affected_initial)
             t_dfp.append(st.ms_total)
@@ -213,7 +231,64 @@ def measure_dfp(g, n, m, args):
                     "l1_err_max": max(errs),
                     "dt_ms": statistics.median(t_dt), "dt_affected": int(statistics.median(aff_dt)),
                     "dt_l1_err_max": max(errs_dt),
-                    "dfp_speedup_vs_dt": statistics.median(t_dt) / statistics.median(t_dfp)})
+                    "dfp_speedup_vs_dt": statistics.median(t_dt) / statistics.median(t_dfp),
+                    "nd_ms": statistics.median(t_nd), "nd_l1_err_max": max(errs_nd),
+                    "df_ms": statistics.median(t_df), "df_l1_err_max": max(errs_df)})
+    return out
+
+
+def measure_temporal(args):
+    """Temporal-stream stand-in for the paper's real-world dynamic graphs (Sec. 5.1.4): the sample order of a
+    seeded R-MAT edge stream (2^20 vertices, 2^24 samples) is its time order; the first 90% is loaded with
+    self-loops, then consecutive insertion-only batches of B = f*|E_T| stream edges are applied, for
+    f = 1e-5, 1e-4, 1e-3 (each size starting again from the 90% snapshot). Static runs from scratch on
+    every snapshot; Naive-dynamic, Dynamic Traversal, DF and DF-P each continue from their own previous
+    ranks. Reports mean time per batch and the worst L1 error against a Static solve at L-inf 1e-13."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2404_08299_gb300 as prdf
+    n, s, d = synth.rmat(20, 1 << 24, seed=3)
+    E = len(s)
+    pre = int(0.9 * E)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    empty = torch.zeros(0, dtype=torch.int32, device="cuda")
+    out = {"n": n, "stream_edges": E, "preloaded": pre, "batches": args.temporal_batches, "sizes": []}
+    for f in (1e-5, 1e-4, 1e-3):
+        g = prdf.Graph(n, t(s[:pre]), t(d[:pre]))
+        R0, _ = g.pagerank_static(tol=1e-13)
+        prev = {k: R0 for k in ("nd", "dt", "df", "dfp")}
+        B = max(1, int(round(f * E)))
+        times = {k: [] for k in ("static", "nd", "dt", "df", "dfp")}
+        errs = {k: [] for k in ("static", "nd", "dt", "df", "dfp")}
+        pos = pre
+        for b in range(args.temporal_batches):
+            if pos + B > E:
+                break
+            bs, bd = t(s[pos:pos + B]), t(d[pos:pos + B])
+            pos += B
+            _, ie = g.apply_batch(empty, empty, bs, bd)
+            ref, _ = g.pagerank_static(tol=1e-13)
+            Rs, st = g.pagerank_static()
+            res = {"static": (Rs, st)}
+            res["nd"] = g.pagerank_static(R0=prev["nd"])
+            Rdt, st_dt, _ = g.pagerank_dt(empty, empty, bs, prev["dt"], ins_mask=ie)
+            res["dt"] = (Rdt, st_dt)
+            Rdf, st_df, _ = g.pagerank_dfp(empty, empty, bs, prev["df"], ins_mask=ie, prune=0)
+            res["df"] = (Rdf, st_df)
+            Rp, st_p, _ = g.pagerank_dfp(empty, empty, bs, prev["dfp"], ins_mask=ie)
+            res["dfp"] = (Rp, st_p)
+            for k, (R, stk) in res.items():
+                times[k].append(stk.ms_total)
+                errs[k].append(float((R - ref).abs().sum()))
+                if k != "static":
+                    prev[k] = R
+        mean = {k: sum(v) / len(v) for k, v in times.items()}
+        out["sizes"].append({"batch_fraction": f, "batch_size": B, "batches_run": len(times["static"]),
+                             "mean_ms": mean, "l1_err_max": {k: max(v) for k, v in errs.items()},
+                             "speedup_vs_static": {k: mean["static"] / mean[k] for k in mean}})
+        del g
+        torch.cuda.empty_cache()
     return out
 
 
@@ -325,6 +400,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default in-degree class thresholds")
     ap.add_argument("--dfp-sizes", type=float, nargs="*", default=[1e-7, 1e-5, 1e-3])
     ap.add_argument("--dfp-batches", type=int, default=3)
+    ap.add_argument("--temporal-batches", type=int, default=10)
     ap.add_argument("--profile-run", action="store_true",
                     help="build the graph and run one solve capped at --max-iter sweeps (for ncu captures)")
     ap.add_argument("--max-iter", type=int, default=500)
@@ -478,6 +554,8 @@ def main():
         del g
         torch.cuda.empty_cache()
         extras["ppr_adjoint"] = measure_ppr(args)
+        if args.temporal_batches > 0:
+            extras["temporal"] = measure_temporal(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
