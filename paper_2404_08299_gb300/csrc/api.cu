@@ -942,23 +942,35 @@ int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t*
   const int32_t n = g->n;
   Csr& old = g->csr[PRDF_OUT];
   const int64_t m = old.m;
-  DBuf<uint8_t> deleted;
-  PRDF_TRY(deleted.alloc((size_t)m, s));
-  PRDF_CUDA(cudaMemsetAsync(deleted.p, 0, (size_t)m, s));
-  if (n_del) k_mark_deleted<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_src, del_dst, n_del, old.off.p, old.adj.p, deleted.p);
-  const int64_t tot = m + n_ins;
-  DBuf<int32_t> rows, cols;
-  DBuf<float> ww;
-  PRDF_TRY(rows.alloc(tot, s));
-  PRDF_TRY(cols.alloc(tot, s));
-  if (g->weighted) PRDF_TRY(ww.alloc(tot, s));
-  k_old_edges<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(n, old.off.p, old.adj.p, g->weighted ? old.w.p : nullptr,
-                                                                        deleted.p, rows.p, cols.p, ww.p);
-  if (n_ins) k_append<<<grid_for(n_ins, kThreads), kThreads, 0, s>>>(ins_src, ins_dst, ins_w, n_ins, m, rows.p, cols.p, ww.p);
-  PRDF_LAUNCH_CHECK();
   Csr nout, nin;
-  PRDF_TRY(build_csr(n, tot, rows.p, cols.p, ww.p, true, true, nout, g->ws, s));
-  PRDF_TRY(build_csr(n, tot, cols.p, rows.p, ww.p, true, true, nin, g->ws, s));
+  if (g->self_loops) {
+    // every vertex already has its self-loop: each row of G and of G' becomes
+    // (old \ D) u I, merged in order (batch_update.cu), no re-sort of the graph
+    PRDF_TRY(update_csr(n, g->csr[PRDF_OUT], del_src, del_dst, n_del, ins_src, ins_dst, ins_w, n_ins, nout, g->ws, s));
+    PRDF_TRY(update_csr(n, g->csr[PRDF_IN], del_dst, del_src, n_del, ins_dst, ins_src, ins_w, n_ins, nin, g->ws, s));
+  } else {
+    // rebuild from the edge list (which also gives every vertex its self-loop)
+    DBuf<uint8_t> deleted;
+    PRDF_TRY(deleted.alloc((size_t)m, s));
+    PRDF_CUDA(cudaMemsetAsync(deleted.p, 0, (size_t)m, s));
+    if (n_del)
+      k_mark_deleted<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_src, del_dst, n_del, old.off.p, old.adj.p,
+                                                                     deleted.p);
+    const int64_t tot = m + n_ins;
+    DBuf<int32_t> rows, cols;
+    DBuf<float> ww;
+    PRDF_TRY(rows.alloc(tot, s));
+    PRDF_TRY(cols.alloc(tot, s));
+    if (g->weighted) PRDF_TRY(ww.alloc(tot, s));
+    k_old_edges<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(n, old.off.p, old.adj.p,
+                                                                          g->weighted ? old.w.p : nullptr, deleted.p,
+                                                                          rows.p, cols.p, ww.p);
+    if (n_ins)
+      k_append<<<grid_for(n_ins, kThreads), kThreads, 0, s>>>(ins_src, ins_dst, ins_w, n_ins, m, rows.p, cols.p, ww.p);
+    PRDF_LAUNCH_CHECK();
+    PRDF_TRY(build_csr(n, tot, rows.p, cols.p, ww.p, true, true, nout, g->ws, s));
+    PRDF_TRY(build_csr(n, tot, cols.p, rows.p, ww.p, true, true, nin, g->ws, s));
+  }
   if (del_eff && n_del)
     k_effective<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_src, del_dst, n_del, 1, old.off.p, old.adj.p,
                                                                nout.off.p, nout.adj.p, del_eff);

@@ -1,0 +1,192 @@
+// Incremental batch update of one CSR (Sec. 3.3 set semantics): every row
+// becomes (old \ D) u I, merged in column order without re-sorting the
+// graph. The batch itself is turned into two small CSRs (D and I, sorted and
+// deduplicated per row, I keeping the maximum weight of duplicates); then
+//   - a D entry removes an element if it is in the old row;
+//   - an I entry adds an element unless it is in the old row and not deleted
+//     (then it only raises that edge's weight to the maximum);
+//   - each surviving old entry moves to
+//       new_off[u] + (j - off[u]) - #(D entries in old, col < c) + #(adding I entries, col < c),
+//   - each adding I entry to
+//       new_off[u] + #(old entries, col < c) - #(D entries in old, col < c) + #(adding I entries before it).
+// Rows without batch entries are a shifted copy. The result equals a rebuild
+// of the whole edge list when every vertex already has its self-loop.
+#include "internal.cuh"
+
+namespace prdf {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* a, int64_t lo, int64_t hi, int32_t c) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool contains(const int64_t* off, const int32_t* adj, int32_t u, int32_t c) {
+  const int64_t e = off[u + 1];
+  const int64_t p = lower_bound_i32(adj, off[u], e, c);
+  return p < e && adj[p] == c;
+}
+
+// row of CSR entry k: the last u with off[u] <= k
+__device__ __forceinline__ int32_t row_of(const int64_t* off, int32_t n, int64_t k) {
+  int32_t lo = 0, hi = n;  // off[lo] <= k < off[hi]
+  while (hi - lo > 1) {
+    const int32_t mid = lo + ((hi - lo) >> 1);
+    if (off[mid] <= k) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// deletion rows with self-loops masked out (self-loops are never deleted)
+__global__ void k_mask_self(const int32_t* __restrict__ r, const int32_t* __restrict__ c, int64_t cnt,
+                            int32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = r[i] == c[i] ? -1 : r[i];
+}
+
+// dflag[k] = D entry k is in the old row; iflag[k] = I entry k adds an element
+__global__ void k_batch_flags(int32_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                              const int64_t* __restrict__ d_off, const int32_t* __restrict__ d_adj, int64_t nd,
+                              const int64_t* __restrict__ i_off, const int32_t* __restrict__ i_adj, int64_t ni,
+                              uint32_t* __restrict__ dflag, uint32_t* __restrict__ iflag) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nd + ni; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k < nd) {
+      const int32_t u = row_of(d_off, n, k);
+      dflag[k] = contains(off, adj, u, d_adj[k]) ? 1u : 0u;
+    } else {
+      const int64_t q = k - nd;
+      const int32_t u = row_of(i_off, n, q);
+      const int32_t c = i_adj[q];
+      const bool surviving = contains(off, adj, u, c) && !contains(d_off, d_adj, u, c);
+      iflag[q] = surviving ? 0u : 1u;
+    }
+  }
+}
+
+// new row lengths: old - removed + added (dpref, ipref: exclusive scans of the flags)
+__global__ void k_new_len(int32_t n, const int64_t* __restrict__ off, const int64_t* __restrict__ d_off,
+                          const int64_t* __restrict__ dpref, const int64_t* __restrict__ i_off,
+                          const int64_t* __restrict__ ipref, int64_t* __restrict__ len) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t removed = dpref[d_off[u + 1]] - dpref[d_off[u]];
+    const int64_t added = ipref[i_off[u + 1]] - ipref[i_off[u]];
+    len[u] = (off[u + 1] - off[u]) - removed + added;
+  }
+}
+
+// surviving old entries (warp per row); a re-inserted surviving edge keeps the larger weight
+__global__ void k_move_old(int32_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                           const float* __restrict__ w, const int64_t* __restrict__ d_off,
+                           const int32_t* __restrict__ d_adj, const int64_t* __restrict__ dpref,
+                           const int64_t* __restrict__ i_off, const int32_t* __restrict__ i_adj,
+                           const float* __restrict__ i_w, const int64_t* __restrict__ ipref,
+                           const int64_t* __restrict__ noff, int32_t* __restrict__ nadj, float* __restrict__ nw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    const int64_t b = off[u], e = off[u + 1], nb = noff[u];
+    const int64_t db = d_off[u], de = d_off[u + 1], ib = i_off[u], ie = i_off[u + 1];
+    if (db == de && ib == ie) {
+      for (int64_t j = b + lane; j < e; j += 32) {
+        nadj[nb + (j - b)] = adj[j];
+        if (nw) nw[nb + (j - b)] = w[j];
+      }
+      continue;
+    }
+    for (int64_t j = b + lane; j < e; j += 32) {
+      const int32_t c = adj[j];
+      const int64_t p = lower_bound_i32(d_adj, db, de, c);
+      if (p < de && d_adj[p] == c) continue;  // deleted (a re-insertion is placed by k_place_new)
+      const int64_t q = lower_bound_i32(i_adj, ib, ie, c);
+      const int64_t pos = nb + (j - b) - (dpref[p] - dpref[db]) + (ipref[q] - ipref[ib]);
+      nadj[pos] = c;
+      if (nw) nw[pos] = (q < ie && i_adj[q] == c) ? fmaxf(w[j], i_w[q]) : w[j];
+    }
+  }
+}
+
+// adding I entries (thread per entry)
+__global__ void k_place_new(int32_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                            const int64_t* __restrict__ d_off, const int32_t* __restrict__ d_adj,
+                            const int64_t* __restrict__ dpref, const int64_t* __restrict__ i_off,
+                            const int32_t* __restrict__ i_adj, const float* __restrict__ i_w,
+                            const uint32_t* __restrict__ iflag, const int64_t* __restrict__ ipref, int64_t ni,
+                            const int64_t* __restrict__ noff, int32_t* __restrict__ nadj, float* __restrict__ nw) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ni; k += (int64_t)gridDim.x * blockDim.x) {
+    if (!iflag[k]) continue;
+    const int32_t u = row_of(i_off, n, k);
+    const int32_t c = i_adj[k];
+    const int64_t old_before = lower_bound_i32(adj, off[u], off[u + 1], c) - off[u];
+    const int64_t db = d_off[u];
+    const int64_t p = lower_bound_i32(d_adj, db, d_off[u + 1], c);
+    const int64_t pos = noff[u] + old_before - (dpref[p] - dpref[db]) + (ipref[k] - ipref[i_off[u]]);
+    nadj[pos] = c;
+    if (nw) nw[pos] = i_w[k];
+  }
+}
+
+}  // namespace
+
+int update_csr(int32_t n, const Csr& old, const int32_t* del_rows, const int32_t* del_cols, int64_t n_del,
+               const int32_t* ins_rows, const int32_t* ins_cols, const float* ins_w, int64_t n_ins, Csr& out,
+               Workspace& ws, cudaStream_t s) {
+  const bool weighted = old.w.p != nullptr;
+  // the batch as two small CSRs over the same rows
+  Csr D, I;
+  {
+    DBuf<int32_t> dr;
+    PRDF_TRY(dr.alloc((size_t)(n_del > 0 ? n_del : 1), s));
+    if (n_del > 0) {
+      k_mask_self<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_rows, del_cols, n_del, dr.p);
+      PRDF_LAUNCH_CHECK();
+    }
+    PRDF_TRY(build_csr(n, n_del, dr.p, del_cols, nullptr, false, true, D, ws, s));
+  }
+  PRDF_TRY(build_csr(n, n_ins, ins_rows, ins_cols, weighted ? ins_w : nullptr, false, false, I, ws, s));
+  const int64_t nd = D.m, ni = I.m;
+  DBuf<uint32_t> dflag, iflag;
+  DBuf<int64_t> dpref, ipref;
+  PRDF_TRY(dflag.alloc((size_t)(nd > 0 ? nd : 1), s));
+  PRDF_TRY(iflag.alloc((size_t)(ni > 0 ? ni : 1), s));
+  PRDF_TRY(dpref.alloc((size_t)nd + 1, s));
+  PRDF_TRY(ipref.alloc((size_t)ni + 1, s));
+  if (nd + ni > 0) {
+    k_batch_flags<<<grid_for(nd + ni, kThreads), kThreads, 0, s>>>(n, old.off.p, old.adj.p, D.off.p, D.adj.p, nd,
+                                                                   I.off.p, I.adj.p, ni, dflag.p, iflag.p);
+    PRDF_LAUNCH_CHECK();
+  }
+  PRDF_TRY(exclusive_scan_u32(dflag.p, nd, dpref.p, ws, s));
+  PRDF_TRY(exclusive_scan_u32(iflag.p, ni, ipref.p, ws, s));
+  DBuf<int64_t> len;
+  PRDF_TRY(len.alloc((size_t)n, s));
+  k_new_len<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, old.off.p, D.off.p, dpref.p, I.off.p, ipref.p, len.p);
+  PRDF_LAUNCH_CHECK();
+  PRDF_TRY(out.off.alloc((size_t)n + 1, s));
+  PRDF_TRY(exclusive_scan_i64(len.p, n, out.off.p, ws, s));
+  PRDF_CUDA(cudaMemcpyAsync(ws.host_i64, out.off.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  out.m = ws.host_i64[0];
+  PRDF_TRY(out.adj.alloc((size_t)(out.m > 0 ? out.m : 1), s));
+  if (weighted) PRDF_TRY(out.w.alloc((size_t)(out.m > 0 ? out.m : 1), s));
+  else out.w.release();
+  k_move_old<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(
+      n, old.off.p, old.adj.p, old.w.p, D.off.p, D.adj.p, dpref.p, I.off.p, I.adj.p, weighted ? I.w.p : nullptr,
+      ipref.p, out.off.p, out.adj.p, out.w.p);
+  PRDF_LAUNCH_CHECK();
+  if (ni > 0) {
+    k_place_new<<<grid_for(ni, kThreads), kThreads, 0, s>>>(n, old.off.p, old.adj.p, D.off.p, D.adj.p, dpref.p,
+                                                            I.off.p, I.adj.p, weighted ? I.w.p : nullptr, iflag.p,
+                                                            ipref.p, ni, out.off.p, out.adj.p, out.w.p);
+    PRDF_LAUNCH_CHECK();
+  }
+  return PRDF_OK;
+}
+
+}  // namespace prdf

@@ -50,6 +50,16 @@ struct Csr {
 int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, const float* w, bool self_loops,
               bool allow_skip, Csr& out, Workspace& ws, cudaStream_t s);
 
+// Batch update of one CSR with set semantics (Sec. 3.3): out gets rows
+// (old \ D) u I in column order, merged without re-sorting (batch_update.cu).
+// D: (del_rows[i], del_cols[i]), self-loops ignored; I: (ins_rows[i],
+// ins_cols[i]) with weights ins_w when old is weighted (duplicates and
+// re-inserted surviving edges keep the maximum). Equal to a rebuild when
+// every row of old holds its own vertex.
+int update_csr(int32_t n, const Csr& old, const int32_t* del_rows, const int32_t* del_cols, int64_t n_del,
+               const int32_t* ins_rows, const int32_t* ins_cols, const float* ins_w, int64_t n_ins, Csr& out,
+               Workspace& ws, cudaStream_t s);
+
 // The graph renumbered so that each in-degree class is a contiguous id range
 // (new id i = vertex perm[i], perm being the in-degree partition).
 struct Relabel {

@@ -151,6 +151,62 @@ def test_apply_batch_empty_and_consecutive():
         check_csr(g, og)
 
 
+def test_apply_batch_weighted_set_semantics():
+    """Weighted rows after a batch: (old \\ D) u I per row; an edge that survives and is inserted again keeps
+    the larger weight, a deleted edge inserted again takes the inserted weight, duplicates take their maximum,
+    self-loops are never deleted."""
+    n, s, d = synth.rmat(10, 8000, seed=21)
+    loops = np.arange(n, dtype=np.int32)
+    s2, d2 = np.concatenate([s, loops]), np.concatenate([d, loops])
+    w0 = synth.edge_weights(s2, d2, seed=21)
+    g = gpu_graph(n, s2, d2, w0)
+    off, adj, ww = (host(x) for x in g.export_csr(prdf().PRDF_OUT))
+    rows = np.repeat(np.arange(n), np.diff(off))
+    old = {(int(a), int(b)): float(x) for a, b, x in zip(rows, adj, ww)}
+    ds, dd, is_, id_ = synth.batch(n, off, adj, 300, seed=21, s1=2)
+    nonself = [(a, b) for (a, b) in old if a != b]
+    rng = np.random.default_rng(5)
+    keep = [nonself[i] for i in rng.choice(len(nonself), 6, replace=False)]
+    ds = np.concatenate([ds, [keep[0][0], keep[1][0], 3]]).astype(np.int32)       # two more deletions + a self-loop
+    dd = np.concatenate([dd, [keep[0][1], keep[1][1], 3]]).astype(np.int32)
+    is_ = np.concatenate([is_, [keep[0][0], keep[2][0], keep[2][0], 3]]).astype(np.int32)  # re-insert deleted,
+    id_ = np.concatenate([id_, [keep[0][1], keep[2][1], keep[2][1], 3]]).astype(np.int32)  # re-insert twice, loop
+    iw = rng.uniform(0.5, 1.5, len(is_)).astype(np.float32)
+    de, ie = g.apply_batch(dev(ds), dev(dd), dev(is_), dev(id_), ins_w=dev(iw))
+    want = dict(old)
+    for a, b in zip(ds.tolist(), dd.tolist()):
+        if a != b:
+            want.pop((a, b), None)
+    survivors = set(want)
+    ins_best = {}
+    for a, b, x in zip(is_.tolist(), id_.tolist(), iw.tolist()):
+        ins_best[(a, b)] = max(ins_best.get((a, b), 0.0), x)
+    for e, x in ins_best.items():
+        want[e] = max(want[e], x) if e in survivors else x
+    P = prdf()
+    for which, flip in ((P.PRDF_OUT, False), (P.PRDF_IN, True)):
+        off1, adj1, w1 = (host(x) for x in g.export_csr(which))
+        r1 = np.repeat(np.arange(n), np.diff(off1))
+        got = {((int(b), int(a)) if flip else (int(a), int(b))): float(x) for a, b, x in zip(r1, adj1, w1)}
+        assert got.keys() == want.keys()
+        assert all(np.float32(got[e]) == np.float32(want[e]) for e in want)
+        for u in range(n):  # rows stay sorted
+            assert np.all(np.diff(adj1[off1[u]:off1[u + 1]]) > 0)
+    assert np.array_equal(host(de), np.array([(a, b) in old and a != b and (a, b) not in want for a, b in
+                                              zip(ds.tolist(), dd.tolist())], np.uint8))
+
+
+def test_apply_batch_on_graph_without_self_loops_rebuilds():
+    """A graph created without self-loops is rebuilt by a batch update, which gives every vertex its self-loop."""
+    n, s, d = synth.rmat(9, 3000, seed=22)
+    g = prdf().Graph(n, dev(s), dev(d), self_loops=False)
+    og = oracle.graph(n, s, d)
+    ds, dd, is_, id_ = synth.batch(n, og.out_off, og.out_adj, 40, seed=22, s1=1)
+    g.apply_batch(dev(ds), dev(dd), dev(is_), dev(id_))
+    og1, _, _ = oracle.apply_batch(og, ds, dd, is_, id_)
+    check_csr(g, og1)
+
+
 def test_initial_and_expand_affected_bit_exact():
     n, s, d = synth.rmat(13, 120000, seed=4)
     g = gpu_graph(n, s, d)
