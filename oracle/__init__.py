@@ -82,6 +82,7 @@ def _l():
         lib.oracle_ppr.argtypes = [i32, ci, P, P, P, P, f64, f64, ci, P, P, P]
         lib.oracle_ppr_adjoint.argtypes = [i32, ci, P, P, P, P, P, P, f64, f64, ci, P, P, P, P]
         lib.oracle_num_threads.restype = ci
+        lib.oracle_set_threads.argtypes = [ci]
         _lib = lib
     return _lib
 
@@ -95,6 +96,11 @@ def _p(a):
         return None
     assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(k: int) -> None:
+    """OpenMP thread count of later oracle calls."""
+    _l().oracle_set_threads(int(k))
 
 
 def num_threads() -> int:

@@ -538,6 +538,16 @@ int oracle_ppr_adjoint(int32_t n, int K, const int64_t* out_off, const int32_t* 
   return 0;
 }
 
+/* Set the OpenMP thread count of later calls (no effect without OpenMP). */
+void oracle_set_threads(int k) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  if (k > 0) omp_set_num_threads(k);
+#else
+  (void)k;
+#endif
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   extern int omp_get_max_threads(void);
