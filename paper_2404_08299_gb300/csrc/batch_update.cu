@@ -9,7 +9,8 @@
 //       new_off[u] + (j - off[u]) - #(D entries in old, col < c) + #(adding I entries, col < c),
 //   - each adding I entry to
 //       new_off[u] + #(old entries, col < c) - #(D entries in old, col < c) + #(adding I entries before it).
-// Rows without batch entries are a shifted copy. The result equals a rebuild
+// Rows without batch entries are copied edge-parallel in contiguous segments
+// between the changed rows, each with one shift. The result equals a rebuild
 // of the whole edge list when every vertex already has its self-loop.
 #include "internal.cuh"
 
@@ -80,34 +81,97 @@ __global__ void k_new_len(int32_t n, const int64_t* __restrict__ off, const int6
   }
 }
 
-// surviving old entries (warp per row); a re-inserted surviving edge keeps the larger weight
-__global__ void k_move_old(int32_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                           const float* __restrict__ w, const int64_t* __restrict__ d_off,
-                           const int32_t* __restrict__ d_adj, const int64_t* __restrict__ dpref,
-                           const int64_t* __restrict__ i_off, const int32_t* __restrict__ i_adj,
-                           const float* __restrict__ i_w, const int64_t* __restrict__ ipref,
-                           const int64_t* __restrict__ noff, int32_t* __restrict__ nadj, float* __restrict__ nw) {
+// rows with batch entries, listed in ascending order (flag, exclusive scan, list)
+__global__ void k_mark_changed(int32_t n, const int64_t* __restrict__ d_off, const int64_t* __restrict__ i_off,
+                               uint32_t* __restrict__ flag) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    flag[u] = (d_off[u + 1] > d_off[u] || i_off[u + 1] > i_off[u]) ? 1u : 0u;
+}
+
+__global__ void k_list_changed(int32_t n, const uint32_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                               int32_t* __restrict__ changed) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    if (flag[u]) changed[pos[u]] = (int32_t)u;
+}
+
+// Old entries of unchanged rows. Between two changed rows every entry moves by
+// the same amount: noff[c] - off[c] of the next changed row c (new_m - m after
+// the last one). A warp takes 256 consecutive entries (8 per lane,
+// lane-strided, so loads and stores stay coalesced) and finds its place in the
+// changed-row list once.
+__global__ void k_copy_unchanged(int32_t n, int64_t m, const int64_t* __restrict__ off,
+                                 const int64_t* __restrict__ noff, const int32_t* __restrict__ changed, int64_t k,
+                                 const int32_t* __restrict__ adj, const float* __restrict__ w,
+                                 int32_t* __restrict__ nadj, float* __restrict__ nw) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = warp; u < n; u += nwarps) {
-    const int64_t b = off[u], e = off[u + 1], nb = noff[u];
-    const int64_t db = d_off[u], de = d_off[u + 1], ib = i_off[u], ie = i_off[u + 1];
-    if (db == de && ib == ie) {
-      for (int64_t j = b + lane; j < e; j += 32) {
-        nadj[nb + (j - b)] = adj[j];
-        if (nw) nw[nb + (j - b)] = w[j];
-      }
-      continue;
+  const int64_t tail_shift = noff[n] - off[n];
+  for (int64_t base = warp * 256; base < m; base += nwarps * 256) {
+    // t = number of changed rows that start at or before base
+    int64_t lo = 0, hi = k;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (off[changed[mid]] <= base) lo = mid + 1; else hi = mid;
     }
-    for (int64_t j = b + lane; j < e; j += 32) {
+    int64_t t = lo;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t j = base + lane + 32 * q;
+      if (j >= m) break;
+      while (t < k && off[changed[t]] <= j) ++t;
+      if (t > 0 && j < off[changed[t - 1] + 1]) continue;  // an entry of a changed row
+      const int64_t to = j + (t < k ? noff[changed[t]] - off[changed[t]] : tail_shift);
+      nadj[to] = adj[j];
+      if (nw) nw[to] = w[j];
+    }
+  }
+}
+
+// length of each changed row (for the entry-parallel pass below)
+__global__ void k_changed_len(const int32_t* __restrict__ changed, int64_t k, const int64_t* __restrict__ off,
+                              int64_t* __restrict__ len) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < k; r += (int64_t)gridDim.x * blockDim.x)
+    len[r] = off[changed[r] + 1] - off[changed[r]];
+}
+
+// Surviving old entries of the changed rows, entry-parallel over their
+// concatenation (cpref: exclusive scan of the row lengths, total T), 256
+// entries per warp so that long rows spread over many warps; a re-inserted
+// surviving edge keeps the larger weight.
+__global__ void k_move_changed(const int32_t* __restrict__ changed, int64_t k, const int64_t* __restrict__ cpref,
+                               int64_t T, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                               const float* __restrict__ w, const int64_t* __restrict__ d_off,
+                               const int32_t* __restrict__ d_adj, const int64_t* __restrict__ dpref,
+                               const int64_t* __restrict__ i_off, const int32_t* __restrict__ i_adj,
+                               const float* __restrict__ i_w, const int64_t* __restrict__ ipref,
+                               const int64_t* __restrict__ noff, int32_t* __restrict__ nadj, float* __restrict__ nw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 256; base < T; base += nwarps * 256) {
+    // r = the changed row holding entry base: the last r with cpref[r] <= base
+    int64_t lo = 0, hi = k;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (cpref[mid] <= base) lo = mid; else hi = mid;
+    }
+    int64_t r = lo;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t x = base + lane + 32 * q;
+      if (x >= T) break;
+      while (cpref[r + 1] <= x) ++r;
+      const int32_t u = changed[r];
+      const int64_t b = off[u], j = b + (x - cpref[r]);
+      const int64_t db = d_off[u], de = d_off[u + 1], ib = i_off[u], ie = i_off[u + 1];
       const int32_t c = adj[j];
       const int64_t p = lower_bound_i32(d_adj, db, de, c);
       if (p < de && d_adj[p] == c) continue;  // deleted (a re-insertion is placed by k_place_new)
-      const int64_t q = lower_bound_i32(i_adj, ib, ie, c);
-      const int64_t pos = nb + (j - b) - (dpref[p] - dpref[db]) + (ipref[q] - ipref[ib]);
+      const int64_t qq = lower_bound_i32(i_adj, ib, ie, c);
+      const int64_t pos = noff[u] + (j - b) - (dpref[p] - dpref[db]) + (ipref[qq] - ipref[ib]);
       nadj[pos] = c;
-      if (nw) nw[pos] = (q < ie && i_adj[q] == c) ? fmaxf(w[j], i_w[q]) : w[j];
+      if (nw) nw[pos] = (qq < ie && i_adj[qq] == c) ? fmaxf(w[j], i_w[qq]) : w[j];
     }
   }
 }
@@ -176,10 +240,45 @@ int update_csr(int32_t n, const Csr& old, const int32_t* del_rows, const int32_t
   PRDF_TRY(out.adj.alloc((size_t)(out.m > 0 ? out.m : 1), s));
   if (weighted) PRDF_TRY(out.w.alloc((size_t)(out.m > 0 ? out.m : 1), s));
   else out.w.release();
-  k_move_old<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(
-      n, old.off.p, old.adj.p, old.w.p, D.off.p, D.adj.p, dpref.p, I.off.p, I.adj.p, weighted ? I.w.p : nullptr,
-      ipref.p, out.off.p, out.adj.p, out.w.p);
+  // the changed rows (those with batch entries), ascending
+  DBuf<uint32_t> cflag;
+  DBuf<int64_t> cpos;
+  PRDF_TRY(cflag.alloc((size_t)n, s));
+  PRDF_TRY(cpos.alloc((size_t)n + 1, s));
+  k_mark_changed<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, D.off.p, I.off.p, cflag.p);
   PRDF_LAUNCH_CHECK();
+  PRDF_TRY(exclusive_scan_u32(cflag.p, n, cpos.p, ws, s));
+  PRDF_CUDA(cudaMemcpyAsync(ws.host_i64, cpos.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  const int64_t k = ws.host_i64[0];
+  DBuf<int32_t> changed;
+  PRDF_TRY(changed.alloc((size_t)(k > 0 ? k : 1), s));
+  if (k > 0) {
+    k_list_changed<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, cflag.p, cpos.p, changed.p);
+    PRDF_LAUNCH_CHECK();
+  }
+  if (old.m > 0) {
+    k_copy_unchanged<<<grid_for((old.m + 7) / 8, kThreads), kThreads, 0, s>>>(
+        n, old.m, old.off.p, out.off.p, changed.p, k, old.adj.p, old.w.p, out.adj.p, out.w.p);
+    PRDF_LAUNCH_CHECK();
+  }
+  if (k > 0) {
+    DBuf<int64_t> clen, cpref;
+    PRDF_TRY(clen.alloc((size_t)k, s));
+    PRDF_TRY(cpref.alloc((size_t)k + 1, s));
+    k_changed_len<<<grid_for(k, kThreads), kThreads, 0, s>>>(changed.p, k, old.off.p, clen.p);
+    PRDF_LAUNCH_CHECK();
+    PRDF_TRY(exclusive_scan_i64(clen.p, k, cpref.p, ws, s));
+    PRDF_CUDA(cudaMemcpyAsync(ws.host_i64, cpref.p + k, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    PRDF_CUDA(cudaStreamSynchronize(s));
+    const int64_t T = ws.host_i64[0];
+    if (T > 0) {
+      k_move_changed<<<grid_for((T + 7) / 8, kThreads), kThreads, 0, s>>>(
+          changed.p, k, cpref.p, T, old.off.p, old.adj.p, old.w.p, D.off.p, D.adj.p, dpref.p, I.off.p, I.adj.p,
+          weighted ? I.w.p : nullptr, ipref.p, out.off.p, out.adj.p, out.w.p);
+      PRDF_LAUNCH_CHECK();
+    }
+  }
   if (ni > 0) {
     k_place_new<<<grid_for(ni, kThreads), kThreads, 0, s>>>(n, old.off.p, old.adj.p, D.off.p, D.adj.p, dpref.p,
                                                             I.off.p, I.adj.p, weighted ? I.w.p : nullptr, iflag.p,
