@@ -7,7 +7,10 @@
 //   per-row sort + unique, by row-length class:
 //     <= 8      one thread, 19-comparator sorting network in registers
 //     <= 32     one warp, bitonic network over shuffles
-//     <= 16384  one block, bitonic sort in shared memory
+//     <= 256    one warp, 8 keys per lane in registers, bitonic network
+//               (in-lane exchanges below distance 8, shuffles above)
+//     <= 2048   a 128-thread block, bitonic sort in 16 KB of shared memory
+//     <= 16384  a 512-thread block, bitonic sort in 128 KB of shared memory
 //     larger    one bit per possible column (bitmap), emitted in order
 //   -> exclusive scan of unique counts -> compaction into the final CSR.
 // Rows are sorted by 64-bit composite keys (column << 32 | ~weight bits), so
@@ -21,7 +24,10 @@ namespace {
 constexpr uint64_t kSent = ~0ull;
 constexpr int kThrThread = 8;
 constexpr int kThrWarp = 32;
+constexpr int kThrWarp8 = 256;
+constexpr int kThrSmallBlock = 2048;
 constexpr int kThrBlock = 16384;
+constexpr int kSmallBlockThreads = 128;
 constexpr int kSortBlockThreads = 512;
 constexpr int64_t kBitmapBudget = 512ll << 20;  // bytes of row bitmaps per pass
 constexpr int kHugeWordsPerThread = 32;
@@ -144,6 +150,78 @@ __global__ void k_sort_warp(const int32_t* __restrict__ list, int64_t count, con
   }
 }
 
+// ---- rows of length <= 256: one warp, 8 keys per lane (element e = 8 * lane + q) ----
+__global__ void k_sort_warp8(const int32_t* __restrict__ list, int64_t count, const int64_t* __restrict__ start,
+                             const uint64_t* __restrict__ tmp, uint64_t* __restrict__ out,
+                             uint32_t* __restrict__ ucnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < count; i += nwarps) {
+    const int32_t v = list[i];
+    const int64_t b = start[v];
+    const int L = (int)(start[v + 1] - b);
+    uint64_t k[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = 8 * lane + q;
+      k[q] = e < L ? tmp[b + e] : kSent;
+    }
+#pragma unroll
+    for (int kk = 2; kk <= 256; kk <<= 1) {
+#pragma unroll
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        if (j >= 8) {
+          // partner e ^ j lives in lane ^ (j / 8), same register
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const uint64_t o = __shfl_xor_sync(0xffffffffu, k[q], j >> 3);
+            const int e = 8 * lane + q;
+            const bool up = (e & kk) == 0;
+            const bool lower = (e & j) == 0;
+            k[q] = (lower == up) ? (k[q] < o ? k[q] : o) : (k[q] < o ? o : k[q]);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int p = q ^ j;
+            if (p > q) {
+              const int e = 8 * lane + q;
+              const bool up = (e & kk) == 0;
+              if ((k[q] > k[p]) == up) {
+                const uint64_t t = k[q];
+                k[q] = k[p];
+                k[p] = t;
+              }
+            }
+          }
+        }
+      }
+    }
+    // first entry of each column run, written in order
+    const uint64_t before = __shfl_up_sync(0xffffffffu, k[7], 1);
+    uint32_t keep = 0, cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint64_t prev = q > 0 ? k[q - 1] : before;
+      const bool first = k[q] != kSent && ((lane == 0 && q == 0) || key_col(prev) != key_col(k[q]));
+      keep |= first ? (1u << q) : 0u;
+      cnt += first ? 1u : 0u;
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    uint32_t pos = incl - cnt;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (keep & (1u << q)) out[b + pos++] = k[q];
+    if (lane == 31) ucnt[v] = incl;
+  }
+}
+
 // block-wide exclusive scan for NT threads (NT a multiple of 32, <= 1024)
 template <int NT>
 __device__ __forceinline__ uint32_t block_scan_u32(uint32_t v, uint32_t* total, uint32_t* sh /* NT/32 */) {
@@ -173,14 +251,14 @@ __device__ __forceinline__ uint32_t block_scan_u32(uint32_t v, uint32_t* total, 
   return r;
 }
 
-// ---- rows of length <= 16384: one block, bitonic sort in shared memory ----
-__global__ void __launch_bounds__(kSortBlockThreads) k_sort_block(const int32_t* __restrict__ list, int64_t count,
-                                                                  const int64_t* __restrict__ start,
-                                                                  const uint64_t* __restrict__ tmp,
-                                                                  uint64_t* __restrict__ out,
-                                                                  uint32_t* __restrict__ ucnt) {
+// ---- rows up to the block's shared-memory keys: one block of NT threads,
+// bitonic sort in shared memory ----
+template <int NT>
+__global__ void __launch_bounds__(NT) k_sort_block(const int32_t* __restrict__ list, int64_t count,
+                                                   const int64_t* __restrict__ start, const uint64_t* __restrict__ tmp,
+                                                   uint64_t* __restrict__ out, uint32_t* __restrict__ ucnt) {
   extern __shared__ uint64_t sk[];
-  __shared__ uint32_t scan_sh[kSortBlockThreads / 32];
+  __shared__ uint32_t scan_sh[NT / 32];
   __shared__ uint32_t total;
   for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
     const int32_t v = list[i];
@@ -188,11 +266,11 @@ __global__ void __launch_bounds__(kSortBlockThreads) k_sort_block(const int32_t*
     const int L = (int)(start[v + 1] - b);
     int P2 = 64;
     while (P2 < L) P2 <<= 1;
-    for (int j = threadIdx.x; j < P2; j += kSortBlockThreads) sk[j] = j < L ? tmp[b + j] : kSent;
+    for (int j = threadIdx.x; j < P2; j += NT) sk[j] = j < L ? tmp[b + j] : kSent;
     __syncthreads();
     for (int k = 2; k <= P2; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int t = threadIdx.x; t < P2; t += kSortBlockThreads) {
+        for (int t = threadIdx.x; t < P2; t += NT) {
           const int p = t ^ j;
           if (p > t) {
             const uint64_t a = sk[t], c = sk[p];
@@ -207,12 +285,12 @@ __global__ void __launch_bounds__(kSortBlockThreads) k_sort_block(const int32_t*
       }
     }
     // stable compaction of the first entry of each column run
-    const int per = P2 / kSortBlockThreads > 0 ? P2 / kSortBlockThreads : 1;
+    const int per = P2 / NT > 0 ? P2 / NT : 1;
     const int j0 = threadIdx.x * per;
     uint32_t mine = 0;
     for (int j = j0; j < j0 + per && j < P2; ++j)
       mine += (sk[j] != kSent && (j == 0 || key_col(sk[j]) != key_col(sk[j - 1]))) ? 1u : 0u;
-    uint32_t pos = block_scan_u32<kSortBlockThreads>(mine, &total, scan_sh);
+    uint32_t pos = block_scan_u32<NT>(mine, &total, scan_sh);
     for (int j = j0; j < j0 + per && j < P2; ++j)
       if (sk[j] != kSent && (j == 0 || key_col(sk[j]) != key_col(sk[j - 1]))) out[b + pos++] = sk[j];
     if (threadIdx.x == 0) ucnt[v] = total;
@@ -291,21 +369,62 @@ __global__ void k_huge_weights(const int32_t* __restrict__ rowlist, const int64_
   }
 }
 
+// Final CSR from the sorted row buckets: row v's ucnt[v] unique keys start at
+// start[v] and go to off[v]. Rows are taken in groups of 32; a light group (at
+// most kCompactGroup entries) is one warp walking the concatenation of its rows'
+// entries with all lanes (the row of an entry from a binary search over the
+// lanes' row starts by shuffles, in a loop with the same trip count on every
+// lane); the rows of heavier groups get a warp each in k_compact_heavy.
+constexpr int64_t kCompactGroup = 4096;
+
+__device__ __forceinline__ bool heavy32(const int64_t* off, int32_t n, int64_t v0) {
+  const int64_t last = v0 + 32 < n ? v0 + 32 : n;
+  return off[last] - off[v0] > kCompactGroup;
+}
+
+__device__ __forceinline__ void emit_key(uint64_t k, int32_t* adj, float* w, int64_t p) {
+  adj[p] = key_col(k);
+  if (w) {
+    const float x = key_w(k);
+    w[p] = x > 0.f ? x : 1.0f;  // an added self-loop carries weight 1
+  }
+}
+
 __global__ void k_compact(int32_t n, const int64_t* __restrict__ start, const uint64_t* __restrict__ sorted,
                           const int64_t* __restrict__ off, int32_t* __restrict__ adj, float* __restrict__ w) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = warp; v < n; v += nwarps) {
-    const int64_t b = start[v], o = off[v], L = off[v + 1] - o;
-    for (int64_t j = lane; j < L; j += 32) {
-      const uint64_t k = sorted[b + j];
-      adj[o + j] = key_col(k);
-      if (w) {
-        const float x = key_w(k);
-        w[o + j] = x > 0.f ? x : 1.0f;  // an added self-loop carries weight 1
+  for (int64_t v0 = warp * 32; v0 < n; v0 += nwarps * 32) {
+    if (heavy32(off, n, v0)) continue;
+    const int64_t v = v0 + lane;
+    const int64_t last = v0 + 32 < n ? v0 + 32 : n;
+    const int64_t ob = v < n ? off[v] : INT64_MAX;
+    const int64_t sb = v < n ? start[v] : 0;
+    const int64_t obeg = off[v0], oend = off[last];
+    for (int64_t base = obeg; base < oend; base += 32) {
+      const int64_t p = base + lane;
+      int r = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int64_t c = __shfl_sync(0xffffffffu, ob, r + step);
+        if (c <= p) r += step;
       }
+      const int64_t src = __shfl_sync(0xffffffffu, sb, r) + (p - __shfl_sync(0xffffffffu, ob, r));
+      if (p < oend) emit_key(sorted[src], adj, w, p);
     }
+  }
+}
+
+__global__ void k_compact_heavy(int32_t n, const int64_t* __restrict__ start, const uint64_t* __restrict__ sorted,
+                                const int64_t* __restrict__ off, int32_t* __restrict__ adj, float* __restrict__ w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    if (!heavy32(off, n, v & ~(int64_t)31)) continue;
+    const int64_t b = start[v], o = off[v], L = off[v + 1] - o;
+    for (int64_t j = lane; j < L; j += 32) emit_key(sorted[b + j], adj, w, o + j);
   }
 }
 
@@ -369,26 +488,36 @@ int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, c
   DBuf<int32_t> rowP;
   PRDF_TRY(rowP.alloc(N, s));
   PartThr t;
-  t.n = 3;
+  t.n = 5;
   t.thr[0] = kThrThread;
   t.thr[1] = kThrWarp;
-  t.thr[2] = kThrBlock;
-  int64_t cls[4];
+  t.thr[2] = kThrWarp8;
+  t.thr[3] = kThrSmallBlock;
+  t.thr[4] = kThrBlock;
+  int64_t cls[6];
   PRDF_TRY(partition_by_degree(start.p, N, t, rowP.p, cls, ws, s));
   const int32_t* l0 = rowP.p;
   const int32_t* l1 = l0 + cls[0];
   const int32_t* l2 = l1 + cls[1];
   const int32_t* l3 = l2 + cls[2];
+  const int32_t* l4 = l3 + cls[3];
+  const int32_t* l5 = l4 + cls[4];
   if (cls[0]) k_sort_thread<<<grid_for(cls[0], T), T, 0, s>>>(l0, cls[0], start.p, tmp.p, srt.p, ucnt.p);
   if (cls[1]) k_sort_warp<<<grid_for(cls[1] * 32, T), T, 0, s>>>(l1, cls[1], start.p, tmp.p, srt.p, ucnt.p);
-  if (cls[2]) {
+  if (cls[2]) k_sort_warp8<<<grid_for(cls[2] * 32, T), T, 0, s>>>(l2, cls[2], start.p, tmp.p, srt.p, ucnt.p);
+  if (cls[3]) {
+    const int smem = kThrSmallBlock * (int)sizeof(uint64_t);
+    k_sort_block<kSmallBlockThreads><<<grid_for(cls[3], 1, kSMs * 16), kSmallBlockThreads, smem, s>>>(
+        l3, cls[3], start.p, tmp.p, srt.p, ucnt.p);
+  }
+  if (cls[4]) {
     const int smem = kThrBlock * (int)sizeof(uint64_t);
-    PRDF_CUDA(cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    const int grid = (int)(cls[2] < kSMs * 2 ? cls[2] : kSMs * 2);
-    k_sort_block<<<grid, kSortBlockThreads, smem, s>>>(l2, cls[2], start.p, tmp.p, srt.p, ucnt.p);
+    PRDF_CUDA(cudaFuncSetAttribute(k_sort_block<kSortBlockThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int grid = (int)(cls[4] < kSMs * 2 ? cls[4] : kSMs * 2);
+    k_sort_block<kSortBlockThreads><<<grid, kSortBlockThreads, smem, s>>>(l4, cls[4], start.p, tmp.p, srt.p, ucnt.p);
   }
   PRDF_LAUNCH_CHECK();
-  if (cls[3]) {
+  if (cls[5]) {
     const int64_t words = (N + 31) / 32;
     const int64_t nchunks = (words + kHugeChunkWords - 1) / kHugeChunkWords;
     int64_t per = kBitmapBudget / (words * 4);
@@ -396,20 +525,20 @@ int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, c
     if (per > 65535) per = 65535;
     DBuf<uint32_t> bm;
     DBuf<int64_t> cc, ccoff;
-    const int64_t rows_batch = cls[3] < per ? cls[3] : per;
+    const int64_t rows_batch = cls[5] < per ? cls[5] : per;
     PRDF_TRY(bm.alloc(rows_batch * words, s));
     PRDF_TRY(cc.alloc(rows_batch * nchunks, s));
     PRDF_TRY(ccoff.alloc(rows_batch * nchunks + 1, s));
-    for (int64_t h0 = 0; h0 < cls[3]; h0 += rows_batch) {
-      const int64_t rb = (cls[3] - h0) < rows_batch ? (cls[3] - h0) : rows_batch;
+    for (int64_t h0 = 0; h0 < cls[5]; h0 += rows_batch) {
+      const int64_t rb = (cls[5] - h0) < rows_batch ? (cls[5] - h0) : rows_batch;
       PRDF_CUDA(cudaMemsetAsync(bm.p, 0, (size_t)(rb * words) * 4, s));
-      k_huge_set<<<dim3(64, (unsigned)rb), T, 0, s>>>(l3 + h0, start.p, tmp.p, bm.p, words);
+      k_huge_set<<<dim3(64, (unsigned)rb), T, 0, s>>>(l5 + h0, start.p, tmp.p, bm.p, words);
       k_huge_count<<<dim3((unsigned)nchunks, (unsigned)rb), 256, 0, s>>>(bm.p, words, nchunks, cc.p);
       PRDF_LAUNCH_CHECK();
       PRDF_TRY(exclusive_scan_i64(cc.p, rb * nchunks, ccoff.p, ws, s));
-      k_huge_emit<<<dim3((unsigned)nchunks, (unsigned)rb), 256, 0, s>>>(l3 + h0, start.p, bm.p, words, nchunks,
+      k_huge_emit<<<dim3((unsigned)nchunks, (unsigned)rb), 256, 0, s>>>(l5 + h0, start.p, bm.p, words, nchunks,
                                                                           ccoff.p, srt.p, ucnt.p);
-      if (w) k_huge_weights<<<dim3(64, (unsigned)rb), T, 0, s>>>(l3 + h0, start.p, tmp.p, ucnt.p, srt.p);
+      if (w) k_huge_weights<<<dim3(64, (unsigned)rb), T, 0, s>>>(l5 + h0, start.p, tmp.p, ucnt.p, srt.p);
       PRDF_LAUNCH_CHECK();
     }
   }
@@ -422,7 +551,8 @@ int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, c
   PRDF_TRY(out.adj.alloc(out.m > 0 ? out.m : 1, s));
   if (w) PRDF_TRY(out.w.alloc(out.m > 0 ? out.m : 1, s));
   else out.w.release();
-  k_compact<<<grid_for(N * 32, T), T, 0, s>>>(n, start.p, srt.p, out.off.p, out.adj.p, w ? out.w.p : nullptr);
+  k_compact<<<grid_for(N, T), T, 0, s>>>(n, start.p, srt.p, out.off.p, out.adj.p, w ? out.w.p : nullptr);
+  k_compact_heavy<<<grid_for(N * 32, T), T, 0, s>>>(n, start.p, srt.p, out.off.p, out.adj.p, w ? out.w.p : nullptr);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }
