@@ -369,62 +369,53 @@ __global__ void k_huge_weights(const int32_t* __restrict__ rowlist, const int64_
   }
 }
 
-// Final CSR from the sorted row buckets: row v's ucnt[v] unique keys start at
-// start[v] and go to off[v]. Rows are taken in groups of 32; a light group (at
-// most kCompactGroup entries) is one warp walking the concatenation of its rows'
-// entries with all lanes (the row of an entry from a binary search over the
-// lanes' row starts by shuffles, in a loop with the same trip count on every
-// lane); the rows of heavier groups get a warp each in k_compact_heavy.
-constexpr int64_t kCompactGroup = 4096;
+// Final CSR from the sorted row buckets: row v's unique keys start at
+// start[v] and go to off[v]. Balanced by entries, not rows: a warp takes
+// kCompactChunk consecutive output entries (lane-strided), finds the row of
+// the first one by binary search, and each lane walks rows forward (a few
+// steps, then a binary search past runs of empty rows).
+constexpr int64_t kCompactChunk = 1024;
 
-__device__ __forceinline__ bool heavy32(const int64_t* off, int32_t n, int64_t v0) {
-  const int64_t last = v0 + 32 < n ? v0 + 32 : n;
-  return off[last] - off[v0] > kCompactGroup;
-}
-
-__device__ __forceinline__ void emit_key(uint64_t k, int32_t* adj, float* w, int64_t p) {
-  adj[p] = key_col(k);
-  if (w) {
-    const float x = key_w(k);
-    w[p] = x > 0.f ? x : 1.0f;  // an added self-loop carries weight 1
-  }
-}
-
-__global__ void k_compact(int32_t n, const int64_t* __restrict__ start, const uint64_t* __restrict__ sorted,
-                          const int64_t* __restrict__ off, int32_t* __restrict__ adj, float* __restrict__ w) {
+__global__ void k_compact(int32_t n, int64_t m, const int64_t* __restrict__ start,
+                          const uint64_t* __restrict__ sorted, const int64_t* __restrict__ off,
+                          int32_t* __restrict__ adj, float* __restrict__ w) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v0 = warp * 32; v0 < n; v0 += nwarps * 32) {
-    if (heavy32(off, n, v0)) continue;
-    const int64_t v = v0 + lane;
-    const int64_t last = v0 + 32 < n ? v0 + 32 : n;
-    const int64_t ob = v < n ? off[v] : INT64_MAX;
-    const int64_t sb = v < n ? start[v] : 0;
-    const int64_t obeg = off[v0], oend = off[last];
-    for (int64_t base = obeg; base < oend; base += 32) {
-      const int64_t p = base + lane;
-      int r = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int64_t c = __shfl_sync(0xffffffffu, ob, r + step);
-        if (c <= p) r += step;
-      }
-      const int64_t src = __shfl_sync(0xffffffffu, sb, r) + (p - __shfl_sync(0xffffffffu, ob, r));
-      if (p < oend) emit_key(sorted[src], adj, w, p);
+  for (int64_t p0 = warp * kCompactChunk; p0 < m; p0 += nwarps * kCompactChunk) {
+    int64_t lo = 0, hi = n;  // the last row r with off[r] <= p0
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (off[mid] <= p0) lo = mid; else hi = mid;
     }
-  }
-}
-
-__global__ void k_compact_heavy(int32_t n, const int64_t* __restrict__ start, const uint64_t* __restrict__ sorted,
-                                const int64_t* __restrict__ off, int32_t* __restrict__ adj, float* __restrict__ w) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = warp; v < n; v += nwarps) {
-    if (!heavy32(off, n, v & ~(int64_t)31)) continue;
-    const int64_t b = start[v], o = off[v], L = off[v + 1] - o;
-    for (int64_t j = lane; j < L; j += 32) emit_key(sorted[b + j], adj, w, o + j);
+    int64_t r = lo, rs = off[r], re = off[r + 1], src = start[r];
+    for (int64_t p = p0 + lane; p < p0 + kCompactChunk && p < m; p += 32) {
+      if (p >= re) {
+        // a few steps forward, then a binary search (CSRs of small batches are mostly empty rows)
+        int steps = 0;
+        do {
+          ++r;
+          re = off[r + 1];
+        } while (p >= re && ++steps < 8);
+        if (p >= re) {
+          int64_t a = r, z = n;  // the last row with off[row] <= p
+          while (z - a > 1) {
+            const int64_t mid = (a + z) >> 1;
+            if (off[mid] <= p) a = mid; else z = mid;
+          }
+          r = a;
+          re = off[r + 1];
+        }
+        rs = off[r];
+        src = start[r];
+      }
+      const uint64_t k = sorted[src + (p - rs)];
+      adj[p] = key_col(k);
+      if (w) {
+        const float x = key_w(k);
+        w[p] = x > 0.f ? x : 1.0f;  // an added self-loop carries weight 1
+      }
+    }
   }
 }
 
@@ -551,8 +542,9 @@ int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, c
   PRDF_TRY(out.adj.alloc(out.m > 0 ? out.m : 1, s));
   if (w) PRDF_TRY(out.w.alloc(out.m > 0 ? out.m : 1, s));
   else out.w.release();
-  k_compact<<<grid_for(N, T), T, 0, s>>>(n, start.p, srt.p, out.off.p, out.adj.p, w ? out.w.p : nullptr);
-  k_compact_heavy<<<grid_for(N * 32, T), T, 0, s>>>(n, start.p, srt.p, out.off.p, out.adj.p, w ? out.w.p : nullptr);
+  if (out.m > 0)
+    k_compact<<<grid_for((out.m + kCompactChunk - 1) / kCompactChunk * 32, T), T, 0, s>>>(
+        n, out.m, start.p, srt.p, out.off.p, out.adj.p, w ? out.w.p : nullptr);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }

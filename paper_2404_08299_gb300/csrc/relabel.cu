@@ -37,66 +37,52 @@ __global__ void k_perm_rowlen(const int64_t* __restrict__ off, const int32_t* __
 }
 
 // new row i = old row perm[i], neighbour ids mapped through inv (weights
-// carried along when present). New rows are taken in groups of 32. A light
-// group (at most kPermGroupEntries entries) is one warp walking the
-// concatenation of its rows' entries with all lanes, so that short rows leave
-// no lane idle; the row of an entry is found by a binary search over the
-// lanes' row starts (shuffles), in a loop with the same trip count on every
-// lane. The rows of heavier groups (the highest in-degree classes) get a warp
-// each in k_perm_rows_heavy.
-constexpr int64_t kPermGroupEntries = 4096;
-
-__device__ __forceinline__ bool heavy_group(const int64_t* noff, int32_t n, int64_t i0) {
-  const int64_t last = i0 + 32 < n ? i0 + 32 : n;
-  return noff[last] - noff[i0] > kPermGroupEntries;
-}
+// carried along when present). Balanced by entries, not rows: a warp takes
+// kPermChunk consecutive entries of the new CSR (lane-strided, so stores stay
+// coalesced), finds the row of the first one by binary search, and each lane
+// walks rows forward for its own entries (a few steps, then a binary search
+// past runs of empty rows). Long rows spread over many warps, short rows pack
+// densely.
+constexpr int64_t kPermChunk = 1024;
 
 __global__ void k_perm_rows(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                             const float* __restrict__ w, const int32_t* __restrict__ perm,
-                            const int32_t* __restrict__ inv, int32_t n, const int64_t* __restrict__ noff,
+                            const int32_t* __restrict__ inv, int32_t n, int64_t m, const int64_t* __restrict__ noff,
                             int32_t* __restrict__ nadj, float* __restrict__ nw) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i0 = warp * 32; i0 < n; i0 += nwarps * 32) {
-    if (heavy_group(noff, n, i0)) continue;
-    const int64_t i = i0 + lane;
-    const int64_t last = i0 + 32 < n ? i0 + 32 : n;
-    // this lane's row: destination start (past the end for lanes beyond n) and source start
-    const int64_t nb = i < n ? noff[i] : INT64_MAX;
-    const int64_t so = i < n ? off[perm[i]] : 0;
-    const int64_t nbeg = noff[i0], nend = noff[last];
-    for (int64_t base = nbeg; base < nend; base += 32) {
-      const int64_t p = base + lane;
-      int r = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int64_t c = __shfl_sync(0xffffffffu, nb, r + step);
-        if (c <= p) r += step;
-      }
-      const int64_t src = __shfl_sync(0xffffffffu, so, r) + (p - __shfl_sync(0xffffffffu, nb, r));
-      if (p < nend) {
-        nadj[p] = inv[adj[src]];
-        if (w) nw[p] = w[src];
-      }
+  for (int64_t p0 = warp * kPermChunk; p0 < m; p0 += nwarps * kPermChunk) {
+    // row of entry p0: the last r with noff[r] <= p0
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (noff[mid] <= p0) lo = mid; else hi = mid;
     }
-  }
-}
-
-__global__ void k_perm_rows_heavy(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                                  const float* __restrict__ w, const int32_t* __restrict__ perm,
-                                  const int32_t* __restrict__ inv, int32_t n, const int64_t* __restrict__ noff,
-                                  int32_t* __restrict__ nadj, float* __restrict__ nw) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp; i < n; i += nwarps) {
-    if (!heavy_group(noff, n, i & ~(int64_t)31)) continue;
-    const int32_t v = perm[i];
-    const int64_t b = off[v], L = off[v + 1] - b, o = noff[i];
-    for (int64_t j = lane; j < L; j += 32) {
-      nadj[o + j] = inv[adj[b + j]];
-      if (w) nw[o + j] = w[b + j];
+    int64_t r = lo, re = noff[r + 1], rs = noff[r];
+    int64_t src = off[perm[r]];
+    for (int64_t p = p0 + lane; p < p0 + kPermChunk && p < m; p += 32) {
+      if (p >= re) {
+        // a few steps forward, then a binary search past runs of empty rows
+        int steps = 0;
+        do {
+          ++r;
+          re = noff[r + 1];
+        } while (p >= re && ++steps < 8);
+        if (p >= re) {
+          int64_t a = r, z = n;  // the last row with noff[row] <= p
+          while (z - a > 1) {
+            const int64_t mid = (a + z) >> 1;
+            if (noff[mid] <= p) a = mid; else z = mid;
+          }
+          r = a;
+          re = noff[r + 1];
+        }
+        rs = noff[r];
+        src = off[perm[r]];
+      }
+      nadj[p] = inv[adj[src + (p - rs)]];
+      if (w) nw[p] = w[src + (p - rs)];
     }
   }
 }
@@ -164,10 +150,9 @@ int permute_csr(const Csr& src, const int32_t* perm, const int32_t* inv, int32_t
   PRDF_TRY(dst.adj.alloc(src.m > 0 ? (size_t)src.m : 1, s));
   if (src.w.p) PRDF_TRY(dst.w.alloc(src.m > 0 ? (size_t)src.m : 1, s));
   else dst.w.release();
-  k_perm_rows<<<grid_for((int64_t)n, kThreads), kThreads, 0, s>>>(src.off.p, src.adj.p, src.w.p, perm, inv, n,
-                                                                   dst.off.p, dst.adj.p, dst.w.p);
-  k_perm_rows_heavy<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(src.off.p, src.adj.p, src.w.p, perm,
-                                                                               inv, n, dst.off.p, dst.adj.p, dst.w.p);
+  if (src.m > 0)
+    k_perm_rows<<<grid_for((src.m + kPermChunk - 1) / kPermChunk * 32, kThreads), kThreads, 0, s>>>(
+        src.off.p, src.adj.p, src.w.p, perm, inv, n, src.m, dst.off.p, dst.adj.p, dst.w.p);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }
