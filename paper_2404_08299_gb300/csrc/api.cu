@@ -334,6 +334,19 @@ int nonempty_classes(const int64_t* cb, int nclass) {
 // change of a sweep is <= tol or max_iter sweeps ran. The host reads the
 // residual every check_every sweeps; sweeps launched past convergence exit at
 // once on the device.
+int ensure_hub(prdf_graph* g, const Csr& c, PprHubTable& t, cudaStream_t s);
+
+// Static sweeps cut the highest in-degree class's rows into the hub chunks
+// of G' (exact partial sums per chunk); the table and the partial buffer are
+// made here, outside any stream capture.
+int prepare_hub_split(prdf_graph* g, SweepArgs& a, cudaStream_t s) {
+  PRDF_TRY(ensure_hub(g, g->rl.in, g->hub_in, s));
+  PRDF_TRY(g->sweep_hub_part.reserve((size_t)(g->hub_in.nchunk > 0 ? g->hub_in.nchunk : 1), s));
+  a.hub = g->hub_in.view();
+  a.hub_part = g->sweep_hub_part.p;
+  return PRDF_OK;
+}
+
 int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, cudaStream_t s, bool expand = true) {
   const int n = g->n;
   const int max_iter = p->max_iter;
@@ -345,7 +358,7 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
   begins_from_counts(rl.count, nci, cb);
   if (dynamic) begins_from_counts(rl.pout_count, nco, cbo);
   const bool expanding = dynamic && expand;
-  const int kps = nonempty_classes(cb, nci) + (expanding ? nonempty_classes(cbo, nco) : 0);
+  int kps = nonempty_classes(cb, nci) + (expanding ? nonempty_classes(cbo, nco) : 0);
   SweepArgs a;
   memset(&a, 0, sizeof(a));
   a.off = rl.in.off.p;
@@ -363,6 +376,10 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
   a.tau_f = p->tau_f;
   a.tau_p = p->tau_p;
   a.prune = p->prune;
+  if (!dynamic) {
+    PRDF_TRY(prepare_hub_split(g, a, s));
+    if (a.hub.nchunk > 0) kps += 1;  // the highest class takes two kernels
+  }
   const int check = p->check_every > 0 ? p->check_every : 8;
   const bool exact = p->accumulate == PRDF_ACC_EXACT;
   const bool timed = p->time_sweeps != 0;
@@ -706,7 +723,12 @@ int iterate_graph(prdf_graph* g, const prdf_params* p, IterResult* res, cudaStre
   int64_t cb[kMaxThr + 2];
   const int nci = rl.thr.n + 1;
   begins_from_counts(rl.count, nci, cb);
-  uint64_t key[8];
+  SweepArgs hub_args;
+  memset(&hub_args, 0, sizeof(hub_args));
+  PRDF_TRY(prepare_hub_split(g, hub_args, s));
+  uint64_t key[10];
+  key[8] = (uint64_t)(uintptr_t)hub_args.hub_part;
+  key[9] = (uint64_t)(uintptr_t)hub_args.hub.chunk_hub;
   key[0] = (uint64_t)(uintptr_t)g->xa.p ^ ((uint64_t)(uintptr_t)g->xb.p << 1);
   key[1] = (uint64_t)(uintptr_t)g->resid.p ^ ((uint64_t)(uintptr_t)g->ctl.p << 1);
   key[2] = rl.version;
@@ -735,6 +757,8 @@ int iterate_graph(prdf_graph* g, const prdf_params* p, IterResult* res, cudaStre
     a.xa = g->xa.p;
     a.xb = g->xb.p;
     a.resid_base = g->resid.p;
+    a.hub = hub_args.hub;
+    a.hub_part = hub_args.hub_part;
     cudaGraph_t graph = nullptr;
     PRDF_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle h;
@@ -786,7 +810,7 @@ int iterate_graph(prdf_graph* g, const prdf_params* p, IterResult* res, cudaStre
   const int k = hit - 1;
   res->final_buf = (k & 1) ? 0 : 1;
   res->launched = hit;
-  res->kernels = (long long)hit * (nonempty_classes(cb, nci) + 1);
+  res->kernels = (long long)hit * (nonempty_classes(cb, nci) + 1 + (hub_args.hub.nchunk > 0 ? 1 : 0));
   res->ms_sweep = 0;
   return PRDF_OK;
 }

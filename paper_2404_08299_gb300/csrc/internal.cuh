@@ -78,6 +78,17 @@ struct Relabel {
   uint64_t version = 0;              // bumped on every rebuild
 };
 
+// Rows of the highest in-degree class are cut into chunks of kHubChunk edges
+// (used by the K-column calls and by the Static sweep): chunk c covers edges
+// [chunk_j0[c], +kHubChunk) of vertex begin + chunk_hub[c]; the chunks of
+// hub i are [hub_first[i], hub_first[i + 1]) in row order.
+constexpr int64_t kHubChunk = 1024;
+struct PprHub {
+  int64_t begin, nhub, nchunk;
+  const int32_t* chunk_hub;
+  const int64_t* chunk_j0;
+  const int64_t* hub_first;
+};
 // Per-sweep arguments of the pull rank kernels (Alg. update).
 struct SweepArgs {
   const int64_t* off;      // in-CSR offsets of G'
@@ -104,6 +115,10 @@ struct SweepArgs {
   uint8_t* wrote;          // 1 where this vertex's slot in xn was written by the previous sweep
   double tau_f, tau_p;
   int prune;               // DF-P (Eq. 2, prune) or DF (Eq. 1)
+  // Static: chunks of the highest in-degree class's rows (nchunk = 0: none)
+  // and one partial sum per chunk (4 words)
+  PprHub hub;
+  uint4* hub_part;
 };
 
 // FP32 stage of the mixed-precision Static sweep (sweep32.cu).
@@ -148,17 +163,8 @@ struct Ppr64Args {
   double alpha, beta, inv_beta;
   uint64_t* dmax;          // max |T(R) - R| (FP64 bits, atomic max)
 };
-// Rows of the highest in-degree class of the K-column calls are cut into
-// chunks of kHubChunk edges: chunk c covers edges [chunk_j0[c], +kHubChunk)
-// of vertex begin + chunk_hub[c]; the chunks of hub i are
-// [hub_first[i], hub_first[i + 1]) in row order.
-constexpr int64_t kHubChunk = 1024;
-struct PprHub {
-  int64_t begin, nhub, nchunk;
-  const int32_t* chunk_hub;
-  const int64_t* chunk_j0;
-  const int64_t* hub_first;
-};
+
+// Owner of a chunk table (PprHub above) of one CSR of the sweep numbering.
 struct PprHubTable {
   int64_t begin = 0, nhub = 0, nchunk = 0;
   DBuf<int32_t> chunk_hub;
@@ -220,7 +226,8 @@ struct prdf_graph {
   prdf::Workspace ws;
   // solver scratch
   prdf::DBuf<double> xa, xb;
-  prdf::PprHubTable hub_in, hub_out;  // chunk tables of the K-column calls (G' and G)
+  prdf::PprHubTable hub_in, hub_out;  // chunk tables of G' (Static sweep, K-column forward) and G (adjoint)
+  prdf::DBuf<uint4> sweep_hub_part;   // Static sweep: one exact partial sum per chunk of G's hub rows
   prdf::DBuf<float2> ppr_part;        // chunk partial sums of one column tile
   prdf::DBuf<float> ya, yb, degf, invf;  // FP32 stage state and degrees (class-contiguous numbering)
   prdf::DBuf<uint32_t> resid32;
@@ -231,7 +238,7 @@ struct prdf_graph {
   prdf::DBuf<int> ctl;               // device iteration counter of the graph-driven loop
   cudaStream_t cap_stream = nullptr; // private stream used to capture graph bodies
   cudaGraphExec_t static_exec = nullptr;
-  uint64_t static_key[8] = {};       // what static_exec was built for
+  uint64_t static_key[10] = {};       // what static_exec was built for
   prdf::Relabel rl;                  // class-contiguous copy used by the sweeps
   // weighted graphs: transition probabilities P_uv = w_uv / sum_k w_uk
   bool ppr_valid = false;

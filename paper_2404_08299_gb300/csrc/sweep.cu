@@ -453,6 +453,56 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a_in, 
   block_max_to(dmax, a.resid);
 }
 
+// Static: rows of the highest in-degree class in 1024-edge chunks (the hub
+// chunk table). A warp per chunk sums the chunk's terms and stores the partial
+// sum; a thread per hub vertex adds its chunks' partials and finishes the
+// vertex. With exact accumulation the partials are integers, so the result is
+// the same bits as any other split; long rows no longer serialise on one block.
+template <bool EXACT>
+__global__ void __launch_bounds__(kThreads) k_sweep_hub_part(const SweepArgs a_in) {
+  const SweepArgs a = resolve(a_in);
+  if (a.prev && bitsd(*a.prev) <= a.tol) return;
+  const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  for (int64_t c = warp; c < a.hub.nchunk; c += nwarps) {
+    const int32_t v = (int32_t)(a.hub.begin + a.hub.chunk_hub[c]);
+    const int64_t jb = a.hub.chunk_j0[c];
+    const int64_t re = a.off[v + 1];
+    const int64_t je = jb + kHubChunk < re ? jb + kHubChunk : re;
+    Acc<EXACT> acc;
+    uint64_t unused = 0;
+    gather_row_vec<32, 2, EXACT, false>(a, jb, je, lane, v, acc, unused, pf, pl);
+    acc.template group_reduce<32>();
+    if (lane == 0) acc.to_shared(reinterpret_cast<uint32_t*>(a.hub_part + c));
+  }
+}
+
+template <bool EXACT>
+__global__ void __launch_bounds__(kThreads) k_sweep_hub_finish(const SweepArgs a_in) {
+  const SweepArgs a = resolve(a_in);
+  if (a.prev && bitsd(*a.prev) <= a.tol) return;
+  const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  uint64_t dmax = 0;
+  // a warp per hub vertex: lanes add strided chunk partials, then the warp reduces
+  for (int64_t h = warp; h < a.hub.nhub; h += nwarps) {
+    const int32_t v = (int32_t)(a.hub.begin + h);
+    Acc<EXACT> tot;
+    for (int64_t c = a.hub.hub_first[h] + lane; c < a.hub.hub_first[h + 1]; c += 32)
+      tot.from_shared(reinterpret_cast<const uint32_t*>(a.hub_part + c));
+    tot.template group_reduce<32>();
+    if (lane == 0) {
+      const uint64_t db = finish_vertex<false>(a, v, tot.value(), ld_gather_b64(a.x + v, pl), pf);
+      dmax = db > dmax ? db : dmax;
+    }
+  }
+  block_max_to(dmax, a.resid);
+}
+
 // Kernel shape of class c: the last class is block-per-vertex, the one before
 // it warp-per-vertex; lower classes by their upper degree bound.
 enum Kind { kT1 = 0, kT4, kG4, kG8, kG16, kG16U8, kWarp, kBlock };
@@ -490,6 +540,7 @@ bool prefer_l1_all() {
   prefer_l1(k_sweep_group<16, 8, EXACT, DYN, false>);
   prefer_l1(k_sweep_warp<2, EXACT, DYN>);
   prefer_l1(k_sweep_block<4, EXACT, DYN>);
+  prefer_l1(k_sweep_hub_part<EXACT>);
   return true;
 }
 
@@ -517,7 +568,14 @@ int launch_all(const SweepArgs& a, const PartThr& t, const int64_t* cb, cudaStre
       case kG16: k_sweep_group<16, 4, EXACT, DYN, false><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kG16U8: k_sweep_group<16, 8, EXACT, DYN, false><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kWarp: k_sweep_warp<2, EXACT, DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      default: k_sweep_block<4, EXACT, DYN><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e); break;
+      default:
+        if (!DYN && a.hub.nchunk > 0 && a.hub.begin == b && a.hub.nhub == cnt && a.hub_part) {
+          k_sweep_hub_part<EXACT><<<grid_for(a.hub.nchunk * 32, kThreads, maxg), kThreads, 0, s>>>(a);
+          k_sweep_hub_finish<EXACT><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a);
+        } else {
+          k_sweep_block<4, EXACT, DYN><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e);
+        }
+        break;
     }
   }
   PRDF_LAUNCH_CHECK();
