@@ -422,6 +422,8 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="build the graph and run one solve capped at --max-iter sweeps (for ncu captures)")
     ap.add_argument("--max-iter", type=int, default=500)
+    ap.add_argument("--profile-precision", type=int, default=0,
+                    help="with --profile-run: 0 = FP64 sweeps, 1 = FP32 stage then FP64 (mixed precision)")
     ap.add_argument("--tile", type=int, default=0, help="column tile of the K-column calls (0: default)")
     ap.add_argument("--profile-ppr", action="store_true",
                     help="build the 2^22 weighted graph and run a few K=64 PPR sweeps (for ncu captures)")
@@ -479,7 +481,8 @@ def main():
     torch.cuda.synchronize()
 
     if args.profile_run:
-        R, st = g.pagerank_static(accumulate=acc, max_iter=args.max_iter, check_every=args.max_iter, time_sweeps=1)
+        R, st = g.pagerank_static(accumulate=acc, max_iter=args.max_iter, check_every=args.max_iter, time_sweeps=1,
+                                  precision=args.profile_precision)
         torch.cuda.synchronize()
         print(json.dumps({"profile_run": args.workload, "n": n, "m": m, "sweeps": st.iterations,
                           "ms_total": st.ms_total}), flush=True)
