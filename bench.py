@@ -199,6 +199,7 @@ def measure_dfp(g, n, m, args):
         t_dt, errs_dt, aff_dt = [], [], []
         t_nd, t_df, errs_nd, errs_df = [], [], [], []
         t_apply = []
+        errs_inf = []
         for b in range(args.dfp_batches):
             off, adj, _ = g.export_csr(prdf.PRDF_OUT)
             size = max(1, int(round(f * m)))
@@ -228,6 +229,7 @@ def measure_dfp(g, n, m, args):
             t_dfp.append(st.ms_total)
             t_static.append(sts.ms_total)
             errs.append(float((R - Rt).abs().sum()))
+            errs_inf.append(float((R - Rt).abs().max() / Rt.abs().max()))
             iters.append(st.iterations)
             aff.append(st.affected_initial)
             R_prev = R
@@ -235,7 +237,7 @@ def measure_dfp(g, n, m, args):
                     "dfp_ms": statistics.median(t_dfp), "static_ms": statistics.median(t_static),
                     "speedup_vs_static": statistics.median(t_static) / statistics.median(t_dfp),
                     "dfp_sweeps": statistics.median(iters), "affected_initial": int(statistics.median(aff)),
-                    "l1_err_max": max(errs),
+                    "l1_err_max": max(errs), "linf_err_rel_max": max(errs_inf),
                     "dt_ms": statistics.median(t_dt), "dt_affected": int(statistics.median(aff_dt)),
                     "dt_l1_err_max": max(errs_dt),
                     "dfp_speedup_vs_dt": statistics.median(t_dt) / statistics.median(t_dfp),

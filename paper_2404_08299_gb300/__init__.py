@@ -357,3 +357,25 @@ class PageRankFn(torch.autograd.Function):
                                                 want_grad_w=need_w, **ctx.kw)
         return (None, gS.to(ctx.S_dtype) if gS is not None else None, gw.to(ctx.w_dtype) if gw is not None else None,
                 None)
+
+
+# Module-level entry points, one per method of the paper (each is the Graph method of the same job).
+
+def static(graph: Graph, R0=None, **kw):
+    """Alg. static (R0 None) or Naive-dynamic (Alg. naive, R0 = previous ranks): (ranks, Stats)."""
+    return graph.pagerank_static(R0, **kw)
+
+
+def dfp(graph: Graph, del_src, del_dst, ins_src, prev_ranks, **kw):
+    """Alg. frontier, DF-P (prune=0 gives DF), on a graph already holding G^t: (ranks, Stats, deltaV or None)."""
+    return graph.pagerank_dfp(del_src, del_dst, ins_src, prev_ranks, **kw)
+
+
+def dt(graph: Graph, del_src, del_dst, ins_src, prev_ranks, **kw):
+    """Alg. traversal (Dynamic Traversal) on a graph already holding G^t: (ranks, Stats, deltaV or None)."""
+    return graph.pagerank_dt(del_src, del_dst, ins_src, prev_ranks, **kw)
+
+
+def ppr(graph: Graph, S, **kw):
+    """K-column weighted personalised PageRank: (R [n, K], Stats)."""
+    return graph.pagerank_ppr(S, **kw)

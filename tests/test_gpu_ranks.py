@@ -216,6 +216,20 @@ def test_dt_empty_batch_is_identity():
     assert float(((R - R0).abs() / R0).max()) <= 4.5e-16
 
 
+def test_module_level_entry_points():
+    """prdf.static / prdf.dfp / prdf.dt are the Graph methods of the same job."""
+    P = prdf()
+    n, s, d = synth.rmat(9, 4000, seed=3)
+    g = gpu_graph(n, s, d)
+    R1, st1 = P.static(g)
+    R2, st2 = g.pagerank_static()
+    assert torch.equal(R1, R2) and st1.iterations == st2.iterations
+    e = torch.zeros(0, dtype=torch.int32, device="cuda")
+    for call in (P.dfp, P.dt):
+        R, st, _ = call(g, e, e, e, R1)
+        assert st.iterations == 1 and float(((R - R1).abs() / R1).max()) <= 4.5e-16
+
+
 def test_autotune_keeps_ranks_bit_identical():
     """The tuner only changes kernel shapes and the vertex numbering; exact accumulation keeps every bit."""
     n, s, d = synth.rmat(13, 150000, seed=12)
