@@ -11,6 +11,8 @@
  *     (Section 4.3, 4.5);
  *   - degree partitioning, Alg. partition (Appendix A.2);
  *   - affected-vertex marking, Alg. affected (Appendix A.3);
+ *   - Dynamic Traversal, Alg. traversal (Section 3.3);
+ *   - Naive-dynamic, Alg. naive (Static from the previous ranks);
  *   - batch updates Delta^{t-} = E^{t-1} \ E^t, Delta^{t+} = E^t \ E^{t-1}
  *     (Section 3.3).
  * Extensions beyond the paper: FP32 sweeps refined in FP64, K-column
@@ -138,11 +140,17 @@ int prdf_graph_export_csr(const prdf_graph* g, int which, int64_t* off, int32_t*
  * Apply a batch update with set semantics (Section 3.3):
  * E^t = (E^{t-1} \ D) u I, self-loops never deleted (Section 5.1.3).
  * del_src/del_dst: int32[n_del], ins_src/ins_dst: int32[n_ins] (device).
- * Rebuilds G and G' in place. del_eff (uint8[n_del], nullable) gets 1 where
+ * Updates G and G' in place: when every vertex already has its self-loop,
+ * each row becomes (old \ D) u I by an order-preserving merge (no re-sort of
+ * the graph); otherwise the graph is rebuilt from its edge list, which gives
+ * every vertex its self-loop. del_eff (uint8[n_del], nullable) gets 1 where
  * the deletion is in Delta^{t-} = E^{t-1} \ E^t; ins_eff (uint8[n_ins],
  * nullable) gets 1 where the insertion is in Delta^{t+} = E^t \ E^{t-1}.
  * Weighted graphs take new edges' weights from ins_w (float32[n_ins]), which
- * is then required.
+ * is then required; an edge inserted again keeps the larger of its weights,
+ * duplicates in the batch take their maximum. Self-loop deletions and
+ * deletions of missing edges are ignored. The sweep numbering and the
+ * partitions are rebuilt for the new graph.
  */
 int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, int64_t n_del,
                            const int32_t* ins_src, const int32_t* ins_dst, const float* ins_w, int64_t n_ins,
