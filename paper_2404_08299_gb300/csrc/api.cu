@@ -636,11 +636,12 @@ int ppr64_step(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int ti
   a.beta = 1.0 - p->alpha;
   a.inv_beta = 1.0 / (1.0 - p->alpha);
   a.dmax = g->resid.p;
-  PRDF_TRY(launch_ppr64_step(a, tile, g->n, op.hub_begin, s));
+  PRDF_TRY(g->ppr_part64.reserve((size_t)(op.hub->nchunk > 0 ? op.hub->nchunk : 1) * (size_t)tile, s));
+  PRDF_TRY(launch_ppr64_step(a, tile, g->n, op.hub_begin, op.hub->view(), g->ppr_part64.p, s));
   PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
   memcpy(dmax, g->ws.host_i64, sizeof(double));
-  *kernels += (long long)((K + tile - 1) / tile) * 2;
+  *kernels += (long long)((K + tile - 1) / tile) * ppr32_kernels(op.hub_begin, op.hub->begin, g->n);
   return PRDF_OK;
 }
 

@@ -180,7 +180,10 @@ int build_ppr_hub(const int64_t* off, int64_t begin, int64_t n, PprHubTable& t, 
 // h.nchunk * tile float2 scratch).
 int launch_ppr32_sweep(const Ppr32Args& a, int tile, int64_t n, int64_t hub_begin, const PprHub& h, float2* part,
                        cudaStream_t s);
-int launch_ppr64_step(const Ppr64Args& a, int tile, int64_t n, int64_t hub_begin, cudaStream_t s);
+// FP64 Jacobi step over tiles of `tile` columns, same ranges as the FP32
+// sweep (part: h.nchunk * tile doubles of scratch).
+int launch_ppr64_step(const Ppr64Args& a, int tile, int64_t n, int64_t hub_begin, const PprHub& h, double* part,
+                      cudaStream_t s);
 int ppr_add_correction(double* R, const float* E, int64_t cnt, cudaStream_t s);
 int launch_grad_w(const int64_t* off, const int32_t* adj, const int32_t* perm, const int64_t* orig_off,
                   const double* lam, const double* Gs, double g_scale, const double* Rr, const double* W, int32_t n,
@@ -228,7 +231,8 @@ struct prdf_graph {
   prdf::DBuf<double> xa, xb;
   prdf::PprHubTable hub_in, hub_out;  // chunk tables of G' (Static sweep, K-column forward) and G (adjoint)
   prdf::DBuf<uint4> sweep_hub_part;   // Static sweep: one exact partial sum per chunk of G's hub rows
-  prdf::DBuf<float2> ppr_part;        // chunk partial sums of one column tile
+  prdf::DBuf<float2> ppr_part;        // chunk partial sums of one column tile (FP32 sweeps)
+  prdf::DBuf<double> ppr_part64;      // chunk partial sums of one column tile (FP64 steps)
   prdf::DBuf<float> ya, yb, degf, invf;  // FP32 stage state and degrees (class-contiguous numbering)
   prdf::DBuf<uint32_t> resid32;
   prdf::DBuf<uint64_t> resid;

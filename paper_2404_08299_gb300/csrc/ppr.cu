@@ -358,85 +358,79 @@ __global__ void k_hub_fill(const int64_t* __restrict__ off, int64_t begin, int64
   }
 }
 
-// FP64 Jacobi step T(R) = alpha P^T R + (1 - alpha) S for a tile of 2G columns:
-// writes T(R) to Rn, the residual (T(R) - R) / (1 - alpha) as FP32 to res32 (if
-// not null) and max |T(R) - R| to *dmax (FP64 bits, atomic max).
-template <int G, bool HUB>
-__global__ void __launch_bounds__(kThreads) k_ppr64_step(const Ppr64Args a, int64_t begin, int64_t end, int c0) {
-  constexpr int kSlots = kThreads / G;
-  __shared__ double ss[HUB ? kSlots : 1][HUB ? 2 * G : 1];
-  const int lane = threadIdx.x % G;
-  const int col = c0 + 2 * lane;
-  const bool colok = col < a.K, two = col + 1 < a.K;
-  uint64_t dmax = 0;
-  const int64_t gstride = HUB ? gridDim.x : ((int64_t)gridDim.x * kThreads) / G;
-  const int64_t g0 = HUB ? blockIdx.x : (blockIdx.x * (int64_t)kThreads + threadIdx.x) / G;
-  const int slot = HUB ? (int)(threadIdx.x / G) : 0;
-  for (int64_t i = begin + g0; HUB ? (i < end) : true; i += gstride) {
-    bool active = i < end;
-    if (!HUB && !active) break;
-    const int32_t v = (int32_t)i;
-    const int64_t b = a.off[v], e = a.off[v + 1];
-    double s0 = 0, s1 = 0;
-    constexpr int U = 4;  // edges in flight per slot
-    const int64_t stride = HUB ? kSlots : 1;
-    for (int64_t j0 = b + slot; j0 < e; j0 += stride * U) {
-      int32_t u[U];
-      double p[U], r0[U], r1[U];
+// ---------------------------------------------------- FP64 Jacobi step ----
+// T(R) = alpha P^T R + (1 - alpha) S for a tile of columns, with the layout of
+// the FP32 sweep (4 columns per lane, LPE = tile / 4 lanes per edge): writes
+// T(R) to Rn, the residual (T(R) - R) / (1 - alpha) as FP32 to res32 (if not
+// null) and max |T(R) - R| to *dmax (FP64 bits, atomic max). Sums are plain
+// FP64 FMAs in a fixed order (edge order within a slot, then slots, then
+// chunks), so every run gives the same bits.
+
+struct Col4d {
+  double v[4];
+};
+
+__device__ __forceinline__ Col4d zero4d() {
+  Col4d c;
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const int64_t j = j0 + (int64_t)k * stride;
-        u[k] = j < e ? __ldg(a.adj + j) : -1;
-        p[k] = j < e ? __ldg(a.P + j) : 0.0;
-      }
+  for (int q = 0; q < 4; ++q) c.v[q] = 0.0;
+  return c;
+}
+
+// columns col .. col + 3 of row u (zero past K); K even: two 16-byte loads
+__device__ __forceinline__ Col4d ld_cols64(const double* R, int64_t u, int K, int col) {
+  Col4d c;
+  const double* src = R + u * K + col;
+  if ((K & 1) == 0 && col + 4 <= K) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(src));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(src + 2));
+    c.v[0] = a.x;
+    c.v[1] = a.y;
+    c.v[2] = b.x;
+    c.v[3] = b.y;
+  } else {
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        r0[k] = 0.0;
-        r1[k] = 0.0;
-        if (u[k] >= 0 && colok) {
-          const double* src = a.R + (int64_t)u[k] * a.K + col;
-          r0[k] = __ldg(src);
-          if (two) r1[k] = __ldg(src + 1);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        if (u[k] < 0) continue;
-        s0 = fma(p[k], r0[k], s0);
-        s1 = fma(p[k], r1[k], s1);
-      }
-    }
-    if (HUB) {
-      ss[slot][2 * lane] = s0;
-      ss[slot][2 * lane + 1] = s1;
-      __syncthreads();
-      if (slot == 0) {
-        s0 = 0;
-        s1 = 0;
-        for (int k = 0; k < kSlots; ++k) {
-          s0 += ss[k][2 * lane];
-          s1 += ss[k][2 * lane + 1];
-        }
-      }
-    }
-    if ((!HUB || slot == 0) && colok) {
-      const int64_t o = (int64_t)v * a.K + col;
-      const double t0 = fma(a.alpha, s0, a.beta * a.S[o]);
-      const double d0 = t0 - a.R[o];
-      a.Rn[o] = t0;
-      if (a.res32) a.res32[o] = (float)(d0 * a.inv_beta);
-      dmax = max(dmax, dbits(fabs(d0)));
-      if (two) {
-        const double t1 = fma(a.alpha, s1, a.beta * a.S[o + 1]);
-        const double d1 = t1 - a.R[o + 1];
-        a.Rn[o + 1] = t1;
-        if (a.res32) a.res32[o + 1] = (float)(d1 * a.inv_beta);
-        dmax = max(dmax, dbits(fabs(d1)));
-      }
-    }
-    if (HUB) __syncthreads();
+    for (int q = 0; q < 4; ++q) c.v[q] = col + q < K ? __ldg(src + q) : 0.0;
   }
-  // block max
+  return c;
+}
+
+template <int U>
+__device__ __forceinline__ void ppr64_edges(const Ppr64Args& a, int64_t j0, int64_t stride, int64_t e, int col,
+                                            bool colok, double* acc) {
+  int32_t u[U];
+  double p[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    const int64_t j = j0 + (int64_t)k * stride;
+    u[k] = j < e ? __ldg(a.adj + j) : -1;
+    p[k] = j < e ? __ldg(a.P + j) : 0.0;
+  }
+  Col4d r[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) r[k] = (u[k] >= 0 && colok) ? ld_cols64(a.R, u[k], a.K, col) : zero4d();
+#pragma unroll
+  for (int k = 0; k < U; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fma(p[k], r[k].v[q], acc[q]);
+}
+
+// T(R), residual and |T(R) - R| for the 4 columns of vertex v
+__device__ __forceinline__ void ppr64_finish4(const Ppr64Args& a, int32_t v, int col, const double* acc,
+                                              uint64_t& dmax) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (col + q >= a.K) break;
+    const int64_t o = (int64_t)v * a.K + col + q;
+    const double t = fma(a.alpha, acc[q], a.beta * a.S[o]);
+    const double d = t - a.R[o];
+    a.Rn[o] = t;
+    if (a.res32) a.res32[o] = (float)(d * a.inv_beta);
+    dmax = max(dmax, dbits(fabs(d)));
+  }
+}
+
+__device__ __forceinline__ void block_max_u64(uint64_t dmax, uint64_t* out) {
   __shared__ uint64_t sm[32];
   dmax = warp_max_u64(dmax);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = dmax;
@@ -444,8 +438,109 @@ __global__ void __launch_bounds__(kThreads) k_ppr64_step(const Ppr64Args a, int6
   if (threadIdx.x < 32) {
     uint64_t x = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0;
     x = warp_max_u64(x);
-    if (threadIdx.x == 0 && x) atomicMax((unsigned long long*)a.dmax, (unsigned long long)x);
+    if (threadIdx.x == 0 && x) atomicMax((unsigned long long*)out, (unsigned long long)x);
   }
+}
+
+template <int LPE>
+__device__ __forceinline__ void merge_slots64(double* t) {
+#pragma unroll
+  for (int o = LPE; o < 32; o <<= 1)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
+}
+
+// one vertex per slot (in-degree up to the two highest classes)
+template <int LPE, int U>
+__global__ void __launch_bounds__(kThreads) k_ppr64_group(const Ppr64Args a, int64_t begin, int64_t end, int c0) {
+  constexpr int kSlots = 32 / LPE;
+  const int sub = threadIdx.x & (LPE - 1);
+  const int slot = (threadIdx.x & 31) / LPE;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const int col = c0 + 4 * sub;
+  const bool colok = col < a.K;
+  uint64_t dmax = 0;
+  for (int64_t base = begin + warp * kSlots; base < end; base += nwarps * kSlots) {
+    const int64_t i = base + slot;
+    if (i >= end) continue;
+    const int32_t v = (int32_t)i;
+    const int64_t b = a.off[v], e = a.off[v + 1];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t j0 = b; j0 < e; j0 += U) ppr64_edges<U>(a, j0, 1, e, col, colok, acc);
+    if (colok) ppr64_finish4(a, v, col, acc, dmax);
+  }
+  block_max_u64(dmax, a.dmax);
+}
+
+// a warp per vertex (mid-degree rows), slots meet by shuffles
+template <int LPE, int U>
+__global__ void __launch_bounds__(kThreads) k_ppr64_warp(const Ppr64Args a, int64_t begin, int64_t end, int c0) {
+  constexpr int kSlots = 32 / LPE;
+  const int sub = threadIdx.x & (LPE - 1);
+  const int slot = (threadIdx.x & 31) / LPE;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const int col = c0 + 4 * sub;
+  const bool colok = col < a.K;
+  uint64_t dmax = 0;
+  for (int64_t i = begin + warp; i < end; i += nwarps) {
+    const int32_t v = (int32_t)i;
+    const int64_t b = a.off[v], e = a.off[v + 1];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t j0 = b + slot; j0 < e; j0 += (int64_t)kSlots * U) ppr64_edges<U>(a, j0, kSlots, e, col, colok, acc);
+    merge_slots64<LPE>(acc);
+    if (slot == 0 && colok) ppr64_finish4(a, v, col, acc, dmax);
+  }
+  block_max_u64(dmax, a.dmax);
+}
+
+// hub rows in 1024-edge chunks: partial sums per chunk, then merged in chunk order
+template <int LPE, int U>
+__global__ void __launch_bounds__(kThreads) k_ppr64_hub_part(const Ppr64Args a, PprHub h, int c0, int tile,
+                                                             double* __restrict__ part) {
+  constexpr int kSlots = 32 / LPE;
+  const int sub = threadIdx.x & (LPE - 1);
+  const int slot = (threadIdx.x & 31) / LPE;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const int col = c0 + 4 * sub;
+  const bool colok = col < a.K;
+  for (int64_t c = warp; c < h.nchunk; c += nwarps) {
+    const int32_t v = (int32_t)(h.begin + h.chunk_hub[c]);
+    const int64_t jb = h.chunk_j0[c];
+    const int64_t re = a.off[v + 1];
+    const int64_t e = jb + kHubChunk < re ? jb + kHubChunk : re;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t j0 = jb + slot; j0 < e; j0 += (int64_t)kSlots * U) ppr64_edges<U>(a, j0, kSlots, e, col, colok, acc);
+    merge_slots64<LPE>(acc);
+    if (slot == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) part[c * tile + 4 * sub + q] = acc[q];
+    }
+  }
+}
+
+template <int LPE>
+__global__ void __launch_bounds__(kThreads) k_ppr64_hub_finish(const Ppr64Args a, PprHub h, int c0, int tile,
+                                                               const double* __restrict__ part) {
+  constexpr int kSlots = 32 / LPE;
+  const int sub = threadIdx.x & (LPE - 1);
+  const int slot = (threadIdx.x & 31) / LPE;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const int col = c0 + 4 * sub;
+  uint64_t dmax = 0;
+  for (int64_t base = warp * kSlots; base < h.nhub; base += nwarps * kSlots) {
+    const int64_t hi = base + slot;
+    if (hi >= h.nhub) continue;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t c = h.hub_first[hi]; c < h.hub_first[hi + 1]; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += part[c * tile + 4 * sub + q];
+    if (col < a.K) ppr64_finish4(a, (int32_t)(h.begin + hi), col, acc, dmax);
+  }
+  block_max_u64(dmax, a.dmax);
 }
 
 // Edge gradient of L = sum_c G_c . R_c with respect to w_uv (out-slot j of
@@ -511,11 +606,17 @@ void launch32_tile(const Ppr32Args& a, const PprHub& h, float2* part, int64_t hu
   (void)kSlots;
 }
 
-template <int G>
-void launch64_tile(const Ppr64Args& a, int64_t lo_b, int64_t lo_e, int64_t hi_e, int c0, cudaStream_t s) {
+template <int LPE>
+void launch64_tile(const Ppr64Args& a, const PprHub& h, double* part, int64_t hub_b, int64_t n, int c0, int tile,
+                   cudaStream_t s) {
   const int maxg = kSMs * 8;
-  if (lo_e > lo_b) k_ppr64_step<G, false><<<grid_for((lo_e - lo_b) * G, kThreads, maxg), kThreads, 0, s>>>(a, lo_b, lo_e, c0);
-  if (hi_e > lo_e) k_ppr64_step<G, true><<<grid_for(hi_e - lo_e, 1, maxg), kThreads, 0, s>>>(a, lo_e, hi_e, c0);
+  if (hub_b > 0) k_ppr64_group<LPE, 4><<<grid_for(hub_b * LPE, kThreads, maxg), kThreads, 0, s>>>(a, 0, hub_b, c0);
+  if (h.begin > hub_b)
+    k_ppr64_warp<LPE, 4><<<grid_for((h.begin - hub_b) * 32, kThreads, maxg), kThreads, 0, s>>>(a, hub_b, h.begin, c0);
+  if (n > h.begin) {
+    k_ppr64_hub_part<LPE, 4><<<grid_for(h.nchunk * 32, kThreads, maxg), kThreads, 0, s>>>(a, h, c0, tile, part);
+    k_ppr64_hub_finish<LPE><<<grid_for(h.nhub * LPE, kThreads, maxg), kThreads, 0, s>>>(a, h, c0, tile, part);
+  }
 }
 
 }  // namespace
@@ -557,13 +658,14 @@ int build_ppr_hub(const int64_t* off, int64_t begin, int64_t n, PprHubTable& t, 
   return PRDF_OK;
 }
 
-int launch_ppr64_step(const Ppr64Args& a, int tile, int64_t n, int64_t hub_begin, cudaStream_t s) {
+int launch_ppr64_step(const Ppr64Args& a, int tile, int64_t n, int64_t hub_begin, const PprHub& h, double* part,
+                      cudaStream_t s) {
   for (int c0 = 0; c0 < a.K; c0 += tile) {
     switch (tile) {
-      case 8: launch64_tile<4>(a, 0, hub_begin, n, c0, s); break;
-      case 16: launch64_tile<8>(a, 0, hub_begin, n, c0, s); break;
-      case 32: launch64_tile<16>(a, 0, hub_begin, n, c0, s); break;
-      default: launch64_tile<32>(a, 0, hub_begin, n, c0, s); break;
+      case 8: launch64_tile<2>(a, h, part, hub_begin, n, c0, tile, s); break;
+      case 16: launch64_tile<4>(a, h, part, hub_begin, n, c0, tile, s); break;
+      case 32: launch64_tile<8>(a, h, part, hub_begin, n, c0, tile, s); break;
+      default: launch64_tile<16>(a, h, part, hub_begin, n, c0, tile, s); break;
     }
   }
   PRDF_LAUNCH_CHECK();
