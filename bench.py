@@ -200,6 +200,7 @@ def measure_dfp(g, n, m, args):
         t_nd, t_df, errs_nd, errs_df = [], [], [], []
         t_apply = []
         errs_inf = []
+        parts = {"partition": [], "mark": [], "iterate": []}
         for b in range(args.dfp_batches):
             off, adj, _ = g.export_csr(prdf.PRDF_OUT)
             size = max(1, int(round(f * m)))
@@ -227,6 +228,9 @@ def measure_dfp(g, n, m, args):
             errs_dt.append(float((Rd - Rt).abs().sum()))
             aff_dt.append(std.affected_initial)
             t_dfp.append(st.ms_total)
+            parts["partition"].append(st.ms_partition)
+            parts["mark"].append(st.ms_mark)
+            parts["iterate"].append(st.ms_iterate)
             t_static.append(sts.ms_total)
             errs.append(float((R - Rt).abs().sum()))
             errs_inf.append(float((R - Rt).abs().max() / Rt.abs().max()))
@@ -236,6 +240,7 @@ def measure_dfp(g, n, m, args):
         out.append({"batch_fraction": f, "batch_size": int(round(f * m)), "batches": args.dfp_batches,
                     "dfp_ms": statistics.median(t_dfp), "static_ms": statistics.median(t_static),
                     "speedup_vs_static": statistics.median(t_static) / statistics.median(t_dfp),
+                    "dfp_ms_parts": {k: statistics.median(v) for k, v in parts.items()},
                     "dfp_sweeps": statistics.median(iters), "affected_initial": int(statistics.median(aff)),
                     "l1_err_max": max(errs), "linf_err_rel_max": max(errs_inf),
                     "dt_ms": statistics.median(t_dt), "dt_affected": int(statistics.median(aff_dt)),

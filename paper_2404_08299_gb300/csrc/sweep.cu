@@ -301,11 +301,14 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, 
   uint64_t dmax = 0;
 
   auto load_v = [&](int64_t i) -> int32_t { return i < end ? (int32_t)i : -1; };
+  // DF / DF-P: the row of an unaffected vertex is not read (its flag can
+  // change in this sweep only when the vertex itself is finished)
   auto load_item = [&](int32_t v, Item<U>& it) {
     it.v = v;
     it.b = 0;
     it.e = 0;
-    if (v >= 0) {
+    const bool live = v >= 0 && (!DYN || a.dV[v]);
+    if (live) {
       if (SELF1) {
         it.b = 0;
         it.e = 1;
@@ -317,8 +320,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, 
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       const int64_t j = it.b + lane + (int64_t)k * G;
-      if (SELF1) it.u[k] = (v >= 0 && k == 0 && lane == 0) ? v : -1;
-      else it.u[k] = (v >= 0 && j < it.e) ? ld_stream_i32(a.adj + j, pf) : -1;
+      if (SELF1) it.u[k] = (live && k == 0 && lane == 0) ? v : -1;
+      else it.u[k] = (live && j < it.e) ? ld_stream_i32(a.adj + j, pf) : -1;
     }
   };
 
