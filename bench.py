@@ -434,6 +434,9 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="column tile of the K-column calls (0: default)")
     ap.add_argument("--profile-ppr", action="store_true",
                     help="build the 2^22 weighted graph and run a few K=64 PPR sweeps (for ncu captures)")
+    ap.add_argument("--profile-dfp", type=float, default=0.0,
+                    help="build the 2^22 R-MAT, solve Static, apply one random batch of this fraction of |E| and run "
+                         "DF-P once (for ncu captures of the build, batch-update, marking and DF-P sweep kernels)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -461,6 +464,24 @@ def main():
                                tile=args.tile)
         torch.cuda.synchronize()
         print(json.dumps({"profile_ppr": True, "n": n, "m": g.m, "sweeps": st.iterations}), flush=True)
+        return 0
+
+    if args.profile_dfp > 0:
+        pbuild.build()
+        synth.build()
+        n, s, d = synth.rmat(22, 1 << 26, seed=1)
+        g = prdf.Graph(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
+        n_, m = g.size()
+        R0, _ = g.pagerank_static()
+        off, adj, _ = g.export_csr(prdf.PRDF_OUT)
+        size = max(1, int(round(args.profile_dfp * m)))
+        ds, dd, is_, id_ = synth.batch(n, off.cpu().numpy(), adj.cpu().numpy(), size, seed=1, s1=0, s2=0)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        de, ie = g.apply_batch(t(ds), t(dd), t(is_), t(id_))
+        R, st, _ = g.pagerank_dfp(t(ds), t(dd), t(is_), R0, del_mask=de, ins_mask=ie)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_dfp": args.profile_dfp, "n": n, "m": m, "batch": size, "sweeps": st.iterations,
+                          "affected_initial": st.affected_initial, "ms_total": st.ms_total}), flush=True)
         return 0
 
     if rank == 0:

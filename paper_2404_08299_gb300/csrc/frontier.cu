@@ -1,7 +1,7 @@
 // Affected-vertex marking (Alg. affected, Appendix A.3 of arXiv 2404.08299):
 // initialAffected over the batch, expandAffected over the out-degree
-// partition of G with thread-, sub-warp-, warp- and block-per-vertex
-// kernels. Flags are uint8; every store writes 1, so concurrent marks of the
+// partition of G with thread-, sub-warp- and warp-per-vertex kernels, and
+// 16 blocks per row for the highest class. Flags are uint8; every store writes 1, so concurrent marks of the
 // same vertex need no atomics, and a flag already set is not stored again.
 // With a third flag array dF the same kernels are one round of the
 // reachability closure of Dynamic Traversal (Alg. traversal): a vertex that
@@ -13,6 +13,7 @@ namespace prdf {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kExpandSlices = 16;  // blocks sharing one row of the highest out-degree class
 
 __global__ void k_initial_affected(const int32_t* __restrict__ del_src, const int32_t* __restrict__ del_dst,
                                    const uint8_t* __restrict__ del_mask, int64_t n_del,
@@ -37,6 +38,32 @@ __global__ void k_initial_affected(const int32_t* __restrict__ del_src, const in
 
 __device__ __forceinline__ bool converged(const uint64_t* r, double tol) { return r && bitsd(*r) <= tol; }
 
+// Mark the targets of edges [j0, e) of one row, `step` apart, kU per lane in
+// flight: the index loads of a round issue together, then their flag loads.
+template <int kU>
+__device__ __forceinline__ void mark_targets(const int32_t* __restrict__ adj, int64_t j0, int64_t e, int step,
+                                             uint8_t* __restrict__ dV, uint8_t* __restrict__ dF) {
+  for (; j0 < e; j0 += (int64_t)step * kU) {
+    int32_t w[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      const int64_t j = j0 + (int64_t)k * step;
+      w[k] = j < e ? adj[j] : -1;
+    }
+    uint8_t f[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) f[k] = w[k] >= 0 ? dV[w[k]] : (uint8_t)1;
+#pragma unroll
+    for (int k = 0; k < kU; ++k)
+      if (!f[k]) {  // most targets are already marked when the frontier is large
+        dV[w[k]] = 1;
+        if (dF) dF[w[k]] = 1;
+      }
+  }
+}
+
+constexpr int kExpandU = 4;
+
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_expand_group(const int64_t* __restrict__ off,
                                                            const int32_t* __restrict__ adj,
@@ -50,34 +77,27 @@ __global__ void __launch_bounds__(kThreads) k_expand_group(const int64_t* __rest
   for (int64_t i = begin + gid; i < end; i += ng) {
     const int32_t u = P[i];
     if (!dN[u]) continue;
-    const int64_t b = off[u], e = off[u + 1];
-    for (int64_t j = b + lane; j < e; j += G) {
-      const int32_t w = adj[j];
-      if (!dV[w]) {  // most targets are already marked when the frontier is large
-        dV[w] = 1;
-        if (dF) dF[w] = 1;
-      }
-    }
+    mark_targets<kExpandU>(adj, off[u] + lane, off[u + 1], G, dV, dF);
   }
 }
 
+// highest out-degree class: blockIdx.y picks one of gridDim.y equal slices of
+// each row, so the longest rows are spread over that many blocks
 __global__ void __launch_bounds__(kThreads) k_expand_block(const int64_t* __restrict__ off,
                                                            const int32_t* __restrict__ adj,
                                                            const int32_t* __restrict__ P, int64_t begin, int64_t end,
                                                            const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
                                                            uint8_t* __restrict__ dF, const uint64_t* resid, double tol) {
   if (converged(resid, tol)) return;
+  const int64_t S = gridDim.y, y = blockIdx.y;
   for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
     const int32_t u = P[i];
     if (!dN[u]) continue;
-    const int64_t b = off[u], e = off[u + 1];
-    for (int64_t j = b + threadIdx.x; j < e; j += kThreads) {
-      const int32_t w = adj[j];
-      if (!dV[w]) {
-        dV[w] = 1;
-        if (dF) dF[w] = 1;
-      }
-    }
+    const int64_t b = off[u], len = off[u + 1] - b;
+    const int64_t span = (len + S - 1) / S;
+    const int64_t sb = b + y * span;
+    const int64_t se = sb + span < b + len ? sb + span : b + len;
+    mark_targets<kExpandU>(adj, sb + threadIdx.x, se, kThreads, dV, dF);
   }
 }
 
@@ -113,7 +133,11 @@ int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, cons
       case 0: k_expand_group<1><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
       case 1: k_expand_group<8><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
       case 2: k_expand_group<32><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
-      default: k_expand_block<<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
+      default: {
+        const dim3 grid(grid_for(cnt, 1, maxg / kExpandSlices), kExpandSlices);
+        k_expand_block<<<grid, kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol);
+        break;
+      }
     }
   }
   PRDF_LAUNCH_CHECK();
