@@ -110,6 +110,16 @@ void prdf_params_default(prdf_params* p);
 const char* prdf_last_error(void);
 const char* prdf_strerror(int code);
 
+/*
+ * Device memory: the library allocates stream-ordered from its own memory
+ * pool on the current device, and memory it frees stays reserved in that
+ * pool for its later calls (no re-mapping of large buffers per build or
+ * batch). This call gives every block of the reserve that no allocation or
+ * pending free still uses back to the driver; synchronise the streams the
+ * library used first. Returns PRDF_OK or PRDF_ECUDA.
+ */
+int prdf_release_cached_memory(void);
+
 /* ---------------------------------------------------------------- graph -- */
 
 /*

@@ -73,6 +73,7 @@ _SIGNATURES = {
     "prdf_params_default": (None, [_P]),
     "prdf_last_error": (ctypes.c_char_p, []),
     "prdf_strerror": (ctypes.c_char_p, [_INT]),
+    "prdf_release_cached_memory": (_INT, []),
     "prdf_graph_create": (_INT, [_I32, _P, _P, _P, _I64, _U, _P, _P]),
     "prdf_graph_destroy": (None, [_P]),
     "prdf_graph_size": (_INT, [_P, _P, _P]),
@@ -149,6 +150,13 @@ def params(**kw) -> _Params:
         setattr(p, k, v)
     p.stream = _stream()
     return p
+
+
+def release_cached_memory():
+    """Return the device memory the library keeps reserved in its pool for later calls
+    (prdf_release_cached_memory); synchronises the current device first."""
+    torch.cuda.synchronize()
+    _check(lib().prdf_release_cached_memory())
 
 
 def partition_noalloc(off: torch.Tensor, thresholds):

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -831,6 +832,36 @@ int alloc_solver(prdf_graph* g, bool dynamic, cudaStream_t s) {
 }  // namespace
 }  // namespace prdf
 
+namespace prdf {
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+}  // namespace
+
+cudaMemPool_t device_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+}  // namespace prdf
+
 using namespace prdf;
 
 extern "C" {
@@ -853,6 +884,13 @@ void prdf_params_default(prdf_params* p) {
 }
 
 const char* prdf_last_error(void) { return g_err; }
+
+int prdf_release_cached_memory(void) {
+  std::lock_guard<std::mutex> lock(prdf::g_pool_mu);
+  for (int d = 0; d < prdf::kMaxDevices; ++d)
+    if (prdf::g_pool[d]) PRDF_CUDA(cudaMemPoolTrimTo(prdf::g_pool[d], 0));
+  return PRDF_OK;
+}
 
 const char* prdf_strerror(int code) {
   switch (code) {

@@ -37,7 +37,15 @@ struct Status {
   } while (0)
 
 // ------------------------------------------------------ device buffer ----
-// Stream-ordered device allocation (cudaMallocAsync) owned by RAII.
+// The library's stream-ordered memory pool on the current device (created on
+// first use, nullptr if that fails). Its release threshold is unbounded:
+// blocks freed by one call stay mapped for the next, where the default pool
+// hands them back to the driver at each synchronisation and large CSR and
+// workspace buffers would be mapped again by every build and batch update.
+// prdf_release_cached_memory() returns the unused reserve.
+cudaMemPool_t device_pool();
+
+// Stream-ordered device allocation (from device_pool()) owned by RAII.
 template <class T>
 struct DBuf {
   T* p = nullptr;
@@ -66,11 +74,13 @@ struct DBuf {
     s = stream;
     n = count;
     if (count == 0) return PRDF_OK;
-    cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), stream);
+    cudaMemPool_t pool = device_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync((void**)&p, count * sizeof(T), pool, stream)
+                         : cudaMallocAsync((void**)&p, count * sizeof(T), stream);
     if (e != cudaSuccess) {
       p = nullptr;
       n = 0;
-      set_error("cudaMallocAsync(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+      set_error("device allocation of %zu bytes: %s", count * sizeof(T), cudaGetErrorString(e));
       return PRDF_ENOMEM;
     }
     return PRDF_OK;

@@ -50,6 +50,19 @@ def test_csr_build_rmat(scale, nsamp):
     check_csr(gpu_graph(n, s, d), oracle.graph(n, s, d))
 
 
+def test_builds_after_releasing_the_memory_pool():
+    """Buffers freed by one graph are reused by the next from the library's pool;
+    after the reserve is released a new build still matches the oracle."""
+    n, s, d = synth.rmat(12, 60000, seed=4)
+    og = oracle.graph(n, s, d)
+    for _ in range(2):
+        g = gpu_graph(n, s, d)
+        check_csr(g, og)
+        del g
+    prdf().release_cached_memory()
+    check_csr(gpu_graph(n, s, d), og)
+
+
 def test_csr_build_grid():
     n, s, d = synth.grid(128, 0.05, seed=1)
     check_csr(gpu_graph(n, s, d), oracle.graph(n, s, d))
