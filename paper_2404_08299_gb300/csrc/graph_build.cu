@@ -28,7 +28,11 @@ constexpr int kThrWarp8 = 256;
 constexpr int kThrSmallBlock = 2048;
 constexpr int kThrBlock = 16384;
 constexpr int kSmallBlockThreads = 128;
+constexpr int kSmallBlockKeys = 16;  // keys per thread: kThrSmallBlock = 128 * 16
 constexpr int kSortBlockThreads = 512;
+constexpr int kSortBlockKeys = 32;   // kThrBlock = 512 * 32
+static_assert(kSmallBlockThreads * kSmallBlockKeys == kThrSmallBlock, "one small-block row fits the block's keys");
+static_assert(kSortBlockThreads * kSortBlockKeys == kThrBlock, "one block row fits the block's keys");
 constexpr int64_t kBitmapBudget = 512ll << 20;  // bytes of row bitmaps per pass
 constexpr int kHugeWordsPerThread = 32;
 constexpr int kHugeChunkWords = 256 * kHugeWordsPerThread;
@@ -251,49 +255,117 @@ __device__ __forceinline__ uint32_t block_scan_u32(uint32_t v, uint32_t* total, 
   return r;
 }
 
-// ---- rows up to the block's shared-memory keys: one block of NT threads,
-// bitonic sort in shared memory ----
-template <int NT>
+// ---- rows up to NT*E keys: one block per row, Batcher's bitonic sorting
+// network with E consecutive keys per thread in registers. Stages whose
+// partners lie E or more positions apart run in shared memory (one barrier
+// each, every active thread owning E/2 pairs); the closer stages run in
+// registers. A row of L keys is padded with sentinels to P2 = the power of
+// two >= max(L, 32E) and handled by P2/E threads (whole warps); the others
+// only meet the barriers. Shared memory keeps one pad slot per E keys so
+// that a thread's E keys and a warp's pair accesses spread over the banks.
+__device__ __forceinline__ void cswap_dir(uint64_t& a, uint64_t& b, bool up) {
+  const bool sw = (a > b) == up;
+  const uint64_t x = sw ? b : a, y = sw ? a : b;
+  a = x;
+  b = y;
+}
+
+template <int NT, int E>
 __global__ void __launch_bounds__(NT) k_sort_block(const int32_t* __restrict__ list, int64_t count,
                                                    const int64_t* __restrict__ start, const uint64_t* __restrict__ tmp,
                                                    uint64_t* __restrict__ out, uint32_t* __restrict__ ucnt) {
-  extern __shared__ uint64_t sk[];
+  static_assert((E & (E - 1)) == 0 && E >= 2 && NT % 32 == 0, "E a power of two, NT whole warps");
+  constexpr int LE = (E >= 32) ? 5 : (E >= 16) ? 4 : (E >= 8) ? 3 : (E >= 4) ? 2 : 1;
+  static_assert((1 << LE) == E, "E up to 32");
+  extern __shared__ uint64_t sk[];  // NT * (E + 1) keys
   __shared__ uint32_t scan_sh[NT / 32];
   __shared__ uint32_t total;
+  const int tid = threadIdx.x;
+  auto pad = [](int t) { return t + (t >> LE); };
   for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
     const int32_t v = list[i];
     const int64_t b = start[v];
     const int L = (int)(start[v + 1] - b);
-    int P2 = 64;
+    int P2 = 32 * E;
     while (P2 < L) P2 <<= 1;
-    for (int j = threadIdx.x; j < P2; j += NT) sk[j] = j < L ? tmp[b + j] : kSent;
+    const int A = P2 / E;  // active threads: a multiple of 32, <= NT
+    const bool act = tid < A;
+    for (int t = tid; t < P2; t += NT) sk[pad(t)] = t < L ? tmp[b + t] : kSent;
     __syncthreads();
-    for (int k = 2; k <= P2; k <<= 1) {
+    uint64_t r[E];
+#pragma unroll
+    for (int x = 0; x < E; ++x) r[x] = act ? sk[pad(tid * E + x)] : kSent;
+    // sizes 2 .. E: within the thread
+#pragma unroll
+    for (int k = 2; k <= E; k <<= 1) {
+      const bool up_hi = (tid & 1) == 0;  // direction bit of size E comes from the thread index
+#pragma unroll
       for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int t = threadIdx.x; t < P2; t += NT) {
-          const int p = t ^ j;
-          if (p > t) {
-            const uint64_t a = sk[t], c = sk[p];
-            const bool up = (t & k) == 0;
-            if ((a > c) == up) {
-              sk[t] = c;
-              sk[p] = a;
-            }
+#pragma unroll
+        for (int x = 0; x < E; ++x)
+          if ((x & j) == 0) cswap_dir(r[x], r[x | j], k < E ? (x & k) == 0 : up_hi);
+      }
+    }
+    // sizes 2E .. P2: far stages in shared memory, the last log2(E) in registers
+    for (int k = 2 * E; k <= P2; k <<= 1) {
+      __syncthreads();  // every thread has read its keys of the previous size
+      if (act) {
+#pragma unroll
+        for (int x = 0; x < E; ++x) sk[pad(tid * E + x)] = r[x];
+      }
+      __syncthreads();
+      for (int j = k >> 1; j >= E; j >>= 1) {
+        if (act) {
+          const int lj = __ffs(j) - 1;
+          for (int q = tid; q < (P2 >> 1); q += A) {
+            const int t = ((q >> lj) << (lj + 1)) | (q & (j - 1));
+            const int p = t | j;
+            uint64_t a = sk[pad(t)], c = sk[pad(p)];
+            cswap_dir(a, c, (t & k) == 0);
+            sk[pad(t)] = a;
+            sk[pad(p)] = c;
           }
         }
         __syncthreads();
       }
+      if (act) {
+#pragma unroll
+        for (int x = 0; x < E; ++x) r[x] = sk[pad(tid * E + x)];
+        const bool up = ((tid * E) & k) == 0;
+#pragma unroll
+        for (int j = E >> 1; j > 0; j >>= 1) {
+#pragma unroll
+          for (int x = 0; x < E; ++x)
+            if ((x & j) == 0) cswap_dir(r[x], r[x | j], up);
+        }
+      }
     }
-    // stable compaction of the first entry of each column run
-    const int per = P2 / NT > 0 ? P2 / NT : 1;
-    const int j0 = threadIdx.x * per;
-    uint32_t mine = 0;
-    for (int j = j0; j < j0 + per && j < P2; ++j)
-      mine += (sk[j] != kSent && (j == 0 || key_col(sk[j]) != key_col(sk[j - 1]))) ? 1u : 0u;
+    // keep the first key of each column run (the largest weight), in order
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int x = 0; x < E; ++x) sk[pad(tid * E + x)] = r[x];
+    }
+    __syncthreads();
+    const uint64_t before = (act && tid > 0) ? sk[pad(tid * E - 1)] : kSent;
+    uint32_t keep = 0, mine = 0;
+    if (act) {
+      uint64_t pv = before;
+#pragma unroll
+      for (int x = 0; x < E; ++x) {
+        const bool k1 = r[x] != kSent && ((tid == 0 && x == 0) || key_col(r[x]) != key_col(pv));
+        keep |= (k1 ? 1u : 0u) << x;
+        mine += k1 ? 1u : 0u;
+        pv = r[x];
+      }
+    }
     uint32_t pos = block_scan_u32<NT>(mine, &total, scan_sh);
-    for (int j = j0; j < j0 + per && j < P2; ++j)
-      if (sk[j] != kSent && (j == 0 || key_col(sk[j]) != key_col(sk[j - 1]))) out[b + pos++] = sk[j];
-    if (threadIdx.x == 0) ucnt[v] = total;
+    if (act) {
+#pragma unroll
+      for (int x = 0; x < E; ++x)
+        if (keep & (1u << x)) out[b + pos++] = r[x];
+    }
+    if (tid == 0) ucnt[v] = total;
     __syncthreads();
   }
 }
@@ -497,15 +569,17 @@ int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, c
   if (cls[1]) k_sort_warp<<<grid_for(cls[1] * 32, T), T, 0, s>>>(l1, cls[1], start.p, tmp.p, srt.p, ucnt.p);
   if (cls[2]) k_sort_warp8<<<grid_for(cls[2] * 32, T), T, 0, s>>>(l2, cls[2], start.p, tmp.p, srt.p, ucnt.p);
   if (cls[3]) {
-    const int smem = kThrSmallBlock * (int)sizeof(uint64_t);
-    k_sort_block<kSmallBlockThreads><<<grid_for(cls[3], 1, kSMs * 16), kSmallBlockThreads, smem, s>>>(
+    const int smem = kSmallBlockThreads * (kSmallBlockKeys + 1) * (int)sizeof(uint64_t);
+    k_sort_block<kSmallBlockThreads, kSmallBlockKeys><<<grid_for(cls[3], 1, kSMs * 16), kSmallBlockThreads, smem, s>>>(
         l3, cls[3], start.p, tmp.p, srt.p, ucnt.p);
   }
   if (cls[4]) {
-    const int smem = kThrBlock * (int)sizeof(uint64_t);
-    PRDF_CUDA(cudaFuncSetAttribute(k_sort_block<kSortBlockThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int smem = kSortBlockThreads * (kSortBlockKeys + 1) * (int)sizeof(uint64_t);
+    PRDF_CUDA(cudaFuncSetAttribute(k_sort_block<kSortBlockThreads, kSortBlockKeys>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int grid = (int)(cls[4] < kSMs * 2 ? cls[4] : kSMs * 2);
-    k_sort_block<kSortBlockThreads><<<grid, kSortBlockThreads, smem, s>>>(l4, cls[4], start.p, tmp.p, srt.p, ucnt.p);
+    k_sort_block<kSortBlockThreads, kSortBlockKeys><<<grid, kSortBlockThreads, smem, s>>>(l4, cls[4], start.p, tmp.p,
+                                                                                       srt.p, ucnt.p);
   }
   PRDF_LAUNCH_CHECK();
   if (cls[5]) {
