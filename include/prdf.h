@@ -84,6 +84,11 @@ typedef struct {
                           loop; 0 (default): the Static FP64 loop runs as one CUDA graph (device-side
                           convergence test, no host round trips) */
   int tile;            /* K-column calls: columns per index fetch (8, 16, 32, 64); 0 = automatic */
+  double expand_pull;  /* DF / DF-P: an expansion round after a sweep runs in pull form (each vertex
+                          outside the affected set looks for a frontier in-neighbour in G') when the
+                          frontier's out-edges exceed expand_pull * |E|, else in push form (Alg.
+                          affected). Both mark the same set. Default 1/16; >= 1 keeps the push form;
+                          must be >= 0. */
   void* stream;        /* cudaStream_t for all work; NULL = legacy default stream */
 } prdf_params;
 

@@ -235,6 +235,10 @@ int check_params(const prdf_params* p) {
     set_error("tau_f / tau_p must not be NaN");
     return PRDF_EINVAL;
   }
+  if (!(p->expand_pull >= 0.0)) {
+    set_error("expand_pull must be >= 0");
+    return PRDF_EINVAL;
+  }
   if (p->precision != PRDF_FP64 && p->precision != PRDF_FP32_REFINE) {
     set_error("unknown precision %d", p->precision);
     return PRDF_EINVAL;
@@ -348,6 +352,8 @@ int prepare_hub_split(prdf_graph* g, SweepArgs& a, cudaStream_t s) {
   return PRDF_OK;
 }
 
+int64_t hub_begin(const Relabel& rl);
+
 int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, cudaStream_t s, bool expand = true) {
   const int n = g->n;
   const int max_iter = p->max_iter;
@@ -360,6 +366,16 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
   if (dynamic) begins_from_counts(rl.pout_count, nco, cbo);
   const bool expanding = dynamic && expand;
   int kps = nonempty_classes(cb, nci) + (expanding ? nonempty_classes(cbo, nco) : 0);
+  // pull-form expansion: frontier count, thread rows below the two highest in-degree classes, warp rows above
+  const int64_t pull_warp_b = hub_begin(rl);
+  unsigned long long fthr = ~0ull;
+  if (expanding) {
+    PRDF_TRY(g->fwork.reserve((size_t)max_iter + 1, s));
+    PRDF_CUDA(cudaMemsetAsync(g->fwork.p, 0, sizeof(unsigned long long) * ((size_t)max_iter + 1), s));
+    const double lim = p->expand_pull * (double)rl.in.m;
+    fthr = lim >= 1.8e19 ? ~0ull : (unsigned long long)lim;
+    kps += 1 + (pull_warp_b > 0 ? 1 : 0) + (n > pull_warp_b ? 1 : 0);
+  }
   SweepArgs a;
   memset(&a, 0, sizeof(a));
   a.off = rl.in.off.p;
@@ -411,9 +427,12 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
       }
       PRDF_TRY(launch_sweep(a, rl.thr, cb, exact, dynamic, s));
       if (timed) PRDF_CUDA(cudaEventRecord(ev.back(), s));
-      if (expanding)
+      if (expanding) {
+        PRDF_TRY(launch_expand_pull(rl.in.off.p, rl.in.adj.p, rl.out.off.p, n, pull_warp_b, g->dN.p, g->dV.p,
+                                    g->fwork.p + i, fthr, g->resid.p + i, p->tol, s));
         PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, nullptr, g->resid.p + i,
-                               p->tol, s));
+                               p->tol, s, g->fwork.p + i, fthr));
+      }
     }
     launched = upto;
     PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid.p + launched - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
@@ -880,6 +899,7 @@ void prdf_params_default(prdf_params* p) {
   p->check_every = 8;
   p->time_sweeps = 0;
   p->tile = 0;
+  p->expand_pull = 1.0 / 16.0;
   p->stream = nullptr;
 }
 

@@ -38,6 +38,68 @@ __global__ void k_initial_affected(const int32_t* __restrict__ del_src, const in
 
 __device__ __forceinline__ bool converged(const uint64_t* r, double tol) { return r && bitsd(*r) <= tol; }
 
+// Direction of one expansion round, chosen on the device: the pull form when
+// the frontier's out-edges (*fw) exceed fthr, else the push form.
+__device__ __forceinline__ bool pull_chosen(const unsigned long long* fw, unsigned long long fthr) {
+  return fw && *fw > fthr;
+}
+
+// out-edges of the frontier: sum of |out(u)| over u with dN[u] set
+__global__ void k_frontier_edges(const uint8_t* __restrict__ dN, const int64_t* __restrict__ off, int64_t n,
+                                 unsigned long long* __restrict__ fw, const uint64_t* resid, double tol) {
+  if (converged(resid, tol)) return;
+  int64_t c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (dN[i]) c += off[i + 1] - off[i];
+  c = warp_sum_i64(c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(fw, (unsigned long long)c);
+}
+
+// Pull form of one expansion round over G' (the same marks as the push form,
+// since w is an out-neighbour of u exactly when u is an in-neighbour of w): a
+// vertex outside dV joins it when an in-neighbour is in the frontier. Only
+// w's own thread (or warp) reads or writes dV[w]; the scan stops at the first
+// frontier in-neighbour.
+__global__ void __launch_bounds__(kThreads) k_pull_thread(const int64_t* __restrict__ off,
+                                                          const int32_t* __restrict__ adj, int64_t begin, int64_t end,
+                                                          const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
+                                                          const unsigned long long* fw, unsigned long long fthr,
+                                                          const uint64_t* resid, double tol) {
+  if (converged(resid, tol) || !pull_chosen(fw, fthr)) return;
+  for (int64_t w = begin + blockIdx.x * (int64_t)kThreads + threadIdx.x; w < end; w += (int64_t)gridDim.x * kThreads) {
+    if (dV[w]) continue;
+    const int64_t e = off[w + 1];
+    for (int64_t j = off[w]; j < e; ++j)
+      if (dN[adj[j]]) {
+        dV[w] = 1;
+        break;
+      }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_pull_warp(const int64_t* __restrict__ off,
+                                                        const int32_t* __restrict__ adj, int64_t begin, int64_t end,
+                                                        const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
+                                                        const unsigned long long* fw, unsigned long long fthr,
+                                                        const uint64_t* resid, double tol) {
+  if (converged(resid, tol) || !pull_chosen(fw, fthr)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  for (int64_t w = begin + warp; w < end; w += nwarps) {
+    if (dV[w]) continue;  // the same value on every lane
+    const int64_t b = off[w], e = off[w + 1];
+    for (int64_t j0 = b; j0 < e; j0 += 32) {
+      const int64_t j = j0 + lane;
+      const bool hit = j < e && dN[adj[j]];
+      if (__any_sync(0xffffffffu, hit)) {
+        if (lane == 0) dV[w] = 1;
+        break;
+      }
+    }
+  }
+}
+
 // Mark the targets of edges [j0, e) of one row, `step` apart, kU per lane in
 // flight: the index loads of a round issue together, then their flag loads.
 template <int kU>
@@ -69,8 +131,9 @@ __global__ void __launch_bounds__(kThreads) k_expand_group(const int64_t* __rest
                                                            const int32_t* __restrict__ adj,
                                                            const int32_t* __restrict__ P, int64_t begin, int64_t end,
                                                            const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
-                                                           uint8_t* __restrict__ dF, const uint64_t* resid, double tol) {
-  if (converged(resid, tol)) return;
+                                                           uint8_t* __restrict__ dF, const uint64_t* resid, double tol,
+                                                           const unsigned long long* fw, unsigned long long fthr) {
+  if (converged(resid, tol) || pull_chosen(fw, fthr)) return;
   const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
   const int64_t gid = (blockIdx.x * (int64_t)kThreads + threadIdx.x) / G;
   const int64_t ng = ((int64_t)gridDim.x * kThreads) / G;
@@ -87,8 +150,9 @@ __global__ void __launch_bounds__(kThreads) k_expand_block(const int64_t* __rest
                                                            const int32_t* __restrict__ adj,
                                                            const int32_t* __restrict__ P, int64_t begin, int64_t end,
                                                            const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
-                                                           uint8_t* __restrict__ dF, const uint64_t* resid, double tol) {
-  if (converged(resid, tol)) return;
+                                                           uint8_t* __restrict__ dF, const uint64_t* resid, double tol,
+                                                           const unsigned long long* fw, unsigned long long fthr) {
+  if (converged(resid, tol) || pull_chosen(fw, fthr)) return;
   const int64_t S = gridDim.y, y = blockIdx.y;
   for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
     const int32_t u = P[i];
@@ -122,7 +186,8 @@ int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, cons
 }
 
 int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, const int64_t* cb, int nclass,
-                  const uint8_t* dN, uint8_t* dV, uint8_t* dF, const uint64_t* resid, double tol, cudaStream_t s) {
+                  const uint8_t* dN, uint8_t* dV, uint8_t* dF, const uint64_t* resid, double tol, cudaStream_t s,
+                  const unsigned long long* fw, unsigned long long fthr) {
   const int maxg = kSMs * 8;
   for (int c = 0; c < nclass; ++c) {
     const int64_t b = cb[c], e = cb[c + 1];
@@ -130,16 +195,31 @@ int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, cons
     const int64_t cnt = e - b;
     const int kind = (nclass == 4) ? c : (c == nclass - 1 ? 3 : c);
     switch (kind) {
-      case 0: k_expand_group<1><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
-      case 1: k_expand_group<8><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
-      case 2: k_expand_group<32><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol); break;
+      case 0: k_expand_group<1><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol, fw, fthr); break;
+      case 1: k_expand_group<8><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol, fw, fthr); break;
+      case 2: k_expand_group<32><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol, fw, fthr); break;
       default: {
         const dim3 grid(grid_for(cnt, 1, maxg / kExpandSlices), kExpandSlices);
-        k_expand_block<<<grid, kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol);
+        k_expand_block<<<grid, kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol, fw, fthr);
         break;
       }
     }
   }
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+int launch_expand_pull(const int64_t* in_off, const int32_t* in_adj, const int64_t* out_off, int64_t n,
+                       int64_t warp_begin, const uint8_t* dN, uint8_t* dV, unsigned long long* fw,
+                       unsigned long long fthr, const uint64_t* resid, double tol, cudaStream_t s) {
+  const int maxg = kSMs * 8;
+  k_frontier_edges<<<grid_for(n, kThreads, kSMs * 4), kThreads, 0, s>>>(dN, out_off, n, fw, resid, tol);
+  if (warp_begin > 0)
+    k_pull_thread<<<grid_for(warp_begin, kThreads, maxg), kThreads, 0, s>>>(in_off, in_adj, 0, warp_begin, dN, dV, fw,
+                                                                            fthr, resid, tol);
+  if (n > warp_begin)
+    k_pull_warp<<<grid_for((n - warp_begin) * 32, kThreads, maxg), kThreads, 0, s>>>(in_off, in_adj, warp_begin, n,
+                                                                                      dN, dV, fw, fthr, resid, tol);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }

@@ -204,11 +204,19 @@ int launch_sweep(const SweepArgs& a, const PartThr& t, const int64_t* class_begi
 int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask, int64_t n_del,
                             const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins, const int32_t* map,
                             uint8_t* dV, uint8_t* dN, cudaStream_t s);
-// expandAffected over the out-degree partition; skipped on the device when *resid <= tol.
+// expandAffected over the out-degree partition; skipped on the device when *resid <= tol,
+// and when fw (nullable) is given, also when *fw > fthr (the pull form runs instead).
 // dF (nullable): also mark in dF every vertex that was not yet in dV (one
 // round of Dynamic Traversal's reachability closure).
 int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, const int64_t* cb, int nclass,
-                  const uint8_t* dN, uint8_t* dV, uint8_t* dF, const uint64_t* resid, double tol, cudaStream_t s);
+                  const uint8_t* dN, uint8_t* dV, uint8_t* dF, const uint64_t* resid, double tol, cudaStream_t s,
+                  const unsigned long long* fw = nullptr, unsigned long long fthr = 0);
+// The same round in pull form over G' (in_off/in_adj; rows from warp_begin on
+// take a warp each): first sums the frontier's out-edges into *fw (zero on
+// entry; out_off is G's offsets), then marks only if *fw > fthr.
+int launch_expand_pull(const int64_t* in_off, const int32_t* in_adj, const int64_t* out_off, int64_t n,
+                       int64_t warp_begin, const uint8_t* dN, uint8_t* dV, unsigned long long* fw,
+                       unsigned long long fthr, const uint64_t* resid, double tol, cudaStream_t s);
 int count_flags(const uint8_t* f, int64_t n, unsigned long long* dev_out, cudaStream_t s);
 
 }  // namespace prdf
@@ -239,6 +247,7 @@ struct prdf_graph {
   prdf::DBuf<uint8_t> dV, dN, wrote;
   prdf::DBuf<uint8_t> dF;  // Dynamic Traversal: next frontier of the closure
   prdf::DBuf<unsigned long long> counter;
+  prdf::DBuf<unsigned long long> fwork;  // frontier out-edges of each expansion round
   prdf::DBuf<int> ctl;               // device iteration counter of the graph-driven loop
   cudaStream_t cap_stream = nullptr; // private stream used to capture graph bodies
   cudaGraphExec_t static_exec = nullptr;

@@ -113,7 +113,8 @@ def test_naive_dynamic_from_previous_ranks():
 def test_static_rejects_bad_params():
     n, s, d = synth.rmat(6, 300, seed=1)
     g = gpu_graph(n, s, d)
-    for kw in ({"alpha": 1.0}, {"alpha": 0.0}, {"tol": 0.0}, {"max_iter": 0}, {"alpha": float("nan")}):
+    for kw in ({"alpha": 1.0}, {"alpha": 0.0}, {"tol": 0.0}, {"max_iter": 0}, {"alpha": float("nan")},
+               {"expand_pull": -1.0}, {"expand_pull": float("nan")}):
         with pytest.raises(prdf().PrdfError) as e:
             g.pagerank_static(**kw)
         assert e.value.code == -1
@@ -133,11 +134,13 @@ def _dynamic_case(seed, scale, nsamp, size):
     return g, og1, R0, (ds, dd, is_, id_, de, ie, dmo, imo)
 
 
+@pytest.mark.parametrize("expand_pull", [1 / 16, 0.0, 2.0])  # automatic, always pull, always push
 @pytest.mark.parametrize("prune", [1, 0])
 @pytest.mark.parametrize("seed,scale,nsamp,size", [(1, 8, 3000, 20), (2, 10, 12000, 60), (3, 12, 50000, 5)])
-def test_dfp_matches_oracle_step_by_step(prune, seed, scale, nsamp, size):
+def test_dfp_matches_oracle_step_by_step(prune, seed, scale, nsamp, size, expand_pull):
     g, og1, R0, (ds, dd, is_, id_, de, ie, dmo, imo) = _dynamic_case(seed, scale, nsamp, size)
-    R, st, dV = g.pagerank_dfp(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True, prune=prune)
+    R, st, dV = g.pagerank_dfp(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True, prune=prune,
+                               expand_pull=expand_pull)
     Ro, sto, dVo, trace = oracle.pagerank_dfp(og1, ds, dd, is_, host(R0), del_mask=dmo, ins_mask=imo, prune=bool(prune))
     assert st.iterations == sto.iterations
     assert st.affected_initial == trace[0]
