@@ -50,13 +50,6 @@ struct BlockSum {
   }
 };
 
-// the two columns (col, col + 1) of row u; K even: one 8-byte load
-__device__ __forceinline__ float2 ld_pair(const float* R, int64_t u, int K, int col, bool two) {
-  const float* src = R + u * K + col;
-  if (two && (K & 1) == 0) return __ldg(reinterpret_cast<const float2*>(src));
-  return make_float2(__ldg(src), two ? __ldg(src + 1) : 0.f);
-}
-
 __device__ __forceinline__ void block_max2_u32(uint32_t dmax, uint32_t rmax, uint32_t* out) {
   __shared__ uint32_t sd[32], sr[32];
 #pragma unroll
@@ -595,7 +588,6 @@ template <int LPE>
 void launch32_tile(const Ppr32Args& a, const PprHub& h, float2* part, int64_t hub_b, int64_t n, int c0, int tile,
                    cudaStream_t s) {
   const int maxg = kSMs * 8;
-  constexpr int kSlots = 32 / LPE;
   if (hub_b > 0) k_ppr32_group<LPE, 4><<<grid_for(hub_b * LPE, kThreads, maxg), kThreads, 0, s>>>(a, 0, hub_b, c0);
   if (h.begin > hub_b)
     k_ppr32_warp<LPE, 8><<<grid_for((h.begin - hub_b) * 32, kThreads, maxg), kThreads, 0, s>>>(a, hub_b, h.begin, c0);
@@ -603,7 +595,6 @@ void launch32_tile(const Ppr32Args& a, const PprHub& h, float2* part, int64_t hu
     k_ppr32_hub_part<LPE, 8><<<grid_for(h.nchunk * 32, kThreads, maxg), kThreads, 0, s>>>(a, h, c0, tile, part);
     k_ppr32_hub_finish<LPE><<<grid_for(h.nhub * LPE, kThreads, maxg), kThreads, 0, s>>>(a, h, c0, tile, part);
   }
-  (void)kSlots;
 }
 
 template <int LPE>
