@@ -111,21 +111,28 @@ class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, index):
+    def __init__(self, index, keep_dir=None):
+        """Samples nvidia-smi every 200 ms into a temporary CSV; with keep_dir, the CSV is also
+        copied there as clocks_rank<index>.csv."""
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+        self.keep_dir = keep_dir
+        self.path = None
 
     def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="clocks_rank%d_" % self.index, suffix=".csv")
+        self.f = os.fdopen(fd, "w")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            self.f.close()
+            os.remove(self.path)
 
     def stop(self):
         if self.proc is None:
@@ -136,21 +143,34 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
-            for line in f:
-                p = [x.strip() for x in line.split(",")]
-                if len(p) < 9:
-                    continue
-                try:
-                    sm.append(float(p[1]))
-                    mx.append(float(p[2]))
-                except ValueError:
-                    continue
-                for k, nm in enumerate(names):
-                    if p[5 + k].lower().startswith("active"):
-                        reasons.add(nm)
+            lines = f.readlines()
+        try:
+            if self.keep_dir:
+                import shutil
+                os.makedirs(self.keep_dir, exist_ok=True)
+                shutil.copyfile(self.path, os.path.join(self.keep_dir, "clocks_rank%d.csv" % self.index))
+            os.remove(self.path)
+        except OSError:
+            pass
+        return self.summarise(lines)
+
+    @classmethod
+    def summarise(cls, lines):
+        """Median SM clock, maximum clock and the throttle reasons seen active, from the CSV lines."""
+        sm, mx, reasons = [], [], set()
+        for line in lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(cls.REASONS):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
@@ -432,6 +452,8 @@ def main():
     ap.add_argument("--profile-precision", type=int, default=0,
                     help="with --profile-run: 0 = FP64 sweeps, 1 = FP32 stage then FP64 (mixed precision)")
     ap.add_argument("--tile", type=int, default=0, help="column tile of the K-column calls (0: default)")
+    ap.add_argument("--clock-dir", default=None,
+                    help="also keep the nvidia-smi clock samples of the timed region in this directory")
     ap.add_argument("--profile-ppr", action="store_true",
                     help="build the 2^22 weighted graph and run a few K=64 PPR sweeps (for ncu captures)")
     ap.add_argument("--profile-dfp", type=float, default=0.0,
@@ -527,7 +549,7 @@ def main():
     torch.cuda.synchronize()
 
     # timed region: K full solves, device-timed with CUDA events on the launching stream
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clock_dir)
     clocks.start()
     time.sleep(0.3)
     if dist:

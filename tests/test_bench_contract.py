@@ -40,3 +40,38 @@ def test_reference_arm_other_ranks_exit_quietly():
              env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_clock_sampler_summary_and_kept_copy(tmp_path, monkeypatch):
+    """The clock record during the timed region: a stand-in nvidia-smi prints two samples, one
+    with power capping active; the summary takes the median clock and lists the reason."""
+    fake = tmp_path / "bin"
+    fake.mkdir()
+    exe = fake / "nvidia-smi"
+    exe.write_text("#!/bin/sh\n"
+                   "echo '0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                   "echo '0, 1950, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                   "sleep 30\n")
+    exe.chmod(0o755)
+    monkeypatch.setenv("PATH", str(fake) + os.pathsep + os.environ["PATH"])
+    sys.path.insert(0, ROOT)
+    import time
+    import bench
+    keep = tmp_path / "keep"
+    c = bench.ClockSampler(0, str(keep))
+    c.start()
+    time.sleep(1.0)
+    r = c.stop()
+    assert r == {"sm_mhz": 2010.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+    assert (keep / "clocks_rank0.csv").read_text().count("\n") == 2
+    assert not os.path.exists(c.path)
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.start()
+    assert c.stop() is None
+    assert not os.path.exists(c.path)
