@@ -68,6 +68,12 @@ def test_graph_create_rejects_bad_sizes_without_touching_the_gpu(built_lib):
     assert built_lib.prdf_strerror(-1) == b"invalid argument"
 
 
+def test_release_cached_memory_without_a_pool_is_a_no_op(built_lib):
+    # no device allocation has happened in this process, so no pool exists to trim
+    built_lib.prdf_release_cached_memory.restype = ctypes.c_int
+    assert built_lib.prdf_release_cached_memory() == 0
+
+
 def test_product_path_has_no_cpu_fallback(monkeypatch, tmp_path):
     import paper_2404_08299_gb300 as prdf
     monkeypatch.setattr(prdf, "LIB_PATH", str(tmp_path / "missing.so"))
