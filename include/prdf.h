@@ -81,8 +81,10 @@ typedef struct {
   int prune;           /* DF-P (1, default) or DF (0), for prdf_pagerank_dfp */
   int check_every;     /* sweeps launched between host convergence checks, default 8 */
   int time_sweeps;     /* 1: time every rank sweep with CUDA events (stats->ms_sweep) from a host-driven
-                          loop; 0 (default): the Static FP64 loop runs as one CUDA graph (device-side
-                          convergence test, no host round trips) */
+                          loop (a residual read every check_every sweeps); 0 (default): every sweep
+                          loop (Static, DF, DF-P, DT, and the FP32 stage of each) runs as one CUDA
+                          graph with the convergence test on the device, no host round trips. Both
+                          give identical results. */
   int tile;            /* K-column calls: columns per index fetch (8, 16, 32, 64); 0 = automatic */
   double expand_pull;  /* DF / DF-P: an expansion round after a sweep runs in pull form (each vertex
                           outside the affected set looks for a frontier in-neighbour in G') when the
@@ -194,21 +196,23 @@ int prdf_graph_set_thresholds(prdf_graph* g, int which, int n_thr, const int64_t
 int prdf_partition(prdf_graph* g, int which, int32_t* P, int64_t* counts_host, void* stream);
 
 /*
- * Alg. partition of prdf_partition, for callers that cannot allocate device
- * memory at this point (their memory is handed out up front by a pool that
- * owns all of it, or their path must not take the device-wide
- * synchronisation that cudaMalloc/cudaFree can imply). The paper has no
- * counterpart: this is a library service. It allocates nothing: its scratch
- * is a fixed device array inside the library (about 512 KB, held by every
- * GPU that loads the library until exit).
+ * Degree partition, the same result as prdf_partition, for callers that
+ * cannot allocate device memory at this point (their memory is handed out up
+ * front by a pool that owns all of it, or their path must not take the
+ * device-wide synchronisation that cudaMalloc/cudaFree can imply). The paper
+ * has no counterpart: this is a library service. It allocates nothing: its
+ * scratch is a fixed device array inside the library (about 512 KB, held by
+ * every GPU that loads the library until exit).
  * off: int64[n+1] device CSR offsets (degree = off[v+1] - off[v]);
  * thresholds as in prdf_graph_set_thresholds (n_thr in 1..3, host array);
  * P: int32[n] device output; counts_host: host int64[n_thr+1] output.
  * n must be in [1, 16777216]; larger n returns PRDF_EINVAL with a message.
  * The first call on each device looks the scratch's device address up
- * (make it before any stream capture). Calls share the scratch: calls that
- * overlap on the GPU race and must be serialised by the caller. Returns
- * after the results are complete on `stream`.
+ * (make it before any stream capture) and keeps it for the life of the
+ * process, so calls after a reset of that device (cudaDeviceReset) are not
+ * supported. Calls share the scratch: calls that overlap on the GPU race and
+ * must be serialised by the caller. Returns after the results are complete
+ * on `stream`.
  */
 int prdf_partition_noalloc(const int64_t* off, int32_t n, int n_thr, const int64_t* thr_host, int32_t* P,
                            int64_t* counts_host, void* stream);
@@ -238,7 +242,12 @@ int prdf_expand_affected(prdf_graph* g, const uint8_t* dN, uint8_t* dV, void* st
  * Static PageRank, Alg. static with Eq. 1: R = 1/n (or R0 if not NULL, which
  * is Naive-dynamic, Alg. naive), partition G' by in-degree, then synchronous
  * pull sweeps until ||R_new - R||_inf <= p->tol or p->max_iter sweeps.
- * ranks: double[n] device output. R0: double[n] device or NULL.
+ * ranks: double[n] device output. R0: double[n] device or NULL; its entries
+ * must be finite and >= 0 and sum to at most 4 (a rank vector sums to 1; the
+ * exact accumulator of the sweeps holds in-neighbour sums below 16), else
+ * PRDF_EINVAL. p->precision = PRDF_FP32_REFINE: FP32 sweeps with compensated
+ * sums until ||dR||_inf <= p->tol_fp32_rel * ||R||_inf, then FP64 sweeps from
+ * their result to p->tol (stats->iterations_fp32 counts the FP32 sweeps).
  * stats may be NULL.
  */
 int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, double* ranks, prdf_stats* stats);
@@ -249,8 +258,16 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
  * deletions (del_src, del_dst, del_mask) and insertions (ins_src, ins_mask)
  * as in prdf_initial_affected (pass the effectiveness masks from
  * prdf_graph_apply_batch to use the effective Delta^{t-}, Delta^{t+});
- * prev_ranks: R^{t-1}, double[n]; ranks: double[n] output (may alias
- * prev_ranks). dV_out: optional uint8[n] receiving the final deltaV.
+ * prev_ranks: R^{t-1}, double[n], in the domain given for R0 of
+ * prdf_pagerank_static (else PRDF_EINVAL); ranks: double[n] output (may
+ * alias prev_ranks). dV_out: optional uint8[n] receiving the final deltaV.
+ * p->precision = PRDF_FP32_REFINE: DF / DF-P sweeps on FP32 ranks with
+ * compensated sums, the prune and expand tests evaluated in FP32, until
+ * ||dR||_inf <= p->tol_fp32_rel * ||R||_inf over the updated vertices; then
+ * FP64 DF / DF-P sweeps to p->tol from that result, on the affected set the
+ * FP32 stage left plus every vertex whose rank it changed (their prune tests
+ * are then decided in FP64). Vertices the FP32 stage left unchanged keep
+ * their FP64 value.
  */
 int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask,
                       int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins,
@@ -266,8 +283,10 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
  * round adds none, i.e. until the affected count stops changing); then Eq. 1
  * sweeps on the affected vertices only, with no prune and no expansion (p->prune
  * and p->tau_f are ignored), until ||R_new - R||_inf <= p->tol or p->max_iter.
- * Unaffected vertices keep prev_ranks. Arguments as for prdf_pagerank_dfp;
- * dV_out receives the closed affected set, stats->affected_initial its size.
+ * Unaffected vertices keep prev_ranks. Arguments as for prdf_pagerank_dfp
+ * (PRDF_FP32_REFINE: the Eq. 1 sweeps run in FP32 to the relative stop, then
+ * in FP64 to p->tol); dV_out receives the closed affected set,
+ * stats->affected_initial its size.
  */
 int prdf_pagerank_dt(prdf_graph* g, const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask,
                      int64_t n_del, const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins,

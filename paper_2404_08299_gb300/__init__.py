@@ -22,6 +22,8 @@ PRDF_FP64, PRDF_FP32_REFINE = 0, 1
 PRDF_ACC_EXACT, PRDF_ACC_FP64 = 0, 1
 PRDF_ADD_SELF_LOOPS = 1
 
+NOALLOC_MAX_N = 1 << 24  # vertex limit of the fixed scratch of prdf_partition_noalloc
+
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ESTATE"}
 
 
@@ -163,12 +165,16 @@ def partition_noalloc(off: torch.Tensor, thresholds):
     """Alg. partition of a device CSR offset array without any device allocation
     (prdf_partition_noalloc). Returns (P int32[n], class sizes)."""
     n = off.numel() - 1
-    P = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    if not 1 <= n <= NOALLOC_MAX_N:
+        raise ValueError("partition_noalloc needs 1 <= n <= %d, got n = %d" % (NOALLOC_MAX_N, n))
+    if not 1 <= len(thresholds) <= 3:
+        raise ValueError("partition_noalloc takes 1 to 3 thresholds")
+    P = torch.empty(n, dtype=torch.int32, device="cuda")
     thr = (ctypes.c_int64 * len(thresholds))(*[int(t) for t in thresholds])
     counts = (ctypes.c_int64 * 4)()
     _check(lib().prdf_partition_noalloc(_ptr(off, torch.int64, name="off"), n, len(thresholds), thr, _ptr(P), counts,
                                         _stream()))
-    return P[:n], list(counts)[:len(thresholds) + 1]
+    return P, list(counts)[:len(thresholds) + 1]
 
 
 class Graph:

@@ -61,22 +61,48 @@ __global__ void k_eq2_factor(const double* __restrict__ deg, int32_t n, double a
     kf[i] = 1.0 / (1.0 - alpha / deg[i]);
 }
 
-// FP32 stage set-up: y[i] = R0[perm[i]] / |out| (R0 = NULL: 1/n) and FP32 degrees
+// FP32 stage set-up: y[i] = R0[perm[i]] / |out| (R0 = NULL: 1/n), rounded
+// once from the FP64 quotient, into ya (and yb), FP32 degrees, and for DF-P
+// the Eq. 2 factor (kf32 = NULL: not needed)
 __global__ void k_init_y(const double* __restrict__ R0, const int32_t* __restrict__ perm, int32_t n,
-                         const double* __restrict__ deg, const double* __restrict__ inv, float* __restrict__ y,
-                         float* __restrict__ degf, float* __restrict__ invf) {
+                         const double* __restrict__ deg, const double* __restrict__ inv,
+                         const double* __restrict__ kf, float* __restrict__ ya, float* __restrict__ yb,
+                         float* __restrict__ degf, float* __restrict__ invf, float* __restrict__ kf32) {
   const double r = 1.0 / (double)n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    y[i] = (float)((R0 ? R0[perm[i]] : r) * inv[i]);
+    const float y = (float)((R0 ? R0[perm[i]] : r) * inv[i]);
+    ya[i] = y;
+    if (yb) yb[i] = y;
     degf[i] = (float)deg[i];
     invf[i] = (float)inv[i];
+    if (kf32) kf32[i] = (float)kf[i];
   }
 }
 
-// FP64 stage start: x = y (exact widening)
+// FP64 stage start of Static: x = y (exact widening)
 __global__ void k_widen(const float* __restrict__ y, int32_t n, double* __restrict__ x) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = (double)y[i];
+}
+
+// FP64 stage start of DF / DF-P / DT: xa holds R^{t-1} / |out| in FP64. A
+// vertex whose FP32 value still equals that start rounded to FP32 was not
+// changed by the FP32 stage (never affected, or changed below FP32
+// resolution) and keeps its FP64 value; the others take the widened FP32
+// value and are affected again, so that the FP64 sweeps decide their
+// prune test in FP64. Both buffers get the result (the copy-through of
+// unaffected vertices relies on them being equal at the start of a loop).
+__global__ void k_widen_keep(const float* __restrict__ y, int32_t n, double* __restrict__ xa, double* __restrict__ xb,
+                             uint8_t* __restrict__ dV) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x0 = xa[i];
+    const float yi = y[i];
+    const bool same = (float)x0 == yi;
+    const double x = same ? x0 : (double)yi;
+    xa[i] = x;
+    xb[i] = x;
+    if (!same && !dV[i]) dV[i] = 1;
+  }
 }
 
 // dst[i, :] = src[perm[i], :] for [n, K] row-major matrices
@@ -145,14 +171,37 @@ __global__ void k_finalize(const double* __restrict__ x, const double* __restric
   }
 }
 
-__global__ void k_check_ids(const int32_t* a, const int32_t* b, int64_t cnt, int32_t n, int* bad) {
+__global__ void k_check_ids(const int32_t* a, const int32_t* b, int64_t cnt, int32_t n, unsigned long long* bad) {
   int f = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
     if (a && (a[i] < 0 || a[i] >= n)) f = 1;
     if (b && (b[i] < 0 || b[i] >= n)) f = 1;
   }
   f = __reduce_or_sync(0xffffffffu, f);
-  if ((threadIdx.x & 31) == 0 && f) atomicOr(bad, 1);
+  if ((threadIdx.x & 31) == 0 && f) atomicOr(bad, 1ull);
+}
+
+// Start-vector check: bad[1] |= 1 for an entry that is negative, NaN or infinite;
+// *sum accumulates the entries (one FP64 atomic per block).
+__global__ void k_check_ranks(const double* __restrict__ R, int64_t n, unsigned long long* bad, double* sum) {
+  __shared__ double sh[32];
+  double acc = 0;
+  int f = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = R[i];
+    if (!(x >= 0.0) || !isfinite(x)) f = 1;
+    else acc += x;
+  }
+  f = __reduce_or_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0 && f) atomicOr(bad + 1, 1ull);
+  acc = warp_sum_f64(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    t = warp_sum_f64(t);
+    if (threadIdx.x == 0 && t != 0.0) atomicAdd(sum, t);
+  }
 }
 
 // position of (u, v) in a sorted CSR row, or -1
@@ -290,22 +339,49 @@ void class_begins(const prdf_graph* g, int which, int64_t* cb) {
   for (int c = 0; c < C; ++c) cb[c + 1] = cb[c] + g->pcount[which][c];
 }
 
-int check_ids(prdf_graph* g, const int32_t* a, const int32_t* b, int64_t cnt, cudaStream_t s) {
-  if (cnt == 0) return PRDF_OK;
-  if ((!a && !b)) return PRDF_OK;
-  DBuf<int> bad;
-  PRDF_TRY(bad.alloc(1, s));
-  PRDF_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-  k_check_ids<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(a, b, cnt, g->n, bad.p);
+// Largest sum of a start vector the sweeps accept. The exact accumulator
+// holds in-neighbour sums below 16, and an in-neighbour sum never exceeds the
+// sum of all ranks (Eq. 1 keeps that sum near 1); a PageRank vector sums to 1.
+constexpr double kMaxRankSum = 4.0;
+
+// Check caller inputs with one device pass and one host synchronisation:
+// the ids of (a, b)[0, na) and (c, d)[0, nc) in [0, n) (NULL arrays skipped),
+// and a start vector R (NULL: none) with finite, non-negative entries that
+// sum to at most kMaxRankSum. what names the vector in the message.
+int check_inputs(prdf_graph* g, const int32_t* a, const int32_t* b, int64_t na, const int32_t* c, const int32_t* d,
+                 int64_t nc, const double* R, const char* what, cudaStream_t s) {
+  const bool ids1 = na > 0 && (a || b), ids2 = nc > 0 && (c || d);
+  if (!ids1 && !ids2 && !R) return PRDF_OK;
+  PRDF_TRY(g->chk.reserve(4, s));
+  PRDF_CUDA(cudaMemsetAsync(g->chk.p, 0, 4 * sizeof(unsigned long long), s));
+  if (ids1) k_check_ids<<<grid_for(na, kThreads), kThreads, 0, s>>>(a, b, na, g->n, g->chk.p);
+  if (ids2) k_check_ids<<<grid_for(nc, kThreads), kThreads, 0, s>>>(c, d, nc, g->n, g->chk.p);
+  if (R)
+    k_check_ranks<<<grid_for(g->n, kThreads, kSMs * 4), kThreads, 0, s>>>(R, g->n, g->chk.p,
+                                                                          reinterpret_cast<double*>(g->chk.p + 2));
   PRDF_LAUNCH_CHECK();
-  PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->chk.p, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
-  if (*(int*)g->ws.host_i64) {
+  const int64_t* h = g->ws.host_i64;
+  if (h[0]) {
     set_error("vertex id outside [0, %d)", g->n);
     return PRDF_EINVAL;
   }
+  if (R) {
+    double sum;
+    memcpy(&sum, &h[2], sizeof(double));
+    if (h[1]) {
+      set_error("%s: entries must be finite and >= 0", what);
+      return PRDF_EINVAL;
+    }
+    if (!(sum <= kMaxRankSum)) {
+      set_error("%s: entries sum to %g, above %g", what, sum, kMaxRankSum);
+      return PRDF_EINVAL;
+    }
+  }
   return PRDF_OK;
 }
+
 
 struct Timer {
   cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -322,8 +398,8 @@ struct Timer {
 struct IterResult {
   int iters = 0;          // sweeps up to and including the first converged one (or max_iter)
   int converged = 0;
-  double final_delta = 0;
-  int final_buf = 0;      // 0: xa holds the result, 1: xb
+  double final_delta = 0; // FP64 loop: L-inf change of the last sweep; FP32 stage: max |dR| of it
+  int final_buf = 0;      // 0: xa (ya) holds the result, 1: xb (yb)
   int launched = 0;       // sweeps issued
   float ms_sweep = 0;     // device time of the first `iters` sweeps (time_sweeps)
   long long kernels = 0;  // kernels launched
@@ -335,71 +411,200 @@ int nonempty_classes(const int64_t* cb, int nclass) {
   return k;
 }
 
-// Launch sweeps (and, for DF/DF-P, the expand after each) until the L-inf
-// change of a sweep is <= tol or max_iter sweeps ran. The host reads the
-// residual every check_every sweeps; sweeps launched past convergence exit at
-// once on the device.
 int ensure_hub(prdf_graph* g, const Csr& c, PprHubTable& t, cudaStream_t s);
-
-// Static sweeps cut the highest in-degree class's rows into the hub chunks
-// of G' (exact partial sums per chunk); the table and the partial buffer are
-// made here, outside any stream capture.
-int prepare_hub_split(prdf_graph* g, SweepArgs& a, cudaStream_t s) {
-  PRDF_TRY(ensure_hub(g, g->rl.in, g->hub_in, s));
-  PRDF_TRY(g->sweep_hub_part.reserve((size_t)(g->hub_in.nchunk > 0 ? g->hub_in.nchunk : 1), s));
-  a.hub = g->hub_in.view();
-  a.hub_part = g->sweep_hub_part.p;
-  return PRDF_OK;
-}
-
 int64_t hub_begin(const Relabel& rl);
 
-int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, cudaStream_t s, bool expand = true) {
-  const int n = g->n;
-  const int max_iter = p->max_iter;
-  PRDF_TRY(g->resid.reserve((size_t)max_iter + 1, s));
-  PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t) * ((size_t)max_iter + 1), s));
-  const Relabel& rl = g->rl;
-  int64_t cb[prdf::kMaxThr + 2], cbo[prdf::kMaxThr + 2];
-  const int nci = rl.thr.n + 1, nco = g->thr[PRDF_OUT].n + 1;
-  begins_from_counts(rl.count, nci, cb);
-  if (dynamic) begins_from_counts(rl.pout_count, nco, cbo);
-  const bool expanding = dynamic && expand;
-  int kps = nonempty_classes(cb, nci) + (expanding ? nonempty_classes(cbo, nco) : 0);
-  // pull-form expansion: frontier count, thread rows below the two highest in-degree classes, warp rows above
-  const int64_t pull_warp_b = hub_begin(rl);
+// ----------------------------------------------------------- the loop ----
+// One loop of synchronous sweeps, Alg. static (every vertex, Eq. 1) or
+// Alg. frontier / Alg. traversal (affected vertices, Eq. 1 or Eq. 2, with an
+// expansion round of Alg. affected after each sweep when `expand`), in FP64
+// or as the FP32 stage of the mixed-precision solve. It runs until the stop
+// rule holds for a sweep or max_iter sweeps ran: FP64, L-inf change <= tol;
+// FP32, max|dR| <= tol_rel * max R.
+//
+// Two drivers run the same kernels:
+//   - host loop: check_every sweeps are launched ahead and one residual is
+//     read; sweeps launched past convergence exit at once on the device.
+//     With time_sweeps each sweep is bracketed by CUDA events.
+//   - CUDA graph: a while node whose body is one iteration (sweep, expansion)
+//     and a one-thread check that advances the device iteration counter; the
+//     kernels find their buffers from that counter. One launch per loop, no
+//     host round trips. The instantiated graph is cached on the graph handle
+//     and rebuilt when any buffer, numbering or parameter it holds changes.
+struct Loop {
+  bool fp32 = false, dynamic = false, expand = false, exact = true;
+  int max_iter = 0;
+  double tol = 0;
+  float tol_rel = 0;
+  SweepArgs a;      // FP64 sweep arguments (per-iteration buffers filled per launch)
+  Sweep32Args a32;  // FP32 sweep arguments
+  int64_t cb[kMaxThr + 2] = {}, cbo[kMaxThr + 2] = {};
+  int nci = 0, nco = 0;
+  int64_t pull_warp_b = 0;
   unsigned long long fthr = ~0ull;
-  if (expanding) {
+  int kernels_per_iter = 0;  // kernels of one iteration (without the graph's check)
+};
+
+int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, bool expand, int max_iter, Loop* L,
+               cudaStream_t s) {
+  const int n = g->n;
+  const Relabel& rl = g->rl;
+  L->fp32 = fp32;
+  L->dynamic = dynamic;
+  L->expand = dynamic && expand;
+  L->exact = p->accumulate == PRDF_ACC_EXACT;
+  L->max_iter = max_iter;
+  L->tol = p->tol;
+  L->tol_rel = (float)p->tol_fp32_rel;
+  L->nci = rl.thr.n + 1;
+  begins_from_counts(rl.count, L->nci, L->cb);
+  L->kernels_per_iter = nonempty_classes(L->cb, L->nci);
+  if (fp32) {
+    PRDF_TRY(g->resid32.reserve(2 * ((size_t)max_iter + 1), s));
+    PRDF_CUDA(cudaMemsetAsync(g->resid32.p, 0, sizeof(uint32_t) * 2 * ((size_t)max_iter + 1), s));
+    Sweep32Args& a = L->a32;
+    memset(&a, 0, sizeof(a));
+    a.off = rl.in.off.p;
+    a.adj = rl.in.adj.p;
+    a.degf = g->degf.p;
+    a.invf = g->invf.p;
+    a.alpha = (float)p->alpha;
+    a.c0 = (float)((1.0 - p->alpha) / (double)n);
+    a.self_loops = g->self_loops ? 1 : 0;
+    a.tol_rel = L->tol_rel;
+    if (dynamic) {
+      a.kf = g->kf32.p;
+      a.dV = g->dV.p;
+      a.dN = g->dN.p;
+      a.wrote = g->wrote.p;
+      a.tau_f = (float)p->tau_f;
+      a.tau_p = (float)p->tau_p;
+      a.prune = p->prune;
+    }
+  } else {
+    PRDF_TRY(g->resid.reserve((size_t)max_iter + 1, s));
+    PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t) * ((size_t)max_iter + 1), s));
+    SweepArgs& a = L->a;
+    memset(&a, 0, sizeof(a));
+    a.off = rl.in.off.p;
+    a.adj = rl.in.adj.p;
+    a.degd = rl.degd.p;
+    a.inv_deg = rl.inv_deg.p;
+    a.kf = rl.kf.p;
+    a.alpha = p->alpha;
+    a.c0 = (1.0 - p->alpha) / (double)n;
+    a.self_loops = g->self_loops ? 1 : 0;
+    a.tol = p->tol;
+    if (dynamic) {
+      a.dV = g->dV.p;
+      a.dN = g->dN.p;
+      a.wrote = g->wrote.p;
+      a.tau_f = p->tau_f;
+      a.tau_p = p->tau_p;
+      a.prune = p->prune;
+    } else {
+      // Static sweeps cut the highest in-degree class's rows into the hub
+      // chunks of G' (exact partial sums per chunk); the table and the partial
+      // buffer are made here, outside any stream capture
+      PRDF_TRY(ensure_hub(g, rl.in, g->hub_in, s));
+      PRDF_TRY(g->sweep_hub_part.reserve((size_t)(g->hub_in.nchunk > 0 ? g->hub_in.nchunk : 1), s));
+      a.hub = g->hub_in.view();
+      a.hub_part = g->sweep_hub_part.p;
+      if (a.hub.nchunk > 0) L->kernels_per_iter += 1;  // the highest class takes two kernels
+    }
+  }
+  if (L->expand) {
+    // pull-form expansion: frontier count, thread rows below the two highest in-degree classes, warp rows above
+    L->nco = g->thr[PRDF_OUT].n + 1;
+    begins_from_counts(rl.pout_count, L->nco, L->cbo);
+    L->pull_warp_b = hub_begin(rl);
     PRDF_TRY(g->fwork.reserve((size_t)max_iter + 1, s));
     PRDF_CUDA(cudaMemsetAsync(g->fwork.p, 0, sizeof(unsigned long long) * ((size_t)max_iter + 1), s));
     const double lim = p->expand_pull * (double)rl.in.m;
-    fthr = lim >= 1.8e19 ? ~0ull : (unsigned long long)lim;
-    kps += 1 + (pull_warp_b > 0 ? 1 : 0) + (n > pull_warp_b ? 1 : 0);
+    L->fthr = lim >= 1.8e19 ? ~0ull : (unsigned long long)lim;
+    L->kernels_per_iter += nonempty_classes(L->cbo, L->nco) + 1 + (L->pull_warp_b > 0 ? 1 : 0) +
+                           (n > L->pull_warp_b ? 1 : 0);
   }
-  SweepArgs a;
-  memset(&a, 0, sizeof(a));
-  a.off = rl.in.off.p;
-  a.adj = rl.in.adj.p;
-  a.degd = rl.degd.p;
-  a.inv_deg = rl.inv_deg.p;
-  a.kf = rl.kf.p;
-  a.alpha = p->alpha;
-  a.c0 = (1.0 - p->alpha) / (double)n;
-  a.self_loops = g->self_loops ? 1 : 0;
-  a.tol = p->tol;
-  a.dV = g->dV.p;
-  a.dN = g->dN.p;
-  a.wrote = g->wrote.p;
-  a.tau_f = p->tau_f;
-  a.tau_p = p->tau_p;
-  a.prune = p->prune;
-  if (!dynamic) {
-    PRDF_TRY(prepare_hub_split(g, a, s));
-    if (a.hub.nchunk > 0) kps += 1;  // the highest class takes two kernels
+  return PRDF_OK;
+}
+
+// The sweep of iteration i (i >= 0: host loop, explicit buffers; i < 0:
+// graph-driven, buffers from the device counter).
+int launch_loop_sweep(prdf_graph* g, const Loop& L, int i, cudaStream_t s) {
+  const Relabel& rl = g->rl;
+  if (L.fp32) {
+    Sweep32Args a = L.a32;
+    if (i >= 0) {
+      a.y = (i & 1) ? g->yb.p : g->ya.p;
+      a.yn = (i & 1) ? g->ya.p : g->yb.p;
+      a.resid = g->resid32.p + 2 * i;
+      a.prev = i > 0 ? g->resid32.p + 2 * (i - 1) : nullptr;
+    } else {
+      a.ctl = g->ctl.p;
+      a.ya = g->ya.p;
+      a.yb = g->yb.p;
+      a.resid_base = g->resid32.p;
+    }
+    return launch_sweep32(a, rl.thr, L.cb, L.dynamic, s);
   }
+  SweepArgs a = L.a;
+  if (i >= 0) {
+    a.x = (i & 1) ? g->xb.p : g->xa.p;
+    a.xn = (i & 1) ? g->xa.p : g->xb.p;
+    a.resid = g->resid.p + i;
+    a.prev = i > 0 ? g->resid.p + i - 1 : nullptr;
+  } else {
+    a.ctl = g->ctl.p;
+    a.xa = g->xa.p;
+    a.xb = g->xb.p;
+    a.resid_base = g->resid.p;
+  }
+  return launch_sweep(a, rl.thr, L.cb, L.exact, L.dynamic, s);
+}
+
+// The expansion round after sweep i (Alg. affected over the frontier deltaN
+// the sweep left), skipped on the device once the loop has converged.
+int launch_loop_expansion(prdf_graph* g, const Loop& L, int i, cudaStream_t s) {
+  if (!L.expand) return PRDF_OK;
+  const Relabel& rl = g->rl;
+  Stop st;
+  if (L.fp32) {
+    st.r32 = g->resid32.p + 2 * (i >= 0 ? i : 0);
+    st.tol_rel = L.tol_rel;
+  } else {
+    st.r64 = g->resid.p + (i >= 0 ? i : 0);
+    st.tol = L.tol;
+  }
+  st.ctl = i >= 0 ? nullptr : g->ctl.p;
+  unsigned long long* fw = g->fwork.p + (i >= 0 ? i : 0);
+  PRDF_TRY(launch_expand_pull(rl.in.off.p, rl.in.adj.p, rl.out.off.p, g->n, L.pull_warp_b, g->dN.p, g->dV.p, fw,
+                              L.fthr, st, s));
+  return launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, L.cbo, L.nco, g->dN.p, g->dV.p, nullptr, st, s, fw,
+                       L.fthr);
+}
+
+// stop rule of sweep i from the residual words read back
+bool loop_stopped(const Loop& L, const void* words, int i, double* delta) {
+  if (L.fp32) {
+    const uint32_t* r = static_cast<const uint32_t*>(words) + 2 * i;
+    float d, m;
+    memcpy(&d, &r[0], 4);
+    memcpy(&m, &r[1], 4);
+    *delta = d;
+    return d <= L.tol_rel * m;
+  }
+  double d;
+  memcpy(&d, static_cast<const uint64_t*>(words) + i, sizeof(double));
+  *delta = d;
+  return d <= L.tol;
+}
+
+int run_host_loop(prdf_graph* g, const Loop& L, const prdf_params* p, IterResult* res, cudaStream_t s) {
+  const int max_iter = L.max_iter;
   const int check = p->check_every > 0 ? p->check_every : 8;
-  const bool exact = p->accumulate == PRDF_ACC_EXACT;
   const bool timed = p->time_sweeps != 0;
+  const size_t wsz = L.fp32 ? 2 * sizeof(uint32_t) : sizeof(uint64_t);
+  const void* resid_dev = L.fp32 ? (const void*)g->resid32.p : (const void*)g->resid.p;
   std::vector<cudaEvent_t> ev;
   struct EvGuard {
     std::vector<cudaEvent_t>& v;
@@ -412,11 +617,6 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
   while (launched < max_iter && !done) {
     const int upto = (launched + check < max_iter) ? launched + check : max_iter;
     for (int i = launched; i < upto; ++i) {
-      a.x = (i & 1) ? g->xb.p : g->xa.p;
-      a.xn = (i & 1) ? g->xa.p : g->xb.p;
-      a.resid = g->resid.p + i;
-      a.prev = i > 0 ? g->resid.p + i - 1 : nullptr;
-      if (expanding) PRDF_CUDA(cudaMemsetAsync(g->dN.p, 0, (size_t)n, s));
       if (timed) {
         cudaEvent_t e0, e1;
         PRDF_CUDA(cudaEventCreate(&e0));
@@ -425,41 +625,35 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
         ev.push_back(e1);
         PRDF_CUDA(cudaEventRecord(e0, s));
       }
-      PRDF_TRY(launch_sweep(a, rl.thr, cb, exact, dynamic, s));
-      if (timed) PRDF_CUDA(cudaEventRecord(ev.back(), s));
-      if (expanding) {
-        PRDF_TRY(launch_expand_pull(rl.in.off.p, rl.in.adj.p, rl.out.off.p, n, pull_warp_b, g->dN.p, g->dV.p,
-                                    g->fwork.p + i, fthr, g->resid.p + i, p->tol, s));
-        PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, nullptr, g->resid.p + i,
-                               p->tol, s, g->fwork.p + i, fthr));
-      }
+      PRDF_TRY(launch_loop_sweep(g, L, i, s));
+      if (timed) PRDF_CUDA(cudaEventRecord(ev.back(), s));  // the sweep alone, not its expansion
+      PRDF_TRY(launch_loop_expansion(g, L, i, s));
     }
     launched = upto;
-    PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid.p + launched - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, (const char*)resid_dev + wsz * (launched - 1), wsz,
+                              cudaMemcpyDeviceToHost, s));
     PRDF_CUDA(cudaStreamSynchronize(s));
-    double last;
-    memcpy(&last, g->ws.host_i64, sizeof(double));
-    done = last <= p->tol;
+    double d;
+    done = loop_stopped(L, g->ws.host_i64, 0, &d);
   }
   std::vector<uint64_t> hr((size_t)launched);
-  PRDF_CUDA(cudaMemcpyAsync(hr.data(), g->resid.p, sizeof(uint64_t) * launched, cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaMemcpyAsync(hr.data(), resid_dev, wsz * launched, cudaMemcpyDeviceToHost, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
   int k = launched - 1;
   res->converged = 0;
   for (int i = 0; i < launched; ++i) {
     double d;
-    memcpy(&d, &hr[i], sizeof(double));
-    if (d <= p->tol) {
+    if (loop_stopped(L, hr.data(), i, &d)) {
       k = i;
       res->converged = 1;
       break;
     }
   }
-  memcpy(&res->final_delta, &hr[k], sizeof(double));
+  loop_stopped(L, hr.data(), k, &res->final_delta);
   res->iters = k + 1;
-  res->final_buf = (k & 1) ? 0 : 1;  // sweep k wrote xb if k is even
+  res->final_buf = (k & 1) ? 0 : 1;  // sweep k wrote the second buffer if k is even
   res->launched = launched;
-  res->kernels = (long long)launched * kps;
+  res->kernels = (long long)launched * L.kernels_per_iter;
   res->ms_sweep = 0;
   if (timed)
     for (int i = 0; i < res->iters; ++i) {
@@ -470,66 +664,112 @@ int iterate(prdf_graph* g, const prdf_params* p, bool dynamic, IterResult* res, 
   return PRDF_OK;
 }
 
-// FP32 stage: sweeps until max|dR| <= tol_fp32_rel * max R or max_iter sweeps.
-// Returns the sweeps run and which y buffer holds the result.
-int iterate32(prdf_graph* g, const prdf_params* p, int* iters, int* final_buf, long long* kernels, cudaStream_t s) {
-  const int max_iter = p->max_iter;
-  PRDF_TRY(g->resid32.reserve(2 * ((size_t)max_iter + 1), s));
-  PRDF_CUDA(cudaMemsetAsync(g->resid32.p, 0, sizeof(uint32_t) * 2 * ((size_t)max_iter + 1), s));
+// The same loop as one CUDA graph (see above).
+int run_graph_loop(prdf_graph* g, const Loop& L, IterResult* res, cudaStream_t s) {
+  PRDF_TRY(g->ctl.reserve(2, s));
+  PRDF_CUDA(cudaMemsetAsync(g->ctl.p, 0, 2 * sizeof(int), s));
+  // what the captured kernels hold: their arguments and the buffers of the graph-driven iteration
+  std::vector<uint64_t> key;
+  auto put = [&key](const void* p, size_t nb) {
+    const size_t at = key.size();
+    key.resize(at + (nb + 7) / 8, 0);
+    memcpy(key.data() + at, p, nb);
+  };
+  auto putv = [&put](uint64_t v) { put(&v, sizeof(v)); };
+  putv(((uint64_t)L.fp32 << 3) | ((uint64_t)L.dynamic << 2) | ((uint64_t)L.expand << 1) | (uint64_t)L.exact);
+  putv((uint64_t)L.max_iter);
+  put(&L.tol, sizeof(L.tol));
+  put(&L.tol_rel, sizeof(L.tol_rel));
+  if (L.fp32) put(&L.a32, sizeof(L.a32));
+  else put(&L.a, sizeof(L.a));
+  put(L.cb, sizeof(L.cb));
+  put(L.cbo, sizeof(L.cbo));
+  putv((uint64_t)L.nci | ((uint64_t)L.nco << 32));
+  putv((uint64_t)L.pull_warp_b);
+  putv(L.fthr);
   const Relabel& rl = g->rl;
-  int64_t cb[kMaxThr + 2];
-  const int nci = rl.thr.n + 1;
-  begins_from_counts(rl.count, nci, cb);
-  Sweep32Args a;
-  memset(&a, 0, sizeof(a));
-  a.off = rl.in.off.p;
-  a.adj = rl.in.adj.p;
-  a.degf = g->degf.p;
-  a.invf = g->invf.p;
-  a.alpha = (float)p->alpha;
-  a.c0 = (float)((1.0 - p->alpha) / (double)g->n);
-  a.self_loops = g->self_loops ? 1 : 0;
-  a.tol_rel = (float)p->tol_fp32_rel;
-  const int check = p->check_every > 0 ? p->check_every : 8;
-  int launched = 0;
-  bool done = false;
-  while (launched < max_iter && !done) {
-    const int upto = (launched + check < max_iter) ? launched + check : max_iter;
-    for (int i = launched; i < upto; ++i) {
-      a.y = (i & 1) ? g->yb.p : g->ya.p;
-      a.yn = (i & 1) ? g->ya.p : g->yb.p;
-      a.resid = g->resid32.p + 2 * i;
-      a.prev = i > 0 ? g->resid32.p + 2 * (i - 1) : nullptr;
-      PRDF_TRY(launch_sweep32(a, rl.thr, cb, s));
+  const void* ptrs[] = {g->ctl.p,     g->xa.p,       g->xb.p,        g->ya.p,       g->yb.p,      g->resid.p,
+                        g->resid32.p, g->fwork.p,    g->dN.p,        g->dV.p,       rl.in.off.p,  rl.in.adj.p,
+                        rl.out.off.p, rl.out.adj.p,  rl.pout.p};
+  put(ptrs, sizeof(ptrs));
+  putv(rl.version);
+  putv((uint64_t)g->n);
+  const int slot = (L.fp32 ? 4 : 0) + (L.dynamic ? 2 : 0) + (L.expand ? 1 : 0);
+  if (!g->loop_exec[slot] || g->loop_key[slot] != key) {
+    if (g->loop_exec[slot]) {
+      cudaGraphExecDestroy(g->loop_exec[slot]);
+      g->loop_exec[slot] = nullptr;
     }
-    launched = upto;
-    PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid32.p + 2 * (launched - 1), 2 * sizeof(uint32_t),
-                              cudaMemcpyDeviceToHost, s));
-    PRDF_CUDA(cudaStreamSynchronize(s));
-    uint32_t hb[2];
-    memcpy(hb, g->ws.host_i64, sizeof(hb));
-    float d, r;
-    memcpy(&d, &hb[0], 4);
-    memcpy(&r, &hb[1], 4);
-    done = d <= (float)p->tol_fp32_rel * r;
+    if (!g->cap_stream) PRDF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    PRDF_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    alignas(cudaGraphNodeParams) unsigned char np_storage[sizeof(cudaGraphNodeParams)];
+    memset(np_storage, 0, sizeof(np_storage));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_storage);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(g->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    int rc = PRDF_OK;
+    if (e == cudaSuccess) {
+      rc = launch_loop_sweep(g, L, -1, g->cap_stream);
+      if (rc == PRDF_OK) rc = launch_loop_expansion(g, L, -1, g->cap_stream);
+      if (rc == PRDF_OK)
+        rc = L.fp32 ? launch_iter_check32(g->ctl.p, g->resid32.p, L.tol_rel, L.max_iter, h, g->cap_stream)
+                    : launch_iter_check(g->ctl.p, g->resid.p, L.tol, L.max_iter, h, g->cap_stream);
+      cudaGraph_t captured = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &captured);
+      if (e == cudaSuccess) e = e2;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && rc == PRDF_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (rc != PRDF_OK) return rc;
+    if (e != cudaSuccess) {
+      set_error("building the iteration graph: %s", cudaGetErrorString(e));
+      return PRDF_ECUDA;
+    }
+    g->loop_exec[slot] = exec;
+    g->loop_key[slot] = key;
   }
-  std::vector<uint32_t> hr(2 * (size_t)launched);
-  PRDF_CUDA(cudaMemcpyAsync(hr.data(), g->resid32.p, sizeof(uint32_t) * 2 * launched, cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaGraphLaunch(g->loop_exec[slot], s));
+  PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
-  int k = launched - 1;
-  for (int i = 0; i < launched; ++i) {
-    float d, r;
-    memcpy(&d, &hr[2 * i], 4);
-    memcpy(&r, &hr[2 * i + 1], 4);
-    if (d <= (float)p->tol_fp32_rel * r) {
-      k = i;
-      break;
-    }
+  int hit = 0;
+  memcpy(&hit, g->ws.host_i64, sizeof(int));
+  if (hit < 1 || hit > L.max_iter) {
+    set_error("iteration graph ran %d sweeps", hit);
+    return PRDF_ECUDA;
   }
-  *iters = k + 1;
-  *final_buf = (k & 1) ? 0 : 1;
-  *kernels = (long long)launched * nonempty_classes(cb, nci);
+  const size_t wsz = L.fp32 ? 2 * sizeof(uint32_t) : sizeof(uint64_t);
+  const char* resid_dev = L.fp32 ? (const char*)g->resid32.p : (const char*)g->resid.p;
+  PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, resid_dev + wsz * (hit - 1), wsz, cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  res->converged = loop_stopped(L, g->ws.host_i64, 0, &res->final_delta) ? 1 : 0;
+  res->iters = hit;
+  const int k = hit - 1;
+  res->final_buf = (k & 1) ? 0 : 1;
+  res->launched = hit;
+  res->kernels = (long long)hit * (L.kernels_per_iter + 1);
+  res->ms_sweep = 0;
   return PRDF_OK;
+}
+
+// One loop with the driver the parameters select: the host loop when every
+// sweep is to be timed (time_sweeps), else the CUDA graph.
+int run_loop(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, bool expand, int max_iter, IterResult* res,
+             cudaStream_t s) {
+  Loop L;
+  PRDF_TRY(loop_setup(g, p, fp32, dynamic, expand, max_iter, &L, s));
+  if (p->time_sweeps) return run_host_loop(g, L, p, res, s);
+  return run_graph_loop(g, L, res, s);
 }
 
 int auto_tile(int K) { return K >= 64 ? 64 : (K >= 32 ? 32 : (K > 8 ? 16 : 8)); }
@@ -728,111 +968,38 @@ int ksolve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, 
   return PRDF_OK;
 }
 
-// Static FP64 loop as one CUDA graph: a while node whose body is one sweep
-// (all classes) and a one-thread check that advances the device iteration
-// counter and stops at L-inf <= tol or max_iter. One launch per solve, no host
-// round trips. The instantiated graph is cached on the graph handle and rebuilt
-// when its buffers, numbering or parameters change.
-int iterate_graph(prdf_graph* g, const prdf_params* p, IterResult* res, cudaStream_t s) {
-  const int max_iter = p->max_iter;
-  const bool exact = p->accumulate == PRDF_ACC_EXACT;
-  PRDF_TRY(g->resid.reserve((size_t)max_iter + 1, s));
-  PRDF_TRY(g->ctl.reserve(2, s));
-  PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t) * ((size_t)max_iter + 1), s));
-  PRDF_CUDA(cudaMemsetAsync(g->ctl.p, 0, 2 * sizeof(int), s));
+// FP32 stage buffers (state, degrees, and for DF-P the Eq. 2 factor)
+int alloc_fp32(prdf_graph* g, bool eq2, cudaStream_t s) {
+  PRDF_TRY(g->ya.reserve(g->n, s));
+  PRDF_TRY(g->yb.reserve(g->n, s));
+  PRDF_TRY(g->degf.reserve(g->n, s));
+  PRDF_TRY(g->invf.reserve(g->n, s));
+  if (eq2) PRDF_TRY(g->kf32.reserve(g->n, s));
+  return PRDF_OK;
+}
+
+// FP32 stage of a dynamic solve (DF / DF-P with expansion, DT without): the
+// affected set and flags are already marked and xa = xb = R^{t-1} / |out|.
+// Runs FP32 sweeps from R^{t-1} to the relative stop, then sets xa = xb to
+// their result (FP64 values kept where the FP32 stage changed nothing),
+// affects every vertex it changed, and clears the copy-through marks, so the
+// FP64 loop continues from there: the affected set the FP32 stage left plus
+// the vertices it moved, whose prune tests the FP64 sweeps then decide.
+int dynamic_fp32_stage(prdf_graph* g, const prdf_params* p, const double* prev_ranks, bool expand, IterResult* it32,
+                       cudaStream_t s) {
+  const int n = g->n;
   const Relabel& rl = g->rl;
-  int64_t cb[kMaxThr + 2];
-  const int nci = rl.thr.n + 1;
-  begins_from_counts(rl.count, nci, cb);
-  SweepArgs hub_args;
-  memset(&hub_args, 0, sizeof(hub_args));
-  PRDF_TRY(prepare_hub_split(g, hub_args, s));
-  uint64_t key[10];
-  key[8] = (uint64_t)(uintptr_t)hub_args.hub_part;
-  key[9] = (uint64_t)(uintptr_t)hub_args.hub.chunk_hub;
-  key[0] = (uint64_t)(uintptr_t)g->xa.p ^ ((uint64_t)(uintptr_t)g->xb.p << 1);
-  key[1] = (uint64_t)(uintptr_t)g->resid.p ^ ((uint64_t)(uintptr_t)g->ctl.p << 1);
-  key[2] = rl.version;
-  memcpy(&key[3], &p->alpha, 8);
-  memcpy(&key[4], &p->tol, 8);
-  key[5] = (uint64_t)max_iter;
-  key[6] = exact ? 1 : 0;
-  key[7] = (uint64_t)(uintptr_t)g->rl.in.adj.p;
-  if (!g->static_exec || memcmp(key, g->static_key, sizeof(key)) != 0) {
-    if (g->static_exec) {
-      cudaGraphExecDestroy(g->static_exec);
-      g->static_exec = nullptr;
-    }
-    if (!g->cap_stream) PRDF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
-    SweepArgs a;
-    memset(&a, 0, sizeof(a));
-    a.off = rl.in.off.p;
-    a.adj = rl.in.adj.p;
-    a.degd = rl.degd.p;
-    a.inv_deg = rl.inv_deg.p;
-    a.alpha = p->alpha;
-    a.c0 = (1.0 - p->alpha) / (double)g->n;
-    a.self_loops = g->self_loops ? 1 : 0;
-    a.tol = p->tol;
-    a.ctl = g->ctl.p;
-    a.xa = g->xa.p;
-    a.xb = g->xb.p;
-    a.resid_base = g->resid.p;
-    a.hub = hub_args.hub;
-    a.hub_part = hub_args.hub_part;
-    cudaGraph_t graph = nullptr;
-    PRDF_CUDA(cudaGraphCreate(&graph, 0));
-    cudaGraphConditionalHandle h;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
-    alignas(cudaGraphNodeParams) unsigned char np_storage[sizeof(cudaGraphNodeParams)];
-    memset(np_storage, 0, sizeof(np_storage));
-    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_storage);
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
-    cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
-    if (e == cudaSuccess)
-      e = cudaStreamBeginCaptureToGraph(g->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    int rc = PRDF_OK;
-    if (e == cudaSuccess) {
-      rc = launch_sweep(a, rl.thr, cb, exact, false, g->cap_stream);
-      if (rc == PRDF_OK) rc = launch_iter_check(g->ctl.p, g->resid.p, p->tol, max_iter, h, g->cap_stream);
-      cudaGraph_t captured = nullptr;
-      cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &captured);
-      if (e == cudaSuccess) e = e2;
-    }
-    cudaGraphExec_t exec = nullptr;
-    if (e == cudaSuccess && rc == PRDF_OK) e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (rc != PRDF_OK) return rc;
-    if (e != cudaSuccess) {
-      set_error("building the iteration graph: %s", cudaGetErrorString(e));
-      return PRDF_ECUDA;
-    }
-    g->static_exec = exec;
-    memcpy(g->static_key, key, sizeof(key));
-  }
-  PRDF_CUDA(cudaGraphLaunch(g->static_exec, s));
-  int hit = 0;
-  PRDF_CUDA(cudaMemcpyAsync(&hit, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  PRDF_CUDA(cudaStreamSynchronize(s));
-  if (hit < 1 || hit > max_iter) {
-    set_error("iteration graph ran %d sweeps", hit);
-    return PRDF_ECUDA;
-  }
-  uint64_t last = 0;
-  PRDF_CUDA(cudaMemcpy(&last, g->resid.p + hit - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost));
-  memcpy(&res->final_delta, &last, sizeof(double));
-  res->iters = hit;
-  res->converged = res->final_delta <= p->tol ? 1 : 0;
-  const int k = hit - 1;
-  res->final_buf = (k & 1) ? 0 : 1;
-  res->launched = hit;
-  res->kernels = (long long)hit * (nonempty_classes(cb, nci) + 1 + (hub_args.hub.nchunk > 0 ? 1 : 0));
-  res->ms_sweep = 0;
+  const bool eq2 = p->prune != 0;
+  PRDF_TRY(alloc_fp32(g, eq2, s));
+  k_init_y<<<grid_for(n, kThreads), kThreads, 0, s>>>(prev_ranks, rl.perm.p, n, rl.degd.p, rl.inv_deg.p,
+                                                     eq2 ? rl.kf.p : nullptr, g->ya.p, g->yb.p, g->degf.p, g->invf.p,
+                                                     eq2 ? g->kf32.p : nullptr);
+  PRDF_LAUNCH_CHECK();
+  PRDF_TRY(run_loop(g, p, true, true, expand, p->max_iter, it32, s));
+  k_widen_keep<<<grid_for(n, kThreads), kThreads, 0, s>>>(it32->final_buf ? g->yb.p : g->ya.p, n, g->xa.p, g->xb.p,
+                                                         g->dV.p);
+  PRDF_LAUNCH_CHECK();
+  PRDF_CUDA(cudaMemsetAsync(g->wrote.p, 0, (size_t)n, s));
   return PRDF_OK;
 }
 
@@ -975,7 +1142,8 @@ void prdf_graph_destroy(prdf_graph* g) {
   if (!g) return;
   cudaStreamSynchronize(g->stream);
   cudaDeviceSynchronize();
-  if (g->static_exec) cudaGraphExecDestroy(g->static_exec);
+  for (auto& e : g->loop_exec)
+    if (e) cudaGraphExecDestroy(e);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   delete g;
 }
@@ -1020,8 +1188,7 @@ int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t*
     return PRDF_ESTATE;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  PRDF_TRY(check_ids(g, del_src, del_dst, n_del, s));
-  PRDF_TRY(check_ids(g, ins_src, ins_dst, n_ins, s));
+  PRDF_TRY(check_inputs(g, del_src, del_dst, n_del, ins_src, ins_dst, n_ins, nullptr, nullptr, s));
   const int32_t n = g->n;
   Csr& old = g->csr[PRDF_OUT];
   const int64_t m = old.m;
@@ -1090,6 +1257,7 @@ int prdf_graph_set_thresholds(prdf_graph* g, int which, int n_thr, const int64_t
   g->thr[which].n = n_thr;
   for (int i = 0; i < kMaxThr; ++i) g->thr[which].thr[i] = i < n_thr ? thr_host[i] : 0;
   g->pvalid[which] = false;
+  if (which == PRDF_OUT) g->rl.pout_valid = false;  // the marking partition follows the out-degree classes
   return PRDF_OK;
 }
 
@@ -1115,8 +1283,7 @@ int prdf_initial_affected(prdf_graph* g, const int32_t* del_src, const int32_t* 
     return PRDF_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  PRDF_TRY(check_ids(g, del_src, del_dst, n_del, s));
-  PRDF_TRY(check_ids(g, ins_src, nullptr, n_ins, s));
+  PRDF_TRY(check_inputs(g, del_src, del_dst, n_del, ins_src, nullptr, n_ins, nullptr, nullptr, s));
   PRDF_TRY(launch_initial_affected(del_src, del_dst, del_mask, n_del, ins_src, ins_mask, n_ins, nullptr, dV, dN, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
   return PRDF_OK;
@@ -1132,7 +1299,7 @@ int prdf_expand_affected(prdf_graph* g, const uint8_t* dN, uint8_t* dV, void* st
   int64_t cb[kMaxThr + 2];
   class_begins(g, PRDF_OUT, cb);
   PRDF_TRY(launch_expand(g->csr[PRDF_OUT].off.p, g->csr[PRDF_OUT].adj.p, g->P[PRDF_OUT].p, cb, g->thr[PRDF_OUT].n + 1,
-                         dN, dV, nullptr, nullptr, 0.0, s));
+                         dN, dV, nullptr, Stop(), s));
   PRDF_CUDA(cudaStreamSynchronize(s));
   return PRDF_OK;
 }
@@ -1144,6 +1311,7 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
   }
   PRDF_TRY(check_params(p));
   cudaStream_t s = (cudaStream_t)p->stream;
+  if (R0) PRDF_TRY(check_inputs(g, nullptr, nullptr, 0, nullptr, nullptr, 0, R0, "R0", s));
   Timer t;
   PRDF_TRY(t.init());
   PRDF_TRY(alloc_solver(g, false, s));
@@ -1157,28 +1325,25 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
   prdf_params p64 = *p;
   if (p->precision == PRDF_FP32_REFINE) {
     // FP32 stage, then FP64 sweeps from its result
-    PRDF_TRY(g->ya.reserve(g->n, s));
-    PRDF_TRY(g->yb.reserve(g->n, s));
-    PRDF_TRY(g->degf.reserve(g->n, s));
-    PRDF_TRY(g->invf.reserve(g->n, s));
+    PRDF_TRY(alloc_fp32(g, false, s));
     k_init_y<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(R0, g->rl.perm.p, g->n, g->rl.degd.p, g->rl.inv_deg.p,
-                                                           g->ya.p, g->degf.p, g->invf.p);
+                                                           nullptr, g->ya.p, nullptr, g->degf.p, g->invf.p, nullptr);
     PRDF_LAUNCH_CHECK();
     PRDF_CUDA(cudaEventRecord(t.e[1], s));
-    int fb32 = 0;
-    PRDF_TRY(iterate32(g, p, &iters32, &fb32, &kernels32, s));
-    k_widen<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(fb32 ? g->yb.p : g->ya.p, g->n, g->xa.p);
+    IterResult it32;
+    PRDF_TRY(run_loop(g, p, true, false, false, p->max_iter, &it32, s));
+    iters32 = it32.iters;
+    k_widen<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(it32.final_buf ? g->yb.p : g->ya.p, g->n, g->xa.p);
     PRDF_LAUNCH_CHECK();
     p64.max_iter = p->max_iter - iters32 > 0 ? p->max_iter - iters32 : 1;
-    kernels32 += 2;
+    kernels32 = it32.kernels + 2;
   } else {
     k_init_x<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(R0, g->rl.perm.p, g->n, g->rl.inv_deg.p, g->xa.p, nullptr);
     PRDF_LAUNCH_CHECK();
     PRDF_CUDA(cudaEventRecord(t.e[1], s));
   }
   IterResult it;
-  if (p64.time_sweeps) PRDF_TRY(iterate(g, &p64, false, &it, s));
-  else PRDF_TRY(iterate_graph(g, &p64, &it, s));
+  PRDF_TRY(run_loop(g, &p64, false, false, false, p64.max_iter, &it, s));
   k_finalize<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, g->rl.degd.p,
                                                            g->rl.perm.p, g->n, ranks, nullptr, nullptr);
   PRDF_LAUNCH_CHECK();
@@ -1213,24 +1378,27 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
   }
   PRDF_TRY(check_params(p));
   cudaStream_t s = (cudaStream_t)p->stream;
-  PRDF_TRY(check_ids(g, del_src, del_dst, n_del, s));
-  PRDF_TRY(check_ids(g, ins_src, nullptr, n_ins, s));
+  PRDF_TRY(check_inputs(g, del_src, del_dst, n_del, ins_src, nullptr, n_ins, prev_ranks, "prev_ranks", s));
   Timer t;
   PRDF_TRY(t.init());
   PRDF_TRY(alloc_solver(g, true, s));
   const int n = g->n;
   PRDF_CUDA(cudaEventRecord(t.e[0], s));
-  // Alg. frontier: R = Rnew = R^{t-1}; partition G and G'; mark; iterate
-  // partitions: G' by in-degree is the sweep numbering; G by out-degree (for marking) per call
-  g->rl.pout_valid = false;
+  // Alg. frontier: R = Rnew = R^{t-1}; partition G and G'; mark; iterate.
+  // The partitions are kept with the graph: G' by in-degree is the sweep
+  // numbering, G by out-degree (for marking) is made with it and stays valid
+  // until the graph or the thresholds change.
+  const bool pout_made = !g->rl.pout_valid;
   PRDF_TRY(ensure_relabelled(g, true, s));
   Relabel& rl = g->rl;
+  bool kf_made = false;
   if (p->prune && rl.kf_alpha != p->alpha) {
     // Eq. 2's per-vertex factor, kept until the numbering or alpha changes
     PRDF_TRY(rl.kf.reserve((size_t)n, s));
     k_eq2_factor<<<grid_for(n, kThreads), kThreads, 0, s>>>(rl.degd.p, n, p->alpha, rl.kf.p);
     PRDF_LAUNCH_CHECK();
     rl.kf_alpha = p->alpha;
+    kf_made = true;
   }
   k_init_x<<<grid_for(n, kThreads), kThreads, 0, s>>>(prev_ranks, rl.perm.p, n, rl.inv_deg.p, g->xa.p, g->xb.p);
   PRDF_LAUNCH_CHECK();
@@ -1243,12 +1411,21 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
   int64_t cbo[kMaxThr + 2];
   begins_from_counts(rl.pout_count, g->thr[PRDF_OUT].n + 1, cbo);
   PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, g->thr[PRDF_OUT].n + 1, g->dN.p, g->dV.p,
-                         nullptr, nullptr, 0.0, s));
+                         nullptr, Stop(), s));
   PRDF_TRY(count_flags(g->dV.p, n, g->counter.p, s));
   PRDF_CUDA(cudaEventRecord(t.e[2], s));
   PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64 + 8, g->counter.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  IterResult it;
-  PRDF_TRY(iterate(g, p, true, &it, s));  // synchronises the stream
+  IterResult it, it32;
+  prdf_params p64 = *p;
+  long long kernels32 = 0;
+  if (p->precision == PRDF_FP32_REFINE) {
+    // FP32 DF-P sweeps to the relative stop, then FP64 DF-P sweeps from their
+    // result with the affected set they leave
+    PRDF_TRY(dynamic_fp32_stage(g, p, prev_ranks, true, &it32, s));
+    p64.max_iter = p->max_iter - it32.iters > 0 ? p->max_iter - it32.iters : 1;
+    kernels32 = it32.kernels + 3;
+  }
+  PRDF_TRY(run_loop(g, &p64, false, true, true, p64.max_iter, &it, s));  // synchronises the stream
   const long long aff0 = (long long)g->ws.host_i64[8];
   k_finalize<<<grid_for(n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, rl.degd.p, rl.perm.p, n,
                                                        ranks, g->dV.p, dV_out);
@@ -1258,20 +1435,21 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
   PRDF_CUDA(cudaStreamSynchronize(s));
   if (stats) {
     memset(stats, 0, sizeof(*stats));
-    stats->iterations = it.iters;
+    stats->iterations = it.iters + it32.iters;
+    stats->iterations_fp32 = it32.iters;
     stats->converged = it.converged;
     stats->final_delta = it.final_delta;
-    stats->sweeps_launched = it.launched;
+    stats->sweeps_launched = it.launched + it32.launched;
     cudaEventElapsedTime(&stats->ms_total, t.e[0], t.e[3]);
     cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
     cudaEventElapsedTime(&stats->ms_mark, t.e[1], t.e[2]);
     cudaEventElapsedTime(&stats->ms_iterate, t.e[2], t.e[3]);
-    stats->ms_sweep = it.ms_sweep;
+    stats->ms_sweep = it.ms_sweep + it32.ms_sweep;
     stats->edges_processed = -1;
     stats->affected_initial = aff0;
-    // out-degree partition + init + initial marking + expand + count + sweeps/expands + finalize
-    stats->kernel_launches = 5 + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, g->thr[PRDF_OUT].n + 1) + 1 +
-                             it.kernels + 1;
+    // (out-degree partition) + init (+ Eq. 2 factor) + initial marking + expand + count + sweeps/expands + finalize
+    stats->kernel_launches = (pout_made ? 5 : 0) + 1 + (kf_made ? 1 : 0) + (n_del + n_ins > 0 ? 1 : 0) +
+                             nonempty_classes(cbo, g->thr[PRDF_OUT].n + 1) + 1 + kernels32 + it.kernels + 1;
   }
   return PRDF_OK;
 }
@@ -1287,16 +1465,15 @@ int prdf_pagerank_dt(prdf_graph* g, const int32_t* del_src, const int32_t* del_d
   }
   PRDF_TRY(check_params(p));
   cudaStream_t s = (cudaStream_t)p->stream;
-  PRDF_TRY(check_ids(g, del_src, del_dst, n_del, s));
-  PRDF_TRY(check_ids(g, ins_src, nullptr, n_ins, s));
+  PRDF_TRY(check_inputs(g, del_src, del_dst, n_del, ins_src, nullptr, n_ins, prev_ranks, "prev_ranks", s));
   Timer t;
   PRDF_TRY(t.init());
   PRDF_TRY(alloc_solver(g, true, s));
   const int n = g->n;
   PRDF_TRY(g->dF.reserve(n, s));
   PRDF_CUDA(cudaEventRecord(t.e[0], s));
-  // Alg. traversal: R = Rnew = R^{t-1}; partition G and G'; mark; close; iterate
-  g->rl.pout_valid = false;
+  // Alg. traversal: R = Rnew = R^{t-1}; partitions (kept with the graph); mark; close; iterate
+  const bool pout_made = !g->rl.pout_valid;
   PRDF_TRY(ensure_relabelled(g, true, s));
   const Relabel& rl = g->rl;
   k_init_x<<<grid_for(n, kThreads), kThreads, 0, s>>>(prev_ranks, rl.perm.p, n, rl.inv_deg.p, g->xa.p, g->xb.p);
@@ -1310,17 +1487,17 @@ int prdf_pagerank_dt(prdf_graph* g, const int32_t* del_src, const int32_t* del_d
   const int nco = g->thr[PRDF_OUT].n + 1;
   int64_t cbo[kMaxThr + 2];
   begins_from_counts(rl.pout_count, nco, cbo);
-  PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, nullptr, nullptr, 0.0, s));
+  PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, nullptr, Stop(), s));
   // reachability closure over G^t: the frontier starts as every affected vertex; each
   // round marks the vertices it reaches that were not yet affected, which form the
   // next frontier, until a round adds none (the affected count stops changing)
-  long long kernels = 5 + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, nco);
+  long long kernels = (pout_made ? 5 : 0) + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, nco);
   PRDF_CUDA(cudaMemcpyAsync(g->dN.p, g->dV.p, (size_t)n, cudaMemcpyDeviceToDevice, s));
   uint8_t* front = g->dN.p;
   uint8_t* next = g->dF.p;
   for (int round = 0; round < n; ++round) {
     PRDF_CUDA(cudaMemsetAsync(next, 0, (size_t)n, s));
-    PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, front, g->dV.p, next, nullptr, 0.0, s));
+    PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, front, g->dV.p, next, Stop(), s));
     PRDF_TRY(count_flags(next, n, g->counter.p, s));
     kernels += nonempty_classes(cbo, nco) + 1;
     unsigned long long added = 0;
@@ -1334,12 +1511,17 @@ int prdf_pagerank_dt(prdf_graph* g, const int32_t* del_src, const int32_t* del_d
   PRDF_TRY(count_flags(g->dV.p, n, g->counter.p, s));
   PRDF_CUDA(cudaEventRecord(t.e[2], s));
   PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64 + 8, g->counter.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  // Eq. 1 on the affected vertices, no prune and no expansion
+  // Eq. 1 on the affected vertices, no prune and no expansion (FP32 stage first in mixed precision)
   prdf_params q = *p;
   q.prune = 0;
   q.tau_f = INFINITY;
-  IterResult it;
-  PRDF_TRY(iterate(g, &q, true, &it, s, false));  // synchronises the stream
+  IterResult it, it32;
+  if (p->precision == PRDF_FP32_REFINE) {
+    PRDF_TRY(dynamic_fp32_stage(g, &q, prev_ranks, false, &it32, s));
+    q.max_iter = p->max_iter - it32.iters > 0 ? p->max_iter - it32.iters : 1;
+    kernels += it32.kernels + 3;
+  }
+  PRDF_TRY(run_loop(g, &q, false, true, false, q.max_iter, &it, s));  // synchronises the stream
   const long long aff = (long long)g->ws.host_i64[8];
   k_finalize<<<grid_for(n, kThreads), kThreads, 0, s>>>(it.final_buf ? g->xb.p : g->xa.p, rl.degd.p, rl.perm.p, n,
                                                        ranks, g->dV.p, dV_out);
@@ -1348,15 +1530,16 @@ int prdf_pagerank_dt(prdf_graph* g, const int32_t* del_src, const int32_t* del_d
   PRDF_CUDA(cudaEventSynchronize(t.e[3]));
   if (stats) {
     memset(stats, 0, sizeof(*stats));
-    stats->iterations = it.iters;
+    stats->iterations = it.iters + it32.iters;
+    stats->iterations_fp32 = it32.iters;
     stats->converged = it.converged;
     stats->final_delta = it.final_delta;
-    stats->sweeps_launched = it.launched;
+    stats->sweeps_launched = it.launched + it32.launched;
     cudaEventElapsedTime(&stats->ms_total, t.e[0], t.e[3]);
     cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
     cudaEventElapsedTime(&stats->ms_mark, t.e[1], t.e[2]);
     cudaEventElapsedTime(&stats->ms_iterate, t.e[2], t.e[3]);
-    stats->ms_sweep = it.ms_sweep;
+    stats->ms_sweep = it.ms_sweep + it32.ms_sweep;
     stats->edges_processed = -1;
     stats->affected_initial = aff;
     stats->kernel_launches = kernels + 1 + it.kernels + 1;

@@ -36,7 +36,21 @@ __global__ void k_initial_affected(const int32_t* __restrict__ del_src, const in
   }
 }
 
-__device__ __forceinline__ bool converged(const uint64_t* r, double tol) { return r && bitsd(*r) <= tol; }
+// The sweep this round follows already met its loop's stop rule: the round does nothing.
+__device__ __forceinline__ bool converged(const Stop& st) {
+  const int it = st.ctl ? st.ctl[0] : 0;
+  if (st.r64) return bitsd(st.r64[it]) <= st.tol;
+  if (st.r32) {
+    const uint32_t* r = st.r32 + 2 * it;
+    return __uint_as_float(r[0]) <= st.tol_rel * __uint_as_float(r[1]);
+  }
+  return false;
+}
+
+// this round's frontier out-edge counter (one per sweep; the graph-driven loop indexes it by ctl[0])
+__device__ __forceinline__ const unsigned long long* round_fw(const unsigned long long* fw, const Stop& st) {
+  return fw ? fw + (st.ctl ? st.ctl[0] : 0) : nullptr;
+}
 
 // Direction of one expansion round, chosen on the device: the pull form when
 // the frontier's out-edges (*fw) exceed fthr, else the push form.
@@ -46,8 +60,9 @@ __device__ __forceinline__ bool pull_chosen(const unsigned long long* fw, unsign
 
 // out-edges of the frontier: sum of |out(u)| over u with dN[u] set
 __global__ void k_frontier_edges(const uint8_t* __restrict__ dN, const int64_t* __restrict__ off, int64_t n,
-                                 unsigned long long* __restrict__ fw, const uint64_t* resid, double tol) {
-  if (converged(resid, tol)) return;
+                                 unsigned long long* fw_base, const Stop st) {
+  if (converged(st)) return;
+  unsigned long long* fw = const_cast<unsigned long long*>(round_fw(fw_base, st));
   int64_t c = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (dN[i]) c += off[i + 1] - off[i];
@@ -64,8 +79,8 @@ __global__ void __launch_bounds__(kThreads) k_pull_thread(const int64_t* __restr
                                                           const int32_t* __restrict__ adj, int64_t begin, int64_t end,
                                                           const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
                                                           const unsigned long long* fw, unsigned long long fthr,
-                                                          const uint64_t* resid, double tol) {
-  if (converged(resid, tol) || !pull_chosen(fw, fthr)) return;
+                                                          const Stop st) {
+  if (converged(st) || !pull_chosen(round_fw(fw, st), fthr)) return;
   for (int64_t w = begin + blockIdx.x * (int64_t)kThreads + threadIdx.x; w < end; w += (int64_t)gridDim.x * kThreads) {
     if (dV[w]) continue;
     const int64_t e = off[w + 1];
@@ -81,8 +96,8 @@ __global__ void __launch_bounds__(kThreads) k_pull_warp(const int64_t* __restric
                                                         const int32_t* __restrict__ adj, int64_t begin, int64_t end,
                                                         const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
                                                         const unsigned long long* fw, unsigned long long fthr,
-                                                        const uint64_t* resid, double tol) {
-  if (converged(resid, tol) || !pull_chosen(fw, fthr)) return;
+                                                        const Stop st) {
+  if (converged(st) || !pull_chosen(round_fw(fw, st), fthr)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
@@ -131,9 +146,9 @@ __global__ void __launch_bounds__(kThreads) k_expand_group(const int64_t* __rest
                                                            const int32_t* __restrict__ adj,
                                                            const int32_t* __restrict__ P, int64_t begin, int64_t end,
                                                            const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
-                                                           uint8_t* __restrict__ dF, const uint64_t* resid, double tol,
+                                                           uint8_t* __restrict__ dF, const Stop st,
                                                            const unsigned long long* fw, unsigned long long fthr) {
-  if (converged(resid, tol) || pull_chosen(fw, fthr)) return;
+  if (converged(st) || pull_chosen(round_fw(fw, st), fthr)) return;
   const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
   const int64_t gid = (blockIdx.x * (int64_t)kThreads + threadIdx.x) / G;
   const int64_t ng = ((int64_t)gridDim.x * kThreads) / G;
@@ -150,9 +165,9 @@ __global__ void __launch_bounds__(kThreads) k_expand_block(const int64_t* __rest
                                                            const int32_t* __restrict__ adj,
                                                            const int32_t* __restrict__ P, int64_t begin, int64_t end,
                                                            const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
-                                                           uint8_t* __restrict__ dF, const uint64_t* resid, double tol,
+                                                           uint8_t* __restrict__ dF, const Stop st,
                                                            const unsigned long long* fw, unsigned long long fthr) {
-  if (converged(resid, tol) || pull_chosen(fw, fthr)) return;
+  if (converged(st) || pull_chosen(round_fw(fw, st), fthr)) return;
   const int64_t S = gridDim.y, y = blockIdx.y;
   for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
     const int32_t u = P[i];
@@ -186,7 +201,7 @@ int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, cons
 }
 
 int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, const int64_t* cb, int nclass,
-                  const uint8_t* dN, uint8_t* dV, uint8_t* dF, const uint64_t* resid, double tol, cudaStream_t s,
+                  const uint8_t* dN, uint8_t* dV, uint8_t* dF, const Stop& st, cudaStream_t s,
                   const unsigned long long* fw, unsigned long long fthr) {
   const int maxg = kSMs * 8;
   for (int c = 0; c < nclass; ++c) {
@@ -195,12 +210,12 @@ int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, cons
     const int64_t cnt = e - b;
     const int kind = (nclass == 4) ? c : (c == nclass - 1 ? 3 : c);
     switch (kind) {
-      case 0: k_expand_group<1><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol, fw, fthr); break;
-      case 1: k_expand_group<8><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol, fw, fthr); break;
-      case 2: k_expand_group<32><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol, fw, fthr); break;
+      case 0: k_expand_group<1><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr); break;
+      case 1: k_expand_group<8><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr); break;
+      case 2: k_expand_group<32><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr); break;
       default: {
         const dim3 grid(grid_for(cnt, 1, maxg / kExpandSlices), kExpandSlices);
-        k_expand_block<<<grid, kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, resid, tol, fw, fthr);
+        k_expand_block<<<grid, kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr);
         break;
       }
     }
@@ -211,15 +226,15 @@ int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, cons
 
 int launch_expand_pull(const int64_t* in_off, const int32_t* in_adj, const int64_t* out_off, int64_t n,
                        int64_t warp_begin, const uint8_t* dN, uint8_t* dV, unsigned long long* fw,
-                       unsigned long long fthr, const uint64_t* resid, double tol, cudaStream_t s) {
+                       unsigned long long fthr, const Stop& st, cudaStream_t s) {
   const int maxg = kSMs * 8;
-  k_frontier_edges<<<grid_for(n, kThreads, kSMs * 4), kThreads, 0, s>>>(dN, out_off, n, fw, resid, tol);
+  k_frontier_edges<<<grid_for(n, kThreads, kSMs * 4), kThreads, 0, s>>>(dN, out_off, n, fw, st);
   if (warp_begin > 0)
     k_pull_thread<<<grid_for(warp_begin, kThreads, maxg), kThreads, 0, s>>>(in_off, in_adj, 0, warp_begin, dN, dV, fw,
-                                                                            fthr, resid, tol);
+                                                                            fthr, st);
   if (n > warp_begin)
     k_pull_warp<<<grid_for((n - warp_begin) * 32, kThreads, maxg), kThreads, 0, s>>>(in_off, in_adj, warp_begin, n,
-                                                                                      dN, dV, fw, fthr, resid, tol);
+                                                                                      dN, dV, fw, fthr, st);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }

@@ -1,6 +1,8 @@
 // Internal declarations shared by the translation units of libprdf.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace prdf {
@@ -121,7 +123,9 @@ struct SweepArgs {
   uint4* hub_part;
 };
 
-// FP32 stage of the mixed-precision Static sweep (sweep32.cu).
+// FP32 stage of the mixed-precision sweeps (sweep32.cu): Static (Eq. 1 on
+// every vertex) or DF / DF-P (Eq. 1 / Eq. 2 on the affected vertices, with
+// the prune and expand flags of Alg. update).
 struct Sweep32Args {
   const int64_t* off;      // in-CSR offsets of G' (class-contiguous numbering)
   const int32_t* adj;      // in-CSR sources
@@ -134,8 +138,25 @@ struct Sweep32Args {
   uint32_t* resid;         // [0]: max |r - R[v]|, [1]: max r of this sweep (FP32 bits, atomic max)
   const uint32_t* prev;    // previous sweep's pair, or null
   float tol_rel;           // the sweep exits at once if prev[0] <= tol_rel * prev[1]
+  // device-driven iteration (CUDA graph): when ctl is set the kernel takes
+  // y/yn/resid/prev for iteration it = ctl[0] from ya/yb/resid_base instead
+  const int* ctl;
+  const float* ya;
+  float* yb;
+  uint32_t* resid_base;
+  // DF / DF-P only (same meaning as in SweepArgs)
+  const float* kf;         // Eq. 2 factor 1 / (1 - alpha / |out(v)|) as float
+  uint8_t* dV;
+  uint8_t* dN;
+  uint8_t* wrote;
+  float tau_f, tau_p;
+  int prune;
 };
-int launch_sweep32(const Sweep32Args& a, const PartThr& t, const int64_t* class_begin, cudaStream_t s);
+int launch_sweep32(const Sweep32Args& a, const PartThr& t, const int64_t* class_begin, bool dynamic, cudaStream_t s);
+// One-thread check of the graph-driven FP32 loop: it = ctl[0]; stop when
+// r32[2 it] <= tol_rel * r32[2 it + 1] or it + 1 >= max_iter; ctl[0] = it + 1.
+int launch_iter_check32(int* ctl, const uint32_t* resid_base, float tol_rel, int max_iter,
+                        cudaGraphConditionalHandle h, cudaStream_t s);
 
 // K-column personalised PageRank (ppr.cu), row-major [n, K] in the class-contiguous numbering.
 struct Ppr32Args {
@@ -200,23 +221,37 @@ int launch_iter_check(int* ctl, const uint64_t* resid_base, double tol, int max_
 int launch_sweep(const SweepArgs& a, const PartThr& t, const int64_t* class_begin, bool exact, bool dynamic,
                  cudaStream_t s);
 
+// Stop rule of the loop an expansion round belongs to, read on the device so
+// that rounds launched after the converged sweep do nothing. FP64 loops:
+// r64[it] <= tol; FP32 stage: r32[2 it] <= tol_rel * r32[2 it + 1]; neither
+// set: the round always runs. it = ctl[0] in the graph-driven loop, else 0
+// (r64 / r32 then point at this sweep's slot).
+struct Stop {
+  const uint64_t* r64 = nullptr;
+  double tol = 0;
+  const uint32_t* r32 = nullptr;
+  float tol_rel = 0;
+  const int* ctl = nullptr;
+};
+
 // Alg. affected kernels (frontier.cu). map (nullable): vertex id -> flag index.
 int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, const uint8_t* del_mask, int64_t n_del,
                             const int32_t* ins_src, const uint8_t* ins_mask, int64_t n_ins, const int32_t* map,
                             uint8_t* dV, uint8_t* dN, cudaStream_t s);
-// expandAffected over the out-degree partition; skipped on the device when *resid <= tol,
-// and when fw (nullable) is given, also when *fw > fthr (the pull form runs instead).
-// dF (nullable): also mark in dF every vertex that was not yet in dV (one
-// round of Dynamic Traversal's reachability closure).
+// expandAffected over the out-degree partition; skipped on the device when the
+// stop rule st holds, and when fw (nullable; this round's counter, indexed by
+// st.ctl in the graph-driven loop) is given, also when *fw > fthr (the pull
+// form runs instead). dF (nullable): also mark in dF every vertex that was not
+// yet in dV (one round of Dynamic Traversal's reachability closure).
 int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, const int64_t* cb, int nclass,
-                  const uint8_t* dN, uint8_t* dV, uint8_t* dF, const uint64_t* resid, double tol, cudaStream_t s,
+                  const uint8_t* dN, uint8_t* dV, uint8_t* dF, const Stop& st, cudaStream_t s,
                   const unsigned long long* fw = nullptr, unsigned long long fthr = 0);
 // The same round in pull form over G' (in_off/in_adj; rows from warp_begin on
 // take a warp each): first sums the frontier's out-edges into *fw (zero on
 // entry; out_off is G's offsets), then marks only if *fw > fthr.
 int launch_expand_pull(const int64_t* in_off, const int32_t* in_adj, const int64_t* out_off, int64_t n,
                        int64_t warp_begin, const uint8_t* dN, uint8_t* dV, unsigned long long* fw,
-                       unsigned long long fthr, const uint64_t* resid, double tol, cudaStream_t s);
+                       unsigned long long fthr, const Stop& st, cudaStream_t s);
 int count_flags(const uint8_t* f, int64_t n, unsigned long long* dev_out, cudaStream_t s);
 
 }  // namespace prdf
@@ -242,16 +277,21 @@ struct prdf_graph {
   prdf::DBuf<float2> ppr_part;        // chunk partial sums of one column tile (FP32 sweeps)
   prdf::DBuf<double> ppr_part64;      // chunk partial sums of one column tile (FP64 steps)
   prdf::DBuf<float> ya, yb, degf, invf;  // FP32 stage state and degrees (class-contiguous numbering)
+  prdf::DBuf<float> kf32;                // FP32 stage of DF-P: Eq. 2 factor
   prdf::DBuf<uint32_t> resid32;
   prdf::DBuf<uint64_t> resid;
   prdf::DBuf<uint8_t> dV, dN, wrote;
   prdf::DBuf<uint8_t> dF;  // Dynamic Traversal: next frontier of the closure
   prdf::DBuf<unsigned long long> counter;
+  prdf::DBuf<unsigned long long> chk;  // input checks: bad-id flag, bad-rank flag, rank sum (double bits)
   prdf::DBuf<unsigned long long> fwork;  // frontier out-edges of each expansion round
   prdf::DBuf<int> ctl;               // device iteration counter of the graph-driven loop
   cudaStream_t cap_stream = nullptr; // private stream used to capture graph bodies
-  cudaGraphExec_t static_exec = nullptr;
-  uint64_t static_key[10] = {};       // what static_exec was built for
+  // instantiated sweep loops (CUDA graphs), one per kind of loop: FP32 stage,
+  // dynamic, expanding (index fp32 * 4 + dynamic * 2 + expand), each with the
+  // arguments and buffers it was captured for
+  cudaGraphExec_t loop_exec[8] = {};
+  std::vector<uint64_t> loop_key[8];
   prdf::Relabel rl;                  // class-contiguous copy used by the sweeps
   // weighted graphs: transition probabilities P_uv = w_uv / sum_k w_uk
   bool ppr_valid = false;

@@ -219,7 +219,9 @@ __device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v,
     const double rold = xself * d;
     const double m = fmax(r, rold);
     if (a.prune && dr <= a.tau_p * m) a.dV[v] = 0;
+    // deltaN holds exactly this sweep's expand set: set or cleared for every vertex
     if (dr > a.tau_f * m) a.dN[v] = 1;
+    else if (a.dN[v]) a.dN[v] = 0;
     a.wrote[v] = 1;
   }
   a.xn[v] = r * ld_stream_f64(a.inv_deg + v, pf);
@@ -247,13 +249,16 @@ __global__ void k_iter_check(int* ctl, const uint64_t* resid_base, double tol, i
 }
 
 // DF / DF-P: an unaffected vertex keeps its rank; its slot in xn is stale
-// only if the previous sweep wrote it (then copy it through).
+// only if the previous sweep wrote it (then copy it through). It is not in
+// this sweep's expand set, so its deltaN flag is cleared (the sweep keeps
+// deltaN exact without a separate clearing pass).
 __device__ __forceinline__ bool skip_unaffected(const SweepArgs& a, int32_t v) {
   if (a.dV[v]) return false;
   if (a.wrote[v]) {
     a.xn[v] = a.x[v];
     a.wrote[v] = 0;
   }
+  if (a.dN[v]) a.dN[v] = 0;
   return true;
 }
 

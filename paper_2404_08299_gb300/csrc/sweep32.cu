@@ -1,10 +1,13 @@
-// FP32 stage of the mixed-precision Static PageRank (an extension of the
-// paper's Alg. static / Eq. 1): rank state y = R / |out| stored in FP32, so a
-// sweep gathers 4 bytes per in-edge, and in-neighbour sums accumulated with
-// compensated summation (Kahan-Babuska: TwoSum of every term, errors summed
-// separately) on the FP32 pipes. Each sweep reports max |r - R[v]| and
-// max r as FP32 bit patterns; the host stops the stage when
-// max|dR| <= tol_fp32_rel * max R and continues in FP64 (api.cu).
+// FP32 stage of the mixed-precision PageRank (an extension of the paper's
+// Alg. static / Alg. frontier with Eq. 1 and Eq. 2): rank state y = R / |out|
+// stored in FP32, so a sweep gathers 4 bytes per in-edge, and in-neighbour
+// sums accumulated with compensated summation (Kahan-Babuska: TwoSum of every
+// term, errors summed separately) on the FP32 pipes. Each sweep reports
+// max |r - R[v]| and max r over the vertices it updates as FP32 bit
+// patterns; the stage stops when max|dR| <= tol_fp32_rel * max R and the
+// solve continues in FP64 (api.cu). The DF / DF-P form updates only the
+// affected vertices, with Alg. update's prune and expand tests evaluated in
+// FP32, and copies the others through, as the FP64 sweep does.
 // Same class-contiguous numbering and kernel shapes as the FP64 sweep.
 #include "internal.cuh"
 
@@ -119,21 +122,68 @@ __device__ __forceinline__ void gather32_vec(const Sweep32Args& a, int64_t b, in
   }
 }
 
-// Eq. 1 in FP32; returns |r - R[v]| and r (both non-negative) as bit patterns
+// Eq. 1 (Static, DF) or Eq. 2 (DF-P) in FP32, with Alg. update's prune and
+// expand tests for DF / DF-P; returns |r - R[v]| and r (both non-negative) as
+// bit patterns
+template <bool DYN>
 __device__ __forceinline__ void finish32(const Sweep32Args& a, int32_t v, float c, uint32_t yself_b, uint64_t pf,
                                         uint32_t& db, uint32_t& rb) {
   const float d = ld_stream_f32(a.degf + v, pf);
-  const float rold = __uint_as_float(yself_b) * d;
-  const float r = fmaf(a.alpha, c, a.c0);
+  const float yself = __uint_as_float(yself_b);
+  const float rold = yself * d;
+  float r;
+  if (DYN && a.prune) r = ld_stream_f32(a.kf + v, pf) * fmaf(a.alpha, c - yself, a.c0);  // Eq. 2
+  else r = fmaf(a.alpha, c, a.c0);                                                        // Eq. 1
+  const float dr = fabsf(r - rold);
+  if (DYN) {
+    const float m = fmaxf(r, rold);
+    if (a.prune && dr <= a.tau_p * m) a.dV[v] = 0;
+    if (dr > a.tau_f * m) a.dN[v] = 1;
+    else if (a.dN[v]) a.dN[v] = 0;
+    a.wrote[v] = 1;
+  }
   a.yn[v] = r * ld_stream_f32(a.invf + v, pf);
-  db = __float_as_uint(fabsf(r - rold));
+  db = __float_as_uint(dr);
   rb = __float_as_uint(r);
+}
+
+// DF / DF-P: an unaffected vertex keeps its rank (copied through when the
+// previous sweep wrote its slot of yn) and leaves this sweep's expand set
+__device__ __forceinline__ bool skip_unaffected32(const Sweep32Args& a, int32_t v) {
+  if (a.dV[v]) return false;
+  if (a.wrote[v]) {
+    a.yn[v] = a.y[v];
+    a.wrote[v] = 0;
+  }
+  if (a.dN[v]) a.dN[v] = 0;
+  return true;
+}
+
+// per-iteration pointers of the graph-driven loop
+__device__ __forceinline__ Sweep32Args resolve32(const Sweep32Args& in) {
+  if (!in.ctl) return in;
+  Sweep32Args a = in;
+  const int it = in.ctl[0];
+  a.y = (it & 1) ? in.yb : in.ya;
+  a.yn = (it & 1) ? const_cast<float*>(in.ya) : in.yb;
+  a.resid = in.resid_base + 2 * it;
+  a.prev = it > 0 ? in.resid_base + 2 * (it - 1) : nullptr;
+  return a;
 }
 
 __device__ __forceinline__ bool converged32(const Sweep32Args& a) {
   if (!a.prev) return false;
   const float d = __uint_as_float(a.prev[0]), rm = __uint_as_float(a.prev[1]);
   return d <= a.tol_rel * rm;
+}
+
+__global__ void k_iter_check32(int* ctl, const uint32_t* resid_base, float tol_rel, int max_iter,
+                               cudaGraphConditionalHandle h) {
+  const int it = ctl[0];
+  const uint32_t* r = resid_base + 2 * it;
+  const bool done = __uint_as_float(r[0]) <= tol_rel * __uint_as_float(r[1]) || it + 1 >= max_iter;
+  ctl[0] = it + 1;
+  cudaGraphSetConditional(h, done ? 0u : 1u);
 }
 
 __device__ __forceinline__ void block_max2_to(uint32_t dmax, uint32_t rmax, uint32_t* out) {
@@ -164,8 +214,9 @@ __device__ __forceinline__ void block_max2_to(uint32_t dmax, uint32_t rmax, uint
   }
 }
 
-template <int G, int U, bool SELF1>
-__global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a, int64_t begin, int64_t end) {
+template <int G, int U, bool SELF1, bool DYN>
+__global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a_in, int64_t begin, int64_t end) {
+  const Sweep32Args a = resolve32(a_in);
   if (converged32(a)) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
   constexpr int kGroupsPerWarp = 32 / G;
@@ -176,8 +227,11 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a,
   uint32_t dmax = 0, rmax = 0;
   for (int64_t base = begin + warp * kGroupsPerWarp; base < end; base += nwarps * kGroupsPerWarp) {
     const int64_t i = base + gw;
-    const bool active = i < end;
+    bool active = i < end;
     const int32_t v = (int32_t)i;
+    // every lane of the group reads the flag before the group's shuffles, and
+    // only the group's lane 0 changes it (in finish32, after them)
+    if (DYN && active && skip_unaffected32(a, v)) active = false;
     Kahan acc;
     uint32_t yself = 0;
     if (active) {
@@ -196,7 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a,
     }
     if (active && lane == 0) {
       uint32_t db, rb;
-      finish32(a, v, acc.value(), yself, pf, db, rb);
+      finish32<DYN>(a, v, acc.value(), yself, pf, db, rb);
       dmax = max(dmax, db);
       rmax = max(rmax, rb);
     }
@@ -204,8 +258,9 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a,
   block_max2_to(dmax, rmax, a.resid);
 }
 
-template <int KV>
-__global__ void __launch_bounds__(kThreads) k_sweep32_warp(const Sweep32Args a, int64_t begin, int64_t end) {
+template <int KV, bool DYN>
+__global__ void __launch_bounds__(kThreads) k_sweep32_warp(const Sweep32Args a_in, int64_t begin, int64_t end) {
+  const Sweep32Args a = resolve32(a_in);
   if (converged32(a)) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
   const int lane = threadIdx.x & 31;
@@ -214,6 +269,11 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_warp(const Sweep32Args a, 
   uint32_t dmax = 0, rmax = 0;
   for (int64_t i = begin + warp; i < end; i += nwarps) {
     const int32_t v = (int32_t)i;
+    // the flag is the same for the whole warp; lane 0 alone changes it, after the shuffles below
+    if (DYN && skip_unaffected32(a, v)) {
+      __syncwarp();
+      continue;
+    }
     const int64_t b = ld_stream_i64(a.off + v, pf), e = ld_stream_i64(a.off + v + 1, pf);
     Kahan acc;
     uint32_t yself = 0;
@@ -223,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_warp(const Sweep32Args a, 
     for (int o = 16; o > 0; o >>= 1) yself = max(yself, __shfl_xor_sync(0xffffffffu, yself, o));
     if (lane == 0) {
       uint32_t db, rb;
-      finish32(a, v, acc.value(), yself, pf, db, rb);
+      finish32<DYN>(a, v, acc.value(), yself, pf, db, rb);
       dmax = max(dmax, db);
       rmax = max(rmax, rb);
     }
@@ -231,16 +291,25 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_warp(const Sweep32Args a, 
   block_max2_to(dmax, rmax, a.resid);
 }
 
-template <int KV>
-__global__ void __launch_bounds__(kThreads) k_sweep32_block(const Sweep32Args a, int64_t begin, int64_t end) {
+template <int KV, bool DYN>
+__global__ void __launch_bounds__(kThreads) k_sweep32_block(const Sweep32Args a_in, int64_t begin, int64_t end) {
+  const Sweep32Args a = resolve32(a_in);
   if (converged32(a)) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
   __shared__ float s_s[kThreads / 32], s_e[kThreads / 32];
   __shared__ uint32_t s_y[kThreads / 32];
+  __shared__ int s_skip;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t dmax = 0, rmax = 0;
   for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
     const int32_t v = (int32_t)i;
+    if (DYN) {
+      if (threadIdx.x == 0) s_skip = skip_unaffected32(a, v) ? 1 : 0;
+      __syncthreads();
+      const int sk = s_skip;
+      __syncthreads();
+      if (sk) continue;
+    }
     const int64_t b = a.off[v], e = a.off[v + 1];
     Kahan acc;
     uint32_t yself = 0;
@@ -262,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_block(const Sweep32Args a,
         ym = max(ym, s_y[k]);
       }
       uint32_t db, rb;
-      finish32(a, v, tot.value(), ym, pf, db, rb);
+      finish32<DYN>(a, v, tot.value(), ym, pf, db, rb);
       dmax = max(dmax, db);
       rmax = max(rmax, rb);
     }
@@ -285,9 +354,8 @@ Kind32 class_kind32(const PartThr& t, int c) {
   return kWarp;
 }
 
-}  // namespace
-
-int launch_sweep32(const Sweep32Args& a, const PartThr& t, const int64_t* cb, cudaStream_t s) {
+template <bool DYN>
+int launch_all32(const Sweep32Args& a, const PartThr& t, const int64_t* cb, cudaStream_t s) {
   const int maxg = kSMs * 8;
   const int C = t.n + 1;
   for (int c = 0; c < C; ++c) {
@@ -298,16 +366,29 @@ int launch_sweep32(const Sweep32Args& a, const PartThr& t, const int64_t* cb, cu
     const bool self1 = a.self_loops && kind == kT1 && t.thr[c] <= 1;
     switch (kind) {
       case kT1:
-        if (self1) k_sweep32_group<1, 1, true><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
-        else k_sweep32_group<1, 1, false><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
+        if (self1) k_sweep32_group<1, 1, true, DYN><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
+        else k_sweep32_group<1, 1, false, DYN><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
         break;
-      case kT4: k_sweep32_group<1, 4, false><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      case kG4: k_sweep32_group<4, 4, false><<<grid_for(cnt * 4, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      case kG16: k_sweep32_group<16, 8, false><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      case kWarp: k_sweep32_warp<2><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      default: k_sweep32_block<4><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kT4: k_sweep32_group<1, 4, false, DYN><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG4: k_sweep32_group<4, 4, false, DYN><<<grid_for(cnt * 4, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG16: k_sweep32_group<16, 8, false, DYN><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kWarp: k_sweep32_warp<2, DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      default: k_sweep32_block<4, DYN><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e); break;
     }
   }
+  PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+}  // namespace
+
+int launch_sweep32(const Sweep32Args& a, const PartThr& t, const int64_t* cb, bool dynamic, cudaStream_t s) {
+  return dynamic ? launch_all32<true>(a, t, cb, s) : launch_all32<false>(a, t, cb, s);
+}
+
+int launch_iter_check32(int* ctl, const uint32_t* resid_base, float tol_rel, int max_iter,
+                        cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_iter_check32<<<1, 1, 0, s>>>(ctl, resid_base, tol_rel, max_iter, h);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }

@@ -51,3 +51,55 @@ def huge_row_edges(n=1 << 15, hub_deg=40000, seed=5):
 def csr_equal(off_a, adj_a, off_b, adj_b):
     return np.array_equal(np.asarray(off_a), np.asarray(off_b)) and np.array_equal(np.asarray(adj_a),
                                                                                     np.asarray(adj_b))
+
+
+def dynamic_case(seed, scale, nsamp, size, thresholds=None):
+    """R-MAT graph on the GPU and in the oracle, R^{t-1} from the oracle, and one random batch
+    (80% insertions, 20% deletions) applied on both sides. Returns
+    (gpu graph, oracle G^t, R^{t-1} on the GPU, (ds, dd, is, id, gpu masks, oracle masks))."""
+    import paper_2404_08299_gb300 as prdf
+    n, s, d = synth.rmat(scale, nsamp, seed=seed)
+    return batch_case(n, s, d, seed, size, thresholds)
+
+
+def batch_case(n, s, d, seed, size, thresholds=None, extra=None):
+    """As dynamic_case for a given edge list; extra = (ds, dd, is, id) appended to the random batch."""
+    import torch
+    import paper_2404_08299_gb300 as prdf
+    og0 = oracle.graph(n, s, d)
+    g = prdf.Graph(n, dev(s, torch.int32), dev(d, torch.int32))
+    if thresholds is not None:
+        g.set_thresholds(prdf.PRDF_IN, thresholds)
+    R0o, _ = oracle.pagerank_static(og0)  # R^{t-1} from the oracle feeds both sides
+    ds, dd, is_, id_ = synth.batch(n, og0.out_off, og0.out_adj, size, seed=seed, s1=7)
+    if extra is not None:
+        ds, dd, is_, id_ = (np.concatenate([a, b]).astype(np.int32) for a, b in zip((ds, dd, is_, id_), extra))
+    de, ie = g.apply_batch(dev(ds), dev(dd), dev(is_), dev(id_))
+    og1, dmo, imo = oracle.apply_batch(og0, ds, dd, is_, id_)
+    return g, og1, dev(R0o), (ds, dd, is_, id_, de, ie, dmo, imo)
+
+
+def planted_hub_case(seed, size=40):
+    """R-MAT with 2^15 vertices plus two planted in-hubs (vertex 7 with about 19 K distinct sources, vertex 11
+    with about 7 K), so that rows of in-degree above 4096 (the block-per-vertex class of the DF / DF-P sweep
+    under the default thresholds) exist; the batch deletes 16 existing in-edges of each hub and inserts 16 new
+    ones on top of `size` random updates."""
+    n, s, d = synth.rmat(15, 1 << 18, seed=seed)
+    h7 = synth.randint(30000, n, seed=seed + 100)
+    h11 = synth.randint(8000, n, seed=seed + 200)
+    s = np.concatenate([s, h7, h11]).astype(np.int32)
+    d = np.concatenate([d, np.full(30000, 7, np.int32), np.full(8000, 11, np.int32)]).astype(np.int32)
+    og0 = oracle.graph(n, s, d)
+    eds, edd, eis, eid = [], [], [], []
+    for k, h in enumerate((7, 11)):
+        row = og0.in_adj[og0.in_off[h]:og0.in_off[h + 1]]
+        row = row[row != h]
+        pick = row[synth.randint(16, len(row), seed=seed + 300 + k)]
+        cand = synth.randint(200, n, seed=seed + 400 + k)
+        new = cand[~np.isin(cand, row) & (cand != h)][:16]
+        eds.append(pick)
+        edd.append(np.full(len(pick), h, np.int32))
+        eis.append(new)
+        eid.append(np.full(len(new), h, np.int32))
+    extra = tuple(np.concatenate(x).astype(np.int32) for x in (eds, edd, eis, eid))
+    return n, s, d, extra

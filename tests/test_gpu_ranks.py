@@ -15,7 +15,7 @@ import torch
 
 import oracle
 import synth
-from helpers import adversarial_edges, dev, host
+from helpers import adversarial_edges, batch_case, dev, dynamic_case, host, planted_hub_case
 
 pytestmark = pytest.mark.gpu
 
@@ -122,23 +122,12 @@ def test_static_rejects_bad_params():
 
 # ------------------------------------------------------------------ DF-P ----
 
-def _dynamic_case(seed, scale, nsamp, size):
-    n, s, d = synth.rmat(scale, nsamp, seed=seed)
-    og0 = oracle.graph(n, s, d)
-    g = gpu_graph(n, s, d)
-    R0o, _ = oracle.pagerank_static(og0)  # R^{t-1} from the oracle feeds both sides
-    R0 = dev(R0o)
-    ds, dd, is_, id_ = synth.batch(n, og0.out_off, og0.out_adj, size, seed=seed, s1=7)
-    de, ie = g.apply_batch(dev(ds), dev(dd), dev(is_), dev(id_))
-    og1, dmo, imo = oracle.apply_batch(og0, ds, dd, is_, id_)
-    return g, og1, R0, (ds, dd, is_, id_, de, ie, dmo, imo)
+def _dynamic_case(seed, scale, nsamp, size, thresholds=None):
+    return dynamic_case(seed, scale, nsamp, size, thresholds)
 
 
-@pytest.mark.parametrize("expand_pull", [1 / 16, 0.0, 2.0])  # automatic, always pull, always push
-@pytest.mark.parametrize("prune", [1, 0])
-@pytest.mark.parametrize("seed,scale,nsamp,size", [(1, 8, 3000, 20), (2, 10, 12000, 60), (3, 12, 50000, 5)])
-def test_dfp_matches_oracle_step_by_step(prune, seed, scale, nsamp, size, expand_pull):
-    g, og1, R0, (ds, dd, is_, id_, de, ie, dmo, imo) = _dynamic_case(seed, scale, nsamp, size)
+def _check_dfp_step_by_step(g, og1, R0, batch, prune, expand_pull):
+    ds, dd, is_, id_, de, ie, dmo, imo = batch
     R, st, dV = g.pagerank_dfp(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True, prune=prune,
                                expand_pull=expand_pull)
     Ro, sto, dVo, trace = oracle.pagerank_dfp(og1, ds, dd, is_, host(R0), del_mask=dmo, ins_mask=imo, prune=bool(prune))
@@ -146,6 +135,87 @@ def test_dfp_matches_oracle_step_by_step(prune, seed, scale, nsamp, size, expand
     assert st.affected_initial == trace[0]
     assert np.array_equal(host(dV), dVo)
     assert np.max(np.abs(host(R) - Ro) / Ro) <= 1e-12
+
+
+@pytest.mark.parametrize("expand_pull", [1 / 16, 0.0, 2.0])  # automatic, always pull, always push
+@pytest.mark.parametrize("prune", [1, 0])
+@pytest.mark.parametrize("seed,scale,nsamp,size", [(1, 8, 3000, 20), (2, 10, 12000, 60), (3, 12, 50000, 5)])
+def test_dfp_matches_oracle_step_by_step(prune, seed, scale, nsamp, size, expand_pull):
+    g, og1, R0, batch = _dynamic_case(seed, scale, nsamp, size)
+    _check_dfp_step_by_step(g, og1, R0, batch, prune, expand_pull)
+
+
+@pytest.mark.parametrize("expand_pull", [1 / 16, 0.0, 2.0])
+@pytest.mark.parametrize("prune", [1, 0])
+def test_dfp_hub_rows_step_by_step(prune, expand_pull):
+    """Rows of in-degree above 4096 run the block-per-vertex kernel of the DF / DF-P sweep (the highest
+    in-degree class under the default thresholds): two planted in-hubs (about 19 K and 7 K sources) whose
+    in-rows the batch changes, flags exact and ranks to 1e-12 against the oracle, step by step."""
+    n, s, d, extra = planted_hub_case(11)
+    g, og1, R0, batch = batch_case(n, s, d, 11, 40, extra=extra)
+    assert (og1.indeg > 4096).sum() == 2
+    _check_dfp_step_by_step(g, og1, R0, batch, prune, expand_pull)
+
+
+@pytest.mark.parametrize("expand_pull", [1 / 16, 0.0, 2.0])
+@pytest.mark.parametrize("prune", [1, 0])
+@pytest.mark.parametrize("thr", [[1, 4, 16, 32, 64], [0, 4]])
+def test_dfp_lowered_thresholds_step_by_step(thr, prune, expand_pull):
+    """Lowered in-degree thresholds put hundreds of rows into the block-per-vertex class (in-degree above
+    64, or above 4) and the warp class: DF / DF-P still match the oracle step by step."""
+    g, og1, R0, batch = _dynamic_case(3, 12, 50000, 5, thresholds=thr)
+    assert (og1.indeg > thr[-1]).sum() >= 80
+    _check_dfp_step_by_step(g, og1, R0, batch, prune, expand_pull)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_and_host_loops_give_the_same_bits(precision):
+    """The sweep loop runs as one CUDA graph (default) or from the host (time_sweeps=1): Static, DF-P and DT
+    return identical ranks, flags and sweep counts either way, in FP64 and in mixed precision."""
+    g, og1, R0, (ds, dd, is_, id_, de, ie, dmo, imo) = _dynamic_case(2, 12, 40000, 30)
+    Rg, stg = g.pagerank_static(precision=precision)
+    Rh, sth = g.pagerank_static(precision=precision, time_sweeps=1)
+    assert torch.equal(Rg, Rh) and stg.iterations == sth.iterations and stg.iterations_fp32 == sth.iterations_fp32
+    for call in (g.pagerank_dfp, g.pagerank_dt):
+        Rg, stg, dVg = call(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True,
+                            precision=precision)
+        Rh, sth, dVh = call(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True,
+                            precision=precision, time_sweeps=1)
+        assert torch.equal(Rg, Rh) and torch.equal(dVg, dVh)
+        assert stg.iterations == sth.iterations and stg.iterations_fp32 == sth.iterations_fp32
+        assert sth.sweeps_launched >= sth.iterations and stg.sweeps_launched == stg.iterations
+
+
+@pytest.mark.parametrize("bad", ["nan", "negative", "inf", "sum"])
+def test_start_vectors_outside_the_sweeps_domain_are_rejected(bad):
+    """R0 (Naive-dynamic) and prev_ranks (DF-P, DT) must be finite, non-negative and sum to at most 4 (the
+    exact accumulator's range); anything else is PRDF_EINVAL and the output is left untouched."""
+    P = prdf()
+    n, s, d = synth.rmat(10, 8000, seed=4)
+    g = gpu_graph(n, s, d)
+    R0 = synth.uniform(n, seed=9)
+    R0 /= R0.sum()
+    if bad == "nan":
+        R0[17] = np.nan
+    elif bad == "negative":
+        R0[3] = -1e-12
+    elif bad == "inf":
+        R0[n - 1] = np.inf
+    else:
+        R0 *= 4.5
+    R0d = dev(R0)
+    e = torch.zeros(0, dtype=torch.int32, device="cuda")
+    with pytest.raises(P.PrdfError) as ex:
+        g.pagerank_static(R0=R0d)
+    assert ex.value.code == -1
+    for call in (g.pagerank_dfp, g.pagerank_dt):
+        with pytest.raises(P.PrdfError) as ex:
+            call(e, e, e, R0d)
+        assert ex.value.code == -1
+    # a valid vector still works after the rejections
+    R1 = synth.uniform(n, seed=9)
+    R, st = g.pagerank_static(R0=dev(R1 / R1.sum()))
+    assert st.converged
 
 
 def test_dfp_error_against_static_reference():

@@ -58,6 +58,31 @@ def test_noalloc_partition_matches_allocating_partition_twice():
         assert torch.equal(P2, P_ref) and cnt2 == cnt_ref[:len(thr) + 1]
 
 
+def test_noalloc_partition_at_its_size_limit():
+    """n = 2^24 exactly with three thresholds (four classes): the last count tiles, the scan's tail and
+    the class totals at the top of the fixed scratch are all used. A graph of 2^24 vertices with 2^22
+    R-MAT samples spreads the degrees over all four classes; bit-exact against prdf_partition."""
+    import paper_2404_08299_gb300 as prdf
+    n_max = prdf.NOALLOC_MAX_N
+    n, s, d = synth.rmat(24, 1 << 22, seed=4)
+    assert n == n_max
+    g = prdf.Graph(n, dev(s, torch.int32), dev(d, torch.int32))
+    thr = [1, 2, 8]
+    for which in (prdf.PRDF_IN, prdf.PRDF_OUT):
+        g.set_thresholds(which, thr)
+        P_ref, cnt_ref = g.partition(which)
+        off, _, _ = g.export_csr(which)
+        assert min(cnt_ref[:4]) > 0
+        for _ in range(2):
+            P, cnt = prdf.partition_noalloc(off, thr)
+            assert torch.equal(P, P_ref) and cnt == cnt_ref[:4]
+    del g
+    with pytest.raises(ValueError):
+        prdf.partition_noalloc(torch.zeros(n_max + 2, dtype=torch.int64, device="cuda"), thr)
+    with pytest.raises(ValueError):
+        prdf.partition_noalloc(torch.zeros(1, dtype=torch.int64, device="cuda"), thr)
+
+
 def test_noalloc_partition_rejects_sizes_beyond_its_scratch():
     import paper_2404_08299_gb300 as prdf
     off = torch.zeros(2, dtype=torch.int64, device="cuda")
