@@ -179,7 +179,8 @@ class ClockSampler:
 
 def measure_mixed(g, R64, m, args):
     """FP32 sweeps with compensated sums to ||dR|| <= 1e-6 ||R|| (relative), then FP64 sweeps to the
-    same L-inf 1e-10: time to tolerance beside the FP64 path and the L-inf distance to its result."""
+    same L-inf 1e-10: time to tolerance beside the FP64 path and the L-inf distance to its result.
+    The result tensor is kept under "_R" for the error against the oracle."""
     import torch
     import paper_2404_08299_gb300 as prdf
     for _ in range(2):
@@ -198,7 +199,7 @@ def measure_mixed(g, R64, m, args):
             "sweeps_fp64": st.iterations - st.iterations_fp32, "converged": bool(st.converged),
             "gteps": st.iterations * m / (ms * 1e-3) / 1e9,
             "linf_vs_fp64_path": float((R - R64).abs().max()),
-            "note": "FP32 stage stops at ||dR||_inf <= 1e-6 ||R||_inf; FP64 stage to L-inf 1e-10"}
+            "note": "FP32 stage stops at ||dR||_inf <= 1e-6 ||R||_inf; FP64 stage to L-inf 1e-10", "_R": R}
 
 
 def measure_dfp(g, n, m, args):
@@ -220,6 +221,7 @@ def measure_dfp(g, n, m, args):
         t_nd, t_df, errs_nd, errs_df = [], [], [], []
         t_apply = []
         errs_inf = []
+        t_mix, errs_mix, sweeps_mix = [], [], []
         parts = {"partition": [], "mark": [], "iterate": []}
         for b in range(args.dfp_batches):
             off, adj, _ = g.export_csr(prdf.PRDF_OUT)
@@ -235,6 +237,8 @@ def measure_dfp(g, n, m, args):
             torch.cuda.synchronize()
             t_apply.append(a0.elapsed_time(a1))
             R, st, _ = g.pagerank_dfp(t(ds), t(dd), t(is_), R_prev, del_mask=de, ins_mask=ie)
+            Rm, stm, _ = g.pagerank_dfp(t(ds), t(dd), t(is_), R_prev, del_mask=de, ins_mask=ie,
+                                        precision=prdf.PRDF_FP32_REFINE)
             Rd, std, _ = g.pagerank_dt(t(ds), t(dd), t(is_), R_prev, del_mask=de, ins_mask=ie)
             Rn, stn = g.pagerank_static(R0=R_prev)  # Naive-dynamic (Alg. naive)
             Rf, stf, _ = g.pagerank_dfp(t(ds), t(dd), t(is_), R_prev, del_mask=de, ins_mask=ie, prune=0)  # DF
@@ -254,6 +258,9 @@ def measure_dfp(g, n, m, args):
             t_static.append(sts.ms_total)
             errs.append(float((R - Rt).abs().sum()))
             errs_inf.append(float((R - Rt).abs().max() / Rt.abs().max()))
+            t_mix.append(stm.ms_total)
+            errs_mix.append(float((Rm - Rt).abs().sum()))
+            sweeps_mix.append((stm.iterations_fp32, stm.iterations - stm.iterations_fp32))
             iters.append(st.iterations)
             aff.append(st.affected_initial)
             R_prev = R
@@ -268,7 +275,103 @@ def measure_dfp(g, n, m, args):
                     "dfp_speedup_vs_dt": statistics.median(t_dt) / statistics.median(t_dfp),
                     "nd_ms": statistics.median(t_nd), "nd_l1_err_max": max(errs_nd),
                     "df_ms": statistics.median(t_df), "df_l1_err_max": max(errs_df),
-                    "apply_batch_ms": statistics.median(t_apply)})
+                    "fp32_refined": {"dfp_ms": statistics.median(t_mix), "l1_err_max": max(errs_mix),
+                                     "speedup_vs_fp64_dfp": statistics.median(t_dfp) / statistics.median(t_mix),
+                                     "sweeps_fp32_fp64": sweeps_mix[len(sweeps_mix) // 2]},
+                    "apply_batch_ms": statistics.median(t_apply),
+                    "errors_against": "GPU Static at L-inf 1e-13 on the same snapshot (see oracle_errors for the "
+                                      "oracle-referenced errors)"})
+    return out
+
+
+def _timed(fn, reps):
+    """Median device time (stats.ms_total) of reps calls, and the last call's result."""
+    ms, res = [], None
+    for _ in range(reps):
+        res = fn()
+        ms.append(res[1].ms_total)
+    return statistics.median(ms), res
+
+
+def measure_oracle_errors(args, og0, h_src, h_dst, R_gpu, R_mixed):
+    """Errors against the FP64 oracle at full size.
+
+    Static: the headline FP64 result and the mixed-precision result against the oracle's own Static solve
+    (Alg. static, same tolerance 1e-10, same start). DF-P: for each batch fraction in --oracle-dfp-sizes one
+    random batch (80% insertions of uniform pairs, 20% deletions of existing non-self-loop edges, drawn from
+    the oracle's CSR) is applied by the oracle (set semantics) and by the GPU to a fresh copy of the base
+    graph; the reference is the oracle's Static solve of G^t at L-inf 1e-13. From the GPU Static ranks of
+    G^0 (L-inf 1e-10) the GPU runs DF-P with tau_f = tau_p in --tau-p, DF-P in mixed precision, DF,
+    Naive-dynamic and Dynamic Traversal, and GPU Static from scratch; each is reported with its device time
+    (median of --oracle-reps calls), sweeps, and L1 / relative L-inf error against the oracle reference."""
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    import paper_2404_08299_gb300 as prdf
+    n = og0.n
+    out = {}
+    t0 = time.time()
+    Ro, sto = oracle.pagerank_static(og0)
+    t_static = time.time() - t0
+
+    def errs(R, ref, ref10=None):
+        r = R.cpu().numpy() if hasattr(R, "cpu") else R
+        d = np.abs(r - ref)
+        e = {"l1": float(d.sum()), "linf": float(d.max()), "linf_rel": float(d.max() / ref.max())}
+        if ref10 is not None:
+            e["l1_vs_oracle_static_1e-10"] = float(np.abs(r - ref10).sum())
+        return e
+
+    out["static"] = dict(errs(R_gpu, Ro), oracle_sweeps=sto.iterations, oracle_seconds=round(t_static, 2),
+                         reference="oracle Static, L-inf 1e-10 (the same iteration and stop rule)")
+    if R_mixed is not None:
+        out["fp32_refined"] = dict(errs(R_mixed, Ro), reference="oracle Static, L-inf 1e-10")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dfp = []
+    for fi, f in enumerate(args.oracle_dfp_sizes):
+        m0 = og0.m
+        size = max(1, int(round(f * m0)))
+        ds, dd, is_, id_ = synth.batch(n, og0.out_off, og0.out_adj, size, seed=1, s1=100 + fi, s2=0)
+        t0 = time.time()
+        og1, _, _ = oracle.apply_batch(og0, ds, dd, is_, id_)
+        ref, st_ref = oracle.pagerank_static(og1, tol=1e-13)
+        # the oracle's from-scratch Static ranks of G^t with the paper's settings (tau 1e-10)
+        ref10, st10 = oracle.pagerank_static(og1)
+        t_ref = time.time() - t0
+        del og1
+        gf = prdf.Graph(n, h_src.cuda(non_blocking=True), h_dst.cuda(non_blocking=True))
+        de, ie = gf.apply_batch(t(ds), t(dd), t(is_), t(id_))
+        b = (t(ds), t(dd), t(is_))
+        rec = {"batch_fraction": f, "batch_size": size, "oracle_reference_sweeps": st_ref.iterations,
+               "oracle_seconds": round(t_ref, 1),
+               "references": "l1, linf: oracle Static of G^t at L-inf 1e-13 (converged); l1_vs_oracle_static_1e-10: "
+                             "the oracle's from-scratch Static of G^t with the paper's tau 1e-10 (%d sweeps)"
+                             % st10.iterations}
+        ms, (Rs, sts) = _timed(lambda: gf.pagerank_static(), args.oracle_reps)
+        rec["static"] = dict(errs(Rs, ref, ref10), ms=ms, sweeps=sts.iterations)
+        rec["dfp"] = []
+        for tau in args.tau_p:
+            ms, (R, st, _) = _timed(lambda: gf.pagerank_dfp(*b, R_gpu, del_mask=de, ins_mask=ie, tau_f=tau, tau_p=tau),
+                                    args.oracle_reps)
+            rec["dfp"].append(dict(errs(R, ref, ref10), tau_f=tau, tau_p=tau, ms=ms, sweeps=st.iterations,
+                                   speedup_vs_static=rec["static"]["ms"] / ms))
+        ms, (R, st, _) = _timed(lambda: gf.pagerank_dfp(*b, R_gpu, del_mask=de, ins_mask=ie,
+                                                        precision=prdf.PRDF_FP32_REFINE), args.oracle_reps)
+        rec["dfp_fp32_refined"] = dict(errs(R, ref, ref10), ms=ms, sweeps_fp32=st.iterations_fp32,
+                                       sweeps_fp64=st.iterations - st.iterations_fp32,
+                                       speedup_vs_static=rec["static"]["ms"] / ms)
+        ms, (R, st, _) = _timed(lambda: gf.pagerank_dfp(*b, R_gpu, del_mask=de, ins_mask=ie, prune=0),
+                                args.oracle_reps)
+        rec["df"] = dict(errs(R, ref, ref10), ms=ms, sweeps=st.iterations)
+        ms, (R, st) = _timed(lambda: gf.pagerank_static(R0=R_gpu), args.oracle_reps)
+        rec["naive_dynamic"] = dict(errs(R, ref, ref10), ms=ms, sweeps=st.iterations)
+        ms, (R, st, _) = _timed(lambda: gf.pagerank_dt(*b, R_gpu, del_mask=de, ins_mask=ie), args.oracle_reps)
+        rec["dt"] = dict(errs(R, ref, ref10), ms=ms, sweeps=st.iterations)
+        dfp.append(rec)
+        del gf, ref, ref10
+        torch.cuda.empty_cache()
+    out["dfp"] = dfp
     return out
 
 
@@ -331,7 +434,10 @@ def measure_ppr(args):
     """Weighted personalised PageRank and its adjoint on the 2^22-vertex R-MAT (2^26 samples, weights
     U[0.5, 1.5) on every edge and self-loop, row-normalised), K = 64 teleport columns each on 16 seed
     vertices with Dirichlet(1) weights, loss sum_c g_c . r_c with g ~ N(0, 1): time to tolerance of the
-    mixed-precision and FP64 forms (same 1e-10 L-inf stop rule) and of the backward pass."""
+    mixed-precision and FP64 forms (same 1e-10 L-inf stop rule) and of the backward pass; the same 64
+    columns solved one per call (K = 1) against the batched call; and, on a sample of columns, the error
+    of every result against the FP64 oracle (forward ranks, dL/dS; dL/dw from the same job restricted to
+    the sampled columns, since it sums over columns)."""
     import numpy as np
     import torch
     import synth
@@ -343,8 +449,10 @@ def measure_ppr(args):
     g = prdf.Graph(n, torch.from_numpy(s2).cuda(), torch.from_numpy(d2).cuda(), torch.from_numpy(w).cuda())
     m = g.m
     K = 64
-    S = torch.from_numpy(synth.ppr_seeds(n, K, n_seed=16, seed=2)).cuda()
-    Gw = torch.from_numpy(synth.normal((n, K), seed=3)).cuda()
+    S_h = synth.ppr_seeds(n, K, n_seed=16, seed=2)
+    S = torch.from_numpy(S_h).cuda()
+    Gw_h = synth.normal((n, K), seed=3)
+    Gw = torch.from_numpy(Gw_h).cuda()
     out = {"n": n, "m": m, "K": K}
     res = {}
     for name, prec in (("fp32_refined", prdf.PRDF_FP32_REFINE), ("fp64", prdf.PRDF_FP64)):
@@ -363,19 +471,59 @@ def measure_ppr(args):
     gS, gw, stb = g.pagerank_backward(res["fp32_refined"], Gw, precision=prdf.PRDF_FP32_REFINE)
     out["backward"] = {"ms": stb.ms_total, "sweeps_fp32": stb.iterations_fp32,
                        "steps_fp64": stb.iterations - stb.iterations_fp32, "converged": bool(stb.converged)}
-    del g
+    # batching: the same 64 columns one per call (K = 1), mixed precision, same stop rule
+    R1 = None
+    if args.ppr_single:
+        single_ms, single_sweeps = 0.0, 0
+        R1 = torch.empty_like(res["fp32_refined"])
+        g.pagerank_ppr(S[:, :1].contiguous(), precision=prdf.PRDF_FP32_REFINE)  # warm-up of the K = 1 shapes
+        for c in range(K):
+            Rc, stc = g.pagerank_ppr(S[:, c:c + 1].contiguous(), precision=prdf.PRDF_FP32_REFINE)
+            single_ms += stc.ms_total
+            single_sweeps += stc.iterations
+            R1[:, c:c + 1] = Rc
+        out["single_column_calls"] = {
+            "calls": K, "ms_total": single_ms, "sweeps_total": single_sweeps,
+            "batched_speedup": single_ms / out["fp32_refined"]["ms"],
+            "linf_vs_batched": float((R1 - res["fp32_refined"]).abs().max()),
+            "note": "64 calls of prdf_pagerank_ppr with K = 1 (mixed precision) against one call with K = 64"}
+    # errors against the FP64 oracle on sampled columns
+    if args.ppr_oracle_cols:
+        import oracle
+        oracle.build()
+        cols = args.ppr_oracle_cols
+        t0 = time.time()
+        og = oracle.graph(n, s2, d2)
+        rows, dsts = oracle.csr_to_edges(og.out_off, og.out_adj)
+        w_out = synth.edge_weights(rows, dsts, seed=1).astype(np.float64)
+        P = oracle.row_normalise(og, w_out)
+        Ro, sto = oracle.ppr(og, P, np.ascontiguousarray(S_h[:, cols]), tol=1e-13)
+        Gc = np.ascontiguousarray(Gw_h[:, cols])
+        _, gSo, gwo, sta = oracle.ppr_adjoint(og, w_out, P, Ro, Gc, tol=1e-13)
+        t_or = time.time() - t0
+        err = {"columns": cols, "oracle_seconds": round(t_or, 1), "oracle_sweeps": sto.iterations,
+               "reference": "oracle K-column PPR and adjoint at L-inf 1e-13 on the sampled columns"}
+        for name in ("fp32_refined", "fp64"):
+            err[name] = float(np.abs(res[name][:, cols].cpu().numpy() - Ro).max())
+        if R1 is not None:
+            err["single_column_calls"] = float(np.abs(R1[:, cols].cpu().numpy() - Ro).max())
+        err["backward_grad_S"] = float(np.abs(gS[:, cols].cpu().numpy() - gSo).max() / np.abs(gSo).max())
+        # dL/dw sums over columns: the GPU runs the same job restricted to the sampled columns
+        Sc = torch.from_numpy(np.ascontiguousarray(S_h[:, cols])).cuda()
+        Rc, _ = g.pagerank_ppr(Sc, precision=prdf.PRDF_FP32_REFINE)
+        _, gwc, _ = g.pagerank_backward(Rc, torch.from_numpy(Gc).cuda(), precision=prdf.PRDF_FP32_REFINE)
+        err["backward_grad_w"] = float(np.abs(gwc.cpu().numpy() - gwo).max() / np.abs(gwo).max())
+        err["note"] = "forward: max abs error; gradients: max abs error / max abs oracle gradient"
+        out["oracle_errors"] = err
+    del g, R1
     torch.cuda.empty_cache()
     return out
 
 
-def cpu_baseline(n, src, dst, m, target_s):
+def cpu_baseline(og, t_build, m, target_s):
     """The FP64 oracle (as it stands) on the host cores: a bounded sample of sweeps
-    of the same Static iteration on the same graph."""
+    of the same Static iteration on the same graph (og, built in t_build seconds)."""
     import oracle
-    oracle.build()
-    t0 = time.time()
-    og = oracle.graph(n, src, dst)
-    t_build = time.time() - t0
     t0 = time.time()
     oracle.pagerank_static(og, tol=0.0, max_iter=1)
     t1 = time.time() - t0
@@ -456,6 +604,15 @@ def main():
                     help="also keep the nvidia-smi clock samples of the timed region in this directory")
     ap.add_argument("--profile-ppr", action="store_true",
                     help="build the 2^22 weighted graph and run a few K=64 PPR sweeps (for ncu captures)")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the errors against the oracle at full size")
+    ap.add_argument("--oracle-dfp-sizes", type=float, nargs="*", default=[1e-4],
+                    help="batch fractions of the DF-P errors against the oracle")
+    ap.add_argument("--tau-p", type=float, nargs="*", default=[1e-6, 3e-7, 1e-7],
+                    help="tau_f = tau_p values of DF-P in the oracle comparison")
+    ap.add_argument("--oracle-reps", type=int, default=3)
+    ap.add_argument("--ppr-oracle-cols", type=int, nargs="*", default=[0, 63],
+                    help="columns of the K = 64 job checked against the oracle (none: skip)")
+    ap.add_argument("--ppr-single", type=int, default=1, help="also solve the 64 columns one per call (K = 1)")
     ap.add_argument("--profile-dfp", type=float, default=0.0,
                     help="build the 2^22 R-MAT, solve Static, apply one random batch of this fraction of |E| and run "
                          "DF-P once (for ncu captures of the build, batch-update, marking and DF-P sweep kernels)")
@@ -494,13 +651,14 @@ def main():
         n, s, d = synth.rmat(22, 1 << 26, seed=1)
         g = prdf.Graph(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
         n_, m = g.size()
-        R0, _ = g.pagerank_static()
+        # host-driven loops (time_sweeps=1): a profiler sees every sweep kernel as its own launch
+        R0, _ = g.pagerank_static(time_sweeps=1)
         off, adj, _ = g.export_csr(prdf.PRDF_OUT)
         size = max(1, int(round(args.profile_dfp * m)))
         ds, dd, is_, id_ = synth.batch(n, off.cpu().numpy(), adj.cpu().numpy(), size, seed=1, s1=0, s2=0)
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
         de, ie = g.apply_batch(t(ds), t(dd), t(is_), t(id_))
-        R, st, _ = g.pagerank_dfp(t(ds), t(dd), t(is_), R0, del_mask=de, ins_mask=ie)
+        R, st, _ = g.pagerank_dfp(t(ds), t(dd), t(is_), R0, del_mask=de, ins_mask=ie, time_sweeps=1)
         torch.cuda.synchronize()
         print(json.dumps({"profile_dfp": args.profile_dfp, "n": n, "m": m, "batch": size, "sweeps": st.iterations,
                           "affected_initial": st.affected_initial, "ms_total": st.ms_total}), flush=True)
@@ -595,8 +753,10 @@ def main():
     c1.record(stream)
     torch.cuda.synchronize()
     extras["cuda_graph_time_to_tol_ms"] = c0.elapsed_time(c1) / args.steps
+    R_mixed = None
     if not args.no_extras:
         extras["fp32_refined"] = measure_mixed(g, R, m, args)
+        R_mixed = extras["fp32_refined"].pop("_R")
 
     # end to end through the public API with host buffers: H2D edge list, graph build, solve, D2H ranks
     h_R = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -619,6 +779,20 @@ def main():
     e2e_step, e2e_edges = aggregate_ranks(sum(e2e_ms) / len(e2e_ms), st2.iterations * m, dist)
     e2e_val = e2e_edges / (e2e_step * 1e-3) / 1e9
 
+    # errors against the FP64 oracle at full size (the oracle graph also serves the CPU baseline)
+    og0, t_og = None, 0.0
+    oracle_errors = None
+    if rank == 0 and world == 1 and (not args.no_oracle or not args.no_cpu_baseline):
+        import oracle
+        oracle.build()
+        t0 = time.time()
+        og0 = oracle.graph(n, src, dst)
+        t_og = time.time() - t0
+    if og0 is not None and not args.no_oracle:
+        oracle_errors = measure_oracle_errors(args, og0, h_src, h_dst, R, R_mixed)
+        extras["oracle_errors"] = oracle_errors
+    del R_mixed
+
     if not args.no_extras and args.dfp_sizes:
         extras["dfp"] = measure_dfp(g, n, m, args)
     if not args.no_extras:
@@ -629,8 +803,8 @@ def main():
             extras["temporal"] = measure_temporal(args)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(n, src, dst, m, args.cpu_seconds)
+    if og0 is not None and not args.no_cpu_baseline:
+        cpu = cpu_baseline(og0, t_og, m, args.cpu_seconds)
 
     if rank == 0:
         kind, prm, desc = WORKLOADS[args.workload]
@@ -644,6 +818,7 @@ def main():
                        "l2": "inputs larger than L2 (in-CSR %.2f GB, rank vector %.0f MB)" % (
                            (4 * m + 8 * (n + 1)) / 1e9, 8 * n / 1e6)},
             "time_to_tol_ms": ms_step, "iterations": iters, "converged": bool(sts[-1].converged),
+            "linf_vs_oracle": oracle_errors["static"]["linf"] if oracle_errors else None,
             "final_delta": sts[-1].final_delta, "paper_style_geps": m / (ms_step * 1e-3) / 1e9,
             "ms_partition": statistics.median(s.ms_partition for s in sts),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -459,7 +459,14 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
   L->nci = rl.thr.n + 1;
   begins_from_counts(rl.count, L->nci, L->cb);
   L->kernels_per_iter = nonempty_classes(L->cb, L->nci);
+  // the highest in-degree class's rows are cut into the hub chunks of G' (a
+  // partial sum per chunk); the table and the partial buffer are made here,
+  // outside any stream capture
+  PRDF_TRY(ensure_hub(g, rl.in, g->hub_in, s));
+  const size_t nchunk = (size_t)(g->hub_in.nchunk > 0 ? g->hub_in.nchunk : 1);
+  if (g->hub_in.nchunk > 0) L->kernels_per_iter += 1;  // the highest class takes two kernels
   if (fp32) {
+    PRDF_TRY(g->sweep_hub_part32.reserve(nchunk, s));
     PRDF_TRY(g->resid32.reserve(2 * ((size_t)max_iter + 1), s));
     PRDF_CUDA(cudaMemsetAsync(g->resid32.p, 0, sizeof(uint32_t) * 2 * ((size_t)max_iter + 1), s));
     Sweep32Args& a = L->a32;
@@ -472,6 +479,8 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
     a.c0 = (float)((1.0 - p->alpha) / (double)n);
     a.self_loops = g->self_loops ? 1 : 0;
     a.tol_rel = L->tol_rel;
+    a.hub = g->hub_in.view();
+    a.hub_part = g->sweep_hub_part32.p;
     if (dynamic) {
       a.kf = g->kf32.p;
       a.dV = g->dV.p;
@@ -482,6 +491,7 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
       a.prune = p->prune;
     }
   } else {
+    PRDF_TRY(g->sweep_hub_part.reserve(nchunk, s));
     PRDF_TRY(g->resid.reserve((size_t)max_iter + 1, s));
     PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t) * ((size_t)max_iter + 1), s));
     SweepArgs& a = L->a;
@@ -495,6 +505,8 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
     a.c0 = (1.0 - p->alpha) / (double)n;
     a.self_loops = g->self_loops ? 1 : 0;
     a.tol = p->tol;
+    a.hub = g->hub_in.view();
+    a.hub_part = g->sweep_hub_part.p;
     if (dynamic) {
       a.dV = g->dV.p;
       a.dN = g->dN.p;
@@ -502,15 +514,6 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
       a.tau_f = p->tau_f;
       a.tau_p = p->tau_p;
       a.prune = p->prune;
-    } else {
-      // Static sweeps cut the highest in-degree class's rows into the hub
-      // chunks of G' (exact partial sums per chunk); the table and the partial
-      // buffer are made here, outside any stream capture
-      PRDF_TRY(ensure_hub(g, rl.in, g->hub_in, s));
-      PRDF_TRY(g->sweep_hub_part.reserve((size_t)(g->hub_in.nchunk > 0 ? g->hub_in.nchunk : 1), s));
-      a.hub = g->hub_in.view();
-      a.hub_part = g->sweep_hub_part.p;
-      if (a.hub.nchunk > 0) L->kernels_per_iter += 1;  // the highest class takes two kernels
     }
   }
   if (L->expand) {
@@ -522,7 +525,7 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
     PRDF_CUDA(cudaMemsetAsync(g->fwork.p, 0, sizeof(unsigned long long) * ((size_t)max_iter + 1), s));
     const double lim = p->expand_pull * (double)rl.in.m;
     L->fthr = lim >= 1.8e19 ? ~0ull : (unsigned long long)lim;
-    L->kernels_per_iter += nonempty_classes(L->cbo, L->nco) + 1 + (L->pull_warp_b > 0 ? 1 : 0) +
+    L->kernels_per_iter += nonempty_classes(L->cbo, L->nco) + (L->pull_warp_b > 0 ? 1 : 0) +
                            (n > L->pull_warp_b ? 1 : 0);
   }
   return PRDF_OK;
@@ -534,16 +537,19 @@ int launch_loop_sweep(prdf_graph* g, const Loop& L, int i, cudaStream_t s) {
   const Relabel& rl = g->rl;
   if (L.fp32) {
     Sweep32Args a = L.a32;
+    // the sweep counts the out-edges of its deltaN for the expansion round after it
     if (i >= 0) {
       a.y = (i & 1) ? g->yb.p : g->ya.p;
       a.yn = (i & 1) ? g->ya.p : g->yb.p;
       a.resid = g->resid32.p + 2 * i;
       a.prev = i > 0 ? g->resid32.p + 2 * (i - 1) : nullptr;
+      a.fw = L.expand ? g->fwork.p + i : nullptr;
     } else {
       a.ctl = g->ctl.p;
       a.ya = g->ya.p;
       a.yb = g->yb.p;
       a.resid_base = g->resid32.p;
+      a.fw_base = L.expand ? g->fwork.p : nullptr;
     }
     return launch_sweep32(a, rl.thr, L.cb, L.dynamic, s);
   }
@@ -553,11 +559,13 @@ int launch_loop_sweep(prdf_graph* g, const Loop& L, int i, cudaStream_t s) {
     a.xn = (i & 1) ? g->xa.p : g->xb.p;
     a.resid = g->resid.p + i;
     a.prev = i > 0 ? g->resid.p + i - 1 : nullptr;
+    a.fw = L.expand ? g->fwork.p + i : nullptr;
   } else {
     a.ctl = g->ctl.p;
     a.xa = g->xa.p;
     a.xb = g->xb.p;
     a.resid_base = g->resid.p;
+    a.fw_base = L.expand ? g->fwork.p : nullptr;
   }
   return launch_sweep(a, rl.thr, L.cb, L.exact, L.dynamic, s);
 }
@@ -577,8 +585,7 @@ int launch_loop_expansion(prdf_graph* g, const Loop& L, int i, cudaStream_t s) {
   }
   st.ctl = i >= 0 ? nullptr : g->ctl.p;
   unsigned long long* fw = g->fwork.p + (i >= 0 ? i : 0);
-  PRDF_TRY(launch_expand_pull(rl.in.off.p, rl.in.adj.p, rl.out.off.p, g->n, L.pull_warp_b, g->dN.p, g->dV.p, fw,
-                              L.fthr, st, s));
+  PRDF_TRY(launch_expand_pull(rl.in.off.p, rl.in.adj.p, g->n, L.pull_warp_b, g->dN.p, g->dV.p, fw, L.fthr, st, s));
   return launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, L.cbo, L.nco, g->dN.p, g->dV.p, nullptr, st, s, fw,
                        L.fthr);
 }
@@ -783,7 +790,8 @@ struct KOp {
   const double* p64;
   int64_t hub_begin;  // first vertex of the two highest in-degree classes
   const PprHubTable* hub;  // chunks of the highest class's rows of this CSR
-  const double* S64;  // right-hand side of the FP64 step
+  const double* S64;  // right-hand side (dense [n, K]), also the start of the iteration
+  bool sparse_rhs;    // look for few non-zero rows in S64 (a teleport on a few seed vertices)
 };
 
 int64_t hub_begin(const Relabel& rl) {
@@ -816,8 +824,9 @@ int ensure_hub(prdf_graph* g, const Csr& c, PprHubTable& t, cudaStream_t s) {
 
 // FP32 K-column solve of R = alpha P^T R + (1 - alpha) rhs from the start held
 // in *cur; on return *cur holds the result (the other buffer is scratch).
-int ppr32_solve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, const float* rhs, float** cur,
-                float** other, int max_iter, int* iters, long long* kernels, cudaStream_t s) {
+int ppr32_solve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, const float* rhs,
+                const int32_t* srow, float** cur, float** other, int max_iter, int* iters, long long* kernels,
+                cudaStream_t s) {
   PRDF_TRY(g->resid32.reserve(2 * ((size_t)max_iter + 1), s));
   PRDF_CUDA(cudaMemsetAsync(g->resid32.p, 0, sizeof(uint32_t) * 2 * ((size_t)max_iter + 1), s));
   PRDF_TRY(g->ppr_part.reserve((size_t)(op.hub->nchunk > 0 ? op.hub->nchunk : 1) * (size_t)tile, s));
@@ -827,6 +836,7 @@ int ppr32_solve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int t
   a.adj = op.adj;
   a.P = op.p32;
   a.S = rhs;
+  a.srow = srow;
   a.K = K;
   a.alpha = (float)p->alpha;
   a.beta = (float)(1.0 - p->alpha);
@@ -878,8 +888,9 @@ int ppr32_solve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int t
 }
 
 // one FP64 Jacobi step Rn = T(R); returns max |T(R) - R|
-int ppr64_step(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, const double* R, double* Rn,
-               float* res32, double* dmax, long long* kernels, cudaStream_t s) {
+int ppr64_step(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, const double* rhs,
+               const int32_t* srow, const double* R, double* Rn, float* res32, double* dmax, long long* kernels,
+               cudaStream_t s) {
   PRDF_TRY(g->resid.reserve(2, s));
   PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t), s));
   Ppr64Args a;
@@ -889,7 +900,8 @@ int ppr64_step(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int ti
   a.P = op.p64;
   a.R = R;
   a.Rn = Rn;
-  a.S = op.S64;
+  a.S = rhs;
+  a.srow = srow;
   a.res32 = res32;
   a.K = K;
   a.alpha = p->alpha;
@@ -918,12 +930,20 @@ struct KSolve {
 int ksolve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, double** out, KSolve* r,
            cudaStream_t s) {
   const int64_t cnt = (int64_t)g->n * K;
+  PprSparseRhs& sp = g->ppr_rhs;
+  sp.rows = 0;
   if (p->precision == PRDF_FP64) {
     PRDF_CUDA(cudaMemcpyAsync(g->R64a.p, op.S64, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s));
+    if (op.sparse_rhs) {
+      PRDF_TRY(ppr_sparse_rhs(op.S64, g->n, K, g->ws, &sp, nullptr, s));
+      r->kernels += 2 + (sp.rows ? 1 : 0);
+    }
+    const double* rhs = sp.rows ? sp.Sc64.p : op.S64;
+    const int32_t* srow = sp.rows ? sp.srow.p : nullptr;
     double* a = g->R64a.p;
     double* b = g->R64b.p;
     for (int it = 0; it < p->max_iter; ++it) {
-      PRDF_TRY(ppr64_step(g, op, p, K, tile, a, b, nullptr, &r->dmax, &r->kernels, s));
+      PRDF_TRY(ppr64_step(g, op, p, K, tile, rhs, srow, a, b, nullptr, &r->dmax, &r->kernels, s));
       ++r->steps64;
       double* tmp = a;
       a = b;
@@ -939,18 +959,29 @@ int ksolve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, 
   PRDF_TRY(g->S32.reserve(cnt, s));
   PRDF_TRY(g->R32a.reserve(cnt, s));
   PRDF_TRY(g->R32b.reserve(cnt, s));
-  PRDF_TRY(ppr_narrow(op.S64, cnt, g->S32.p, s));
-  PRDF_CUDA(cudaMemcpyAsync(g->R32a.p, g->S32.p, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s));
+  if (op.sparse_rhs) {
+    // a teleport on few vertices: the first solve reads a 4-byte row index per vertex instead of its row
+    PRDF_TRY(ppr_sparse_rhs(op.S64, g->n, K, g->ws, &sp, g->R32a.p, s));
+    r->kernels += 2 + (sp.rows ? 1 : 0);
+  }
+  const double* rhs64 = sp.rows ? sp.Sc64.p : op.S64;
+  const int32_t* srow = sp.rows ? sp.srow.p : nullptr;
+  if (!sp.rows) {
+    PRDF_TRY(ppr_narrow(op.S64, cnt, g->S32.p, s));
+    PRDF_CUDA(cudaMemcpyAsync(g->R32a.p, g->S32.p, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s));
+  }
   float* cur = g->R32a.p;
   float* oth = g->R32b.p;
   int it32 = 0;
-  PRDF_TRY(ppr32_solve(g, op, p, K, tile, g->S32.p, &cur, &oth, p->max_iter, &it32, &r->kernels, s));
+  PRDF_TRY(ppr32_solve(g, op, p, K, tile, sp.rows ? sp.Sc32.p : g->S32.p, srow, &cur, &oth, p->max_iter, &it32,
+                       &r->kernels, s));
   r->iters32 += it32;
   PRDF_TRY(ppr_widen(cur, cnt, g->R64a.p, s));
   r->kernels += 2;
   const int kRounds = 8;
   for (int round = 0; round < kRounds; ++round) {
-    PRDF_TRY(ppr64_step(g, op, p, K, tile, g->R64a.p, g->R64b.p, g->S32.p, &r->dmax, &r->kernels, s));
+    // FP64 Jacobi step: T(R) and the residual (T(R) - R) / (1 - alpha), dense, in S32
+    PRDF_TRY(ppr64_step(g, op, p, K, tile, rhs64, srow, g->R64a.p, g->R64b.p, g->S32.p, &r->dmax, &r->kernels, s));
     ++r->steps64;
     if (r->dmax <= p->tol) {
       r->converged = 1;
@@ -959,7 +990,7 @@ int ksolve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, 
     PRDF_CUDA(cudaMemcpyAsync(g->R32a.p, g->S32.p, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s));
     cur = g->R32a.p;
     oth = g->R32b.p;
-    PRDF_TRY(ppr32_solve(g, op, p, K, tile, g->S32.p, &cur, &oth, p->max_iter, &it32, &r->kernels, s));
+    PRDF_TRY(ppr32_solve(g, op, p, K, tile, g->S32.p, nullptr, &cur, &oth, p->max_iter, &it32, &r->kernels, s));
     r->iters32 += it32;
     PRDF_TRY(ppr_add_correction(g->R64a.p, cur, cnt, s));
     r->kernels += 1;
@@ -1580,7 +1611,7 @@ int prdf_pagerank_ppr(prdf_graph* g, const double* S, int K, double* R, const pr
   PRDF_LAUNCH_CHECK();
   PRDF_CUDA(cudaEventRecord(t.e[1], s));
   PRDF_TRY(ensure_hub(g, g->rl.in, g->hub_in, s));
-  const KOp op{g->rl.in.off.p, g->rl.in.adj.p, g->pin32.p, g->pin64.p, hub_begin(g->rl), &g->hub_in, g->S64.p};
+  const KOp op{g->rl.in.off.p, g->rl.in.adj.p, g->pin32.p, g->pin64.p, hub_begin(g->rl), &g->hub_in, g->S64.p, true};
   KSolve ks;
   ks.kernels = 1;
   double* Rfinal = nullptr;
@@ -1676,7 +1707,8 @@ int prdf_pagerank_backward(prdf_graph* g, const double* R, const double* G, int 
   PRDF_LAUNCH_CHECK();
   PRDF_CUDA(cudaEventRecord(t.e[1], s));
   PRDF_TRY(ensure_hub(g, g->rl.out, g->hub_out, s));
-  const KOp op{g->rl.out.off.p, g->rl.out.adj.p, g->pout32.p, g->pout64.p, hub_begin(g->rl), &g->hub_out, g->S64.p};
+  const KOp op{g->rl.out.off.p, g->rl.out.adj.p, g->pout32.p, g->pout64.p, hub_begin(g->rl), &g->hub_out, g->S64.p,
+               false};
   KSolve ks;
   ks.kernels = 1;
   double* lam = nullptr;

@@ -58,18 +58,6 @@ __device__ __forceinline__ bool pull_chosen(const unsigned long long* fw, unsign
   return fw && *fw > fthr;
 }
 
-// out-edges of the frontier: sum of |out(u)| over u with dN[u] set
-__global__ void k_frontier_edges(const uint8_t* __restrict__ dN, const int64_t* __restrict__ off, int64_t n,
-                                 unsigned long long* fw_base, const Stop st) {
-  if (converged(st)) return;
-  unsigned long long* fw = const_cast<unsigned long long*>(round_fw(fw_base, st));
-  int64_t c = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (dN[i]) c += off[i + 1] - off[i];
-  c = warp_sum_i64(c);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(fw, (unsigned long long)c);
-}
-
 // Pull form of one expansion round over G' (the same marks as the push form,
 // since w is an out-neighbour of u exactly when u is an in-neighbour of w): a
 // vertex outside dV joins it when an in-neighbour is in the frontier. Only
@@ -224,11 +212,10 @@ int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, cons
   return PRDF_OK;
 }
 
-int launch_expand_pull(const int64_t* in_off, const int32_t* in_adj, const int64_t* out_off, int64_t n,
-                       int64_t warp_begin, const uint8_t* dN, uint8_t* dV, unsigned long long* fw,
-                       unsigned long long fthr, const Stop& st, cudaStream_t s) {
+int launch_expand_pull(const int64_t* in_off, const int32_t* in_adj, int64_t n, int64_t warp_begin,
+                       const uint8_t* dN, uint8_t* dV, const unsigned long long* fw, unsigned long long fthr,
+                       const Stop& st, cudaStream_t s) {
   const int maxg = kSMs * 8;
-  k_frontier_edges<<<grid_for(n, kThreads, kSMs * 4), kThreads, 0, s>>>(dN, out_off, n, fw, st);
   if (warp_begin > 0)
     k_pull_thread<<<grid_for(warp_begin, kThreads, maxg), kThreads, 0, s>>>(in_off, in_adj, 0, warp_begin, dN, dV, fw,
                                                                             fthr, st);

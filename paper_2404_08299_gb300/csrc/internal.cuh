@@ -117,6 +117,8 @@ struct SweepArgs {
   uint8_t* wrote;          // 1 where this vertex's slot in xn was written by the previous sweep
   double tau_f, tau_p;
   int prune;               // DF-P (Eq. 2, prune) or DF (Eq. 1)
+  unsigned long long* fw;  // null, or: += out-edges of the vertices this sweep puts into deltaN
+  unsigned long long* fw_base;  // graph-driven loop: fw of iteration it is fw_base + it
   // Static: chunks of the highest in-degree class's rows (nchunk = 0: none)
   // and one partial sum per chunk (4 words)
   PprHub hub;
@@ -151,6 +153,12 @@ struct Sweep32Args {
   uint8_t* wrote;
   float tau_f, tau_p;
   int prune;
+  unsigned long long* fw;       // as in SweepArgs
+  unsigned long long* fw_base;
+  // chunks of the highest in-degree class's rows (nchunk = 0: a block per row)
+  // and one compensated partial sum (s, e) per chunk
+  PprHub hub;
+  float2* hub_part;
 };
 int launch_sweep32(const Sweep32Args& a, const PartThr& t, const int64_t* class_begin, bool dynamic, cudaStream_t s);
 // One-thread check of the graph-driven FP32 loop: it = ctl[0]; stop when
@@ -166,6 +174,7 @@ struct Ppr32Args {
   const float* R;          // current [n, K]
   float* Rn;               // next [n, K]
   const float* S;          // right-hand side [n, K] (teleport, or residual / (1 - alpha))
+  const int32_t* srow;     // null: S is dense; else S holds compact rows and row v is S[srow[v]] (-1: zero)
   int K;
   float alpha, beta;       // alpha, 1 - alpha
   uint32_t* resid;         // [0] max |R_new - R|, [1] max |R_new| (FP32 bits, atomic max)
@@ -178,7 +187,8 @@ struct Ppr64Args {
   const double* P;
   const double* R;
   double* Rn;              // T(R)
-  const double* S;
+  const double* S;         // right-hand side, dense or compact rows as in Ppr32Args
+  const int32_t* srow;
   float* res32;            // (T(R) - R) / (1 - alpha) in FP32, or null
   int K;
   double alpha, beta, inv_beta;
@@ -205,6 +215,19 @@ int launch_ppr32_sweep(const Ppr32Args& a, int tile, int64_t n, int64_t hub_begi
 // sweep (part: h.nchunk * tile doubles of scratch).
 int launch_ppr64_step(const Ppr64Args& a, int tile, int64_t n, int64_t hub_begin, const PprHub& h, double* part,
                       cudaStream_t s);
+// Sparse teleport: the rows of S (double [n, K]) with a non-zero entry. When
+// at most n / 4 rows are non-zero, srow[v] gets v's compact row (-1 for none),
+// Sc64 / Sc32 the rows in FP64 / FP32, R32 (float [n, K]) the FP32 matrix
+// (the iteration's start R = S) and rows their count; otherwise rows = 0 and
+// the dense form is kept. Sweeps then read 4 bytes per vertex instead of the
+// vertex's whole teleport row.
+struct PprSparseRhs {
+  int64_t rows = 0;
+  DBuf<int32_t> srow;
+  DBuf<double> Sc64;
+  DBuf<float> Sc32;
+};
+int ppr_sparse_rhs(const double* S, int64_t n, int K, Workspace& ws, PprSparseRhs* out, float* R32, cudaStream_t s);
 int ppr_add_correction(double* R, const float* E, int64_t cnt, cudaStream_t s);
 int launch_grad_w(const int64_t* off, const int32_t* adj, const int32_t* perm, const int64_t* orig_off,
                   const double* lam, const double* Gs, double g_scale, const double* Rr, const double* W, int32_t n,
@@ -247,11 +270,11 @@ int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, cons
                   const uint8_t* dN, uint8_t* dV, uint8_t* dF, const Stop& st, cudaStream_t s,
                   const unsigned long long* fw = nullptr, unsigned long long fthr = 0);
 // The same round in pull form over G' (in_off/in_adj; rows from warp_begin on
-// take a warp each): first sums the frontier's out-edges into *fw (zero on
-// entry; out_off is G's offsets), then marks only if *fw > fthr.
-int launch_expand_pull(const int64_t* in_off, const int32_t* in_adj, const int64_t* out_off, int64_t n,
-                       int64_t warp_begin, const uint8_t* dN, uint8_t* dV, unsigned long long* fw,
-                       unsigned long long fthr, const Stop& st, cudaStream_t s);
+// take a warp each): marks only if *fw, the frontier's out-edges (counted by
+// the sweep before it), exceeds fthr.
+int launch_expand_pull(const int64_t* in_off, const int32_t* in_adj, int64_t n, int64_t warp_begin,
+                       const uint8_t* dN, uint8_t* dV, const unsigned long long* fw, unsigned long long fthr,
+                       const Stop& st, cudaStream_t s);
 int count_flags(const uint8_t* f, int64_t n, unsigned long long* dev_out, cudaStream_t s);
 
 }  // namespace prdf
@@ -273,7 +296,8 @@ struct prdf_graph {
   // solver scratch
   prdf::DBuf<double> xa, xb;
   prdf::PprHubTable hub_in, hub_out;  // chunk tables of G' (Static sweep, K-column forward) and G (adjoint)
-  prdf::DBuf<uint4> sweep_hub_part;   // Static sweep: one exact partial sum per chunk of G's hub rows
+  prdf::DBuf<uint4> sweep_hub_part;   // FP64 sweeps: one exact partial sum per chunk of G's hub rows
+  prdf::DBuf<float2> sweep_hub_part32;  // FP32 sweeps: one compensated partial sum per chunk
   prdf::DBuf<float2> ppr_part;        // chunk partial sums of one column tile (FP32 sweeps)
   prdf::DBuf<double> ppr_part64;      // chunk partial sums of one column tile (FP64 steps)
   prdf::DBuf<float> ya, yb, degf, invf;  // FP32 stage state and degrees (class-contiguous numbering)
@@ -302,6 +326,7 @@ struct prdf_graph {
   prdf::DBuf<float> pout32;
   // K-column scratch
   prdf::DBuf<double> S64, R64a, R64b;
+  prdf::PprSparseRhs ppr_rhs;        // compact teleport rows of the last forward call (rows = 0: dense)
   prdf::DBuf<float> S32, R32a, R32b;
 };
 

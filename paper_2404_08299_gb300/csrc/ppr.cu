@@ -127,15 +127,20 @@ __device__ __forceinline__ Own4 ppr32_own(const Ppr32Args& a, int32_t v, int col
   for (int q = 0; q < 4; ++q) w.s[q] = w.o[q] = 0.f;
   if (col >= a.K) return w;
   const int64_t o = (int64_t)v * a.K + col;
+  // right-hand side row: dense, or (srow) the compact row of v, none when v has no teleport mass
+  const int64_t sr = a.srow ? (int64_t)a.srow[v] : (int64_t)v;
+  const float* S = sr >= 0 ? a.S + sr * a.K + col : nullptr;
   if ((a.K & 3) == 0) {
-    const float4 s4 = *reinterpret_cast<const float4*>(a.S + o);
     const float4 o4 = *reinterpret_cast<const float4*>(a.R + o);
-    w.s[0] = s4.x; w.s[1] = s4.y; w.s[2] = s4.z; w.s[3] = s4.w;
     w.o[0] = o4.x; w.o[1] = o4.y; w.o[2] = o4.z; w.o[3] = o4.w;
+    if (S) {
+      const float4 s4 = *reinterpret_cast<const float4*>(S);
+      w.s[0] = s4.x; w.s[1] = s4.y; w.s[2] = s4.z; w.s[3] = s4.w;
+    }
   } else {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      w.s[q] = col + q < a.K ? a.S[o + q] : 0.f;
+      w.s[q] = (S && col + q < a.K) ? S[q] : 0.f;
       w.o[q] = col + q < a.K ? a.R[o + q] : 0.f;
     }
   }
@@ -411,11 +416,13 @@ __device__ __forceinline__ void ppr64_edges(const Ppr64Args& a, int64_t j0, int6
 // T(R), residual and |T(R) - R| for the 4 columns of vertex v
 __device__ __forceinline__ void ppr64_finish4(const Ppr64Args& a, int32_t v, int col, const double* acc,
                                               uint64_t& dmax) {
+  const int64_t sr = a.srow ? (int64_t)a.srow[v] : (int64_t)v;  // as in ppr32_own
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     if (col + q >= a.K) break;
     const int64_t o = (int64_t)v * a.K + col + q;
-    const double t = fma(a.alpha, acc[q], a.beta * a.S[o]);
+    const double sv = sr >= 0 ? a.S[sr * a.K + col + q] : 0.0;
+    const double t = fma(a.alpha, acc[q], a.beta * sv);
     const double d = t - a.R[o];
     a.Rn[o] = t;
     if (a.res32) a.res32[o] = (float)(d * a.inv_beta);
@@ -569,6 +576,41 @@ __global__ void k_grad_w(const int64_t* __restrict__ off, const int32_t* __restr
 }
 
 // R64 += (double) E32
+// rows of a [n, K] matrix with a non-zero entry (flag per row)
+__global__ void k_row_nonzero(const double* __restrict__ S, int64_t n, int K, uint32_t* __restrict__ flag) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    bool nz = false;
+    for (int c = lane; c < K; c += 32) nz = nz || S[v * K + c] != 0.0;
+    nz = __any_sync(0xffffffffu, nz);
+    if (lane == 0) flag[v] = nz ? 1u : 0u;
+  }
+}
+
+// srow[v] = compact row of v or -1; Sc64 / Sc32 (FP64 / FP32) get the non-zero rows, and R32 (zero on
+// entry) the FP32 rows at their place
+__global__ void k_row_compact(const double* __restrict__ S, int64_t n, int K, const uint32_t* __restrict__ flag,
+                              const int64_t* __restrict__ pos, int32_t* __restrict__ srow, double* __restrict__ Sc64,
+                              float* __restrict__ Sc32, float* __restrict__ R32) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const bool nz = flag[v] != 0;
+    const int64_t r = nz ? pos[v] : -1;
+    if (lane == 0) srow[v] = (int32_t)r;
+    if (!nz) continue;
+    for (int c = lane; c < K; c += 32) {
+      const double x = S[v * K + c];
+      Sc64[r * K + c] = x;
+      Sc32[r * K + c] = (float)x;
+      if (R32) R32[v * K + c] = (float)x;
+    }
+  }
+}
+
 __global__ void k_add_correction(double* __restrict__ R, const float* __restrict__ E, int64_t cnt) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
     R[i] += (double)E[i];
@@ -669,6 +711,30 @@ int launch_grad_w(const int64_t* off, const int32_t* adj, const int32_t* perm, c
   k_grad_w<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(off, adj, perm, orig_off, lam, Gs, g_scale, Rr, W, n,
                                                                      K, alpha, grad_w);
   PRDF_LAUNCH_CHECK();
+  return PRDF_OK;
+}
+
+int ppr_sparse_rhs(const double* S, int64_t n, int K, Workspace& ws, PprSparseRhs* out, float* R32, cudaStream_t s) {
+  out->rows = 0;
+  DBuf<uint32_t> flag;
+  DBuf<int64_t> pos;
+  PRDF_TRY(flag.alloc((size_t)n, s));
+  PRDF_TRY(pos.alloc((size_t)n + 1, s));
+  k_row_nonzero<<<grid_for(n * 32, kThreads), kThreads, 0, s>>>(S, n, K, flag.p);
+  PRDF_LAUNCH_CHECK();
+  PRDF_TRY(exclusive_scan_u32(flag.p, n, pos.p, ws, s));
+  PRDF_CUDA(cudaMemcpyAsync(ws.host_i64, pos.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PRDF_CUDA(cudaStreamSynchronize(s));
+  const int64_t rows = ws.host_i64[0];
+  if (rows * 4 > n) return PRDF_OK;  // dense enough: keep the dense form
+  PRDF_TRY(out->srow.reserve((size_t)n, s));
+  PRDF_TRY(out->Sc64.reserve((size_t)(rows > 0 ? rows : 1) * K, s));
+  PRDF_TRY(out->Sc32.reserve((size_t)(rows > 0 ? rows : 1) * K, s));
+  if (R32) PRDF_CUDA(cudaMemsetAsync(R32, 0, sizeof(float) * (size_t)n * K, s));
+  k_row_compact<<<grid_for(n * 32, kThreads), kThreads, 0, s>>>(S, n, K, flag.p, pos.p, out->srow.p, out->Sc64.p,
+                                                                out->Sc32.p, R32);
+  PRDF_LAUNCH_CHECK();
+  out->rows = rows;
   return PRDF_OK;
 }
 

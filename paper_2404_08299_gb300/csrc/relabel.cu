@@ -186,7 +186,11 @@ int build_relabelled(prdf_graph* g, cudaStream_t s) {
   PRDF_LAUNCH_CHECK();
   r.kf_alpha = -1;
   r.valid = true;
-  r.pout_valid = false;
+  // the out-degree partition of the marking kernels (Alg. partition over G) is
+  // made with the numbering, so that DF / DF-P / DT find it ready after a batch
+  PRDF_TRY(r.pout.reserve((size_t)n, s));
+  PRDF_TRY(partition_by_degree(r.out.off.p, n, g->thr[PRDF_OUT], r.pout.p, r.pout_count, g->ws, s));
+  r.pout_valid = true;
   ++r.version;
   g->ppr_valid = false;
   return PRDF_OK;

@@ -203,7 +203,7 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
 // Static path.
 template <bool DYN>
 __device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v, double c, uint64_t xself_b,
-                                                  uint64_t pf) {
+                                                  uint64_t pf, uint64_t& fwsum) {
   const double xself = bitsd(xself_b);
   const double d = ld_stream_f64(a.degd + v, pf);
   double r;
@@ -219,9 +219,14 @@ __device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v,
     const double rold = xself * d;
     const double m = fmax(r, rold);
     if (a.prune && dr <= a.tau_p * m) a.dV[v] = 0;
-    // deltaN holds exactly this sweep's expand set: set or cleared for every vertex
-    if (dr > a.tau_f * m) a.dN[v] = 1;
-    else if (a.dN[v]) a.dN[v] = 0;
+    // deltaN holds exactly this sweep's expand set: set or cleared for every vertex; the out-edges of
+    // the set are counted for the choice of the expansion round's direction
+    if (dr > a.tau_f * m) {
+      a.dN[v] = 1;
+      fwsum += (uint64_t)d;
+    } else if (a.dN[v]) {
+      a.dN[v] = 0;
+    }
     a.wrote[v] = 1;
   }
   a.xn[v] = r * ld_stream_f64(a.inv_deg + v, pf);
@@ -237,6 +242,7 @@ __device__ __forceinline__ SweepArgs resolve(const SweepArgs& in) {
   a.xn = (it & 1) ? const_cast<double*>(in.xa) : in.xb;
   a.resid = in.resid_base + it;
   a.prev = it > 0 ? in.resid_base + it - 1 : nullptr;
+  a.fw = in.fw_base ? in.fw_base + it : nullptr;
   return a;
 }
 
@@ -275,6 +281,26 @@ __device__ __forceinline__ void block_max_to(uint64_t dmax, uint64_t* out) {
   }
 }
 
+// Sweep epilogue of a block: the L-inf change (max) and, for DF / DF-P, the
+// out-edges of the vertices put into deltaN (sum, when fw is given).
+template <bool DYN>
+__device__ __forceinline__ void block_epilogue(const SweepArgs& a, uint64_t dmax, uint64_t fwsum) {
+  block_max_to(dmax, a.resid);
+  if (DYN && a.fw) {
+    __shared__ uint64_t shs[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    fwsum = (uint64_t)warp_sum_i64((int64_t)fwsum);
+    __syncthreads();  // shs is written after every warp left block_max_to's shared reads
+    if (lane == 0) shs[wid] = fwsum;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t x = lane < (int)(blockDim.x >> 5) ? shs[lane] : 0;
+      x = (uint64_t)warp_sum_i64((int64_t)x);
+      if (lane == 0 && x) atomicAdd((unsigned long long*)a.fw, (unsigned long long)x);
+    }
+  }
+}
+
 // Work item of a group: list entry, vertex, its row of G' and the first
 // G*U indices of the row (this lane's share).
 template <int U>
@@ -303,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, 
   const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   const int64_t step = nwarps * kGroupsPerWarp;
-  uint64_t dmax = 0;
+  uint64_t dmax = 0, fwsum = 0;
 
   auto load_v = [&](int64_t i) -> int32_t { return i < end ? (int32_t)i : -1; };
   // DF / DF-P: the row of an unaffected vertex is not read (its flag can
@@ -379,12 +405,12 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, 
       }
     }
     if (active && lane == 0) {
-      const uint64_t db = finish_vertex<DYN>(a, cur.v, acc.value(), xself, pf);
+      const uint64_t db = finish_vertex<DYN>(a, cur.v, acc.value(), xself, pf, fwsum);
       dmax = db > dmax ? db : dmax;
     }
     cur = nxt;
   }
-  block_max_to(dmax, a.resid);
+  block_epilogue<DYN>(a, dmax, fwsum);
 }
 
 // one warp per vertex, 16-byte index loads; the next vertex's list entry and
@@ -397,7 +423,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_warp(const SweepArgs a_in, i
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-  uint64_t dmax = 0;
+  uint64_t dmax = 0, fwsum = 0;
   int64_t i = begin + warp;
   int32_t v = i < end ? (int32_t)i : -1;
   int64_t b = v >= 0 ? ld_stream_i64(a.off + v, pf) : 0, e = v >= 0 ? ld_stream_i64(a.off + v + 1, pf) : 0;
@@ -413,14 +439,14 @@ __global__ void __launch_bounds__(kThreads) k_sweep_warp(const SweepArgs a_in, i
     const int64_t bn = vn >= 0 ? ld_stream_i64(a.off + vn, pf) : 0, en = vn >= 0 ? ld_stream_i64(a.off + vn + 1, pf) : 0;
     acc.template group_reduce<32>();
     if (active && lane == 0) {
-      const uint64_t db = finish_vertex<DYN>(a, v, acc.value(), xself, pf);
+      const uint64_t db = finish_vertex<DYN>(a, v, acc.value(), xself, pf, fwsum);
       dmax = db > dmax ? db : dmax;
     }
     v = vn;
     b = bn;
     e = en;
   }
-  block_max_to(dmax, a.resid);
+  block_epilogue<DYN>(a, dmax, fwsum);
 }
 
 // one block per vertex (high in-degree)
@@ -431,7 +457,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a_in, 
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
   __shared__ uint32_t s_acc[kThreads / 32][4];
   __shared__ int s_skip;
-  uint64_t dmax = 0;
+  uint64_t dmax = 0, fwsum = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
     const int32_t v = (int32_t)i;
@@ -453,20 +479,23 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a_in, 
     if (threadIdx.x == 0) {
       Acc<EXACT> tot;
       for (int k = 0; k < kThreads / 32; ++k) tot.from_shared(s_acc[k]);
-      const uint64_t db = finish_vertex<DYN>(a, v, tot.value(), xb, pf);
+      const uint64_t db = finish_vertex<DYN>(a, v, tot.value(), xb, pf, fwsum);
       dmax = db > dmax ? db : dmax;
     }
     __syncthreads();
   }
-  block_max_to(dmax, a.resid);
+  block_epilogue<DYN>(a, dmax, fwsum);
 }
 
-// Static: rows of the highest in-degree class in 1024-edge chunks (the hub
-// chunk table). A warp per chunk sums the chunk's terms and stores the partial
-// sum; a thread per hub vertex adds its chunks' partials and finishes the
-// vertex. With exact accumulation the partials are integers, so the result is
-// the same bits as any other split; long rows no longer serialise on one block.
-template <bool EXACT>
+// Rows of the highest in-degree class in 1024-edge chunks (the hub chunk
+// table). A warp per chunk sums the chunk's terms and stores the partial sum;
+// a warp per hub vertex adds its chunks' partials and finishes the vertex.
+// With exact accumulation the partials are integers, so the result is the
+// same bits as any other split; long rows no longer serialise on one block.
+// DF / DF-P: chunks of unaffected hubs are skipped; the finishing warp copies
+// an unaffected hub through. A hub's flag changes only in its finishing warp,
+// which runs after every chunk of the sweep has read it.
+template <bool EXACT, bool DYN>
 __global__ void __launch_bounds__(kThreads) k_sweep_hub_part(const SweepArgs a_in) {
   const SweepArgs a = resolve(a_in);
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
@@ -476,6 +505,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_hub_part(const SweepArgs a_i
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   for (int64_t c = warp; c < a.hub.nchunk; c += nwarps) {
     const int32_t v = (int32_t)(a.hub.begin + a.hub.chunk_hub[c]);
+    if (DYN && !a.dV[v]) continue;  // the same flag on every lane
     const int64_t jb = a.hub.chunk_j0[c];
     const int64_t re = a.off[v + 1];
     const int64_t je = jb + kHubChunk < re ? jb + kHubChunk : re;
@@ -487,7 +517,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_hub_part(const SweepArgs a_i
   }
 }
 
-template <bool EXACT>
+template <bool EXACT, bool DYN>
 __global__ void __launch_bounds__(kThreads) k_sweep_hub_finish(const SweepArgs a_in) {
   const SweepArgs a = resolve(a_in);
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
@@ -495,20 +525,28 @@ __global__ void __launch_bounds__(kThreads) k_sweep_hub_finish(const SweepArgs a
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-  uint64_t dmax = 0;
+  uint64_t dmax = 0, fwsum = 0;
   // a warp per hub vertex: lanes add strided chunk partials, then the warp reduces
   for (int64_t h = warp; h < a.hub.nhub; h += nwarps) {
     const int32_t v = (int32_t)(a.hub.begin + h);
+    if (DYN) {
+      // every lane reads the flag before lane 0 may change it
+      const bool skip = __shfl_sync(0xffffffffu, lane == 0 ? (int)(a.dV[v] == 0) : 0, 0) != 0;
+      if (skip) {
+        if (lane == 0) skip_unaffected(a, v);
+        continue;
+      }
+    }
     Acc<EXACT> tot;
     for (int64_t c = a.hub.hub_first[h] + lane; c < a.hub.hub_first[h + 1]; c += 32)
       tot.from_shared(reinterpret_cast<const uint32_t*>(a.hub_part + c));
     tot.template group_reduce<32>();
     if (lane == 0) {
-      const uint64_t db = finish_vertex<false>(a, v, tot.value(), ld_gather_b64(a.x + v, pl), pf);
+      const uint64_t db = finish_vertex<DYN>(a, v, tot.value(), ld_gather_b64(a.x + v, pl), pf, fwsum);
       dmax = db > dmax ? db : dmax;
     }
   }
-  block_max_to(dmax, a.resid);
+  block_epilogue<DYN>(a, dmax, fwsum);
 }
 
 // Kernel shape of class c: the last class is block-per-vertex, the one before
@@ -548,7 +586,7 @@ bool prefer_l1_all() {
   prefer_l1(k_sweep_group<16, 8, EXACT, DYN, false>);
   prefer_l1(k_sweep_warp<2, EXACT, DYN>);
   prefer_l1(k_sweep_block<4, EXACT, DYN>);
-  prefer_l1(k_sweep_hub_part<EXACT>);
+  prefer_l1(k_sweep_hub_part<EXACT, DYN>);
   return true;
 }
 
@@ -577,9 +615,9 @@ int launch_all(const SweepArgs& a, const PartThr& t, const int64_t* cb, cudaStre
       case kG16U8: k_sweep_group<16, 8, EXACT, DYN, false><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kWarp: k_sweep_warp<2, EXACT, DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       default:
-        if (!DYN && a.hub.nchunk > 0 && a.hub.begin == b && a.hub.nhub == cnt && a.hub_part) {
-          k_sweep_hub_part<EXACT><<<grid_for(a.hub.nchunk * 32, kThreads, maxg), kThreads, 0, s>>>(a);
-          k_sweep_hub_finish<EXACT><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a);
+        if (a.hub.nchunk > 0 && a.hub.begin == b && a.hub.nhub == cnt && a.hub_part) {
+          k_sweep_hub_part<EXACT, DYN><<<grid_for(a.hub.nchunk * 32, kThreads, maxg), kThreads, 0, s>>>(a);
+          k_sweep_hub_finish<EXACT, DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a);
         } else {
           k_sweep_block<4, EXACT, DYN><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e);
         }

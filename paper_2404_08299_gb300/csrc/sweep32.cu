@@ -127,7 +127,7 @@ __device__ __forceinline__ void gather32_vec(const Sweep32Args& a, int64_t b, in
 // bit patterns
 template <bool DYN>
 __device__ __forceinline__ void finish32(const Sweep32Args& a, int32_t v, float c, uint32_t yself_b, uint64_t pf,
-                                        uint32_t& db, uint32_t& rb) {
+                                        uint32_t& db, uint32_t& rb, uint64_t& fwsum) {
   const float d = ld_stream_f32(a.degf + v, pf);
   const float yself = __uint_as_float(yself_b);
   const float rold = yself * d;
@@ -138,8 +138,12 @@ __device__ __forceinline__ void finish32(const Sweep32Args& a, int32_t v, float 
   if (DYN) {
     const float m = fmaxf(r, rold);
     if (a.prune && dr <= a.tau_p * m) a.dV[v] = 0;
-    if (dr > a.tau_f * m) a.dN[v] = 1;
-    else if (a.dN[v]) a.dN[v] = 0;
+    if (dr > a.tau_f * m) {
+      a.dN[v] = 1;
+      fwsum += (uint64_t)d;
+    } else if (a.dN[v]) {
+      a.dN[v] = 0;
+    }
     a.wrote[v] = 1;
   }
   a.yn[v] = r * ld_stream_f32(a.invf + v, pf);
@@ -168,6 +172,7 @@ __device__ __forceinline__ Sweep32Args resolve32(const Sweep32Args& in) {
   a.yn = (it & 1) ? const_cast<float*>(in.ya) : in.yb;
   a.resid = in.resid_base + 2 * it;
   a.prev = it > 0 ? in.resid_base + 2 * (it - 1) : nullptr;
+  a.fw = in.fw_base ? in.fw_base + it : nullptr;
   return a;
 }
 
@@ -214,6 +219,24 @@ __device__ __forceinline__ void block_max2_to(uint32_t dmax, uint32_t rmax, uint
   }
 }
 
+// block epilogue: the pair (max |dR|, max R) and, for DF / DF-P, the out-edges of the new deltaN
+template <bool DYN>
+__device__ __forceinline__ void block_epilogue32(const Sweep32Args& a, uint32_t dmax, uint32_t rmax, uint64_t fwsum) {
+  block_max2_to(dmax, rmax, a.resid);
+  if (DYN && a.fw) {
+    __shared__ uint64_t shs[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    fwsum = (uint64_t)warp_sum_i64((int64_t)fwsum);
+    if (lane == 0) shs[wid] = fwsum;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t x = lane < (int)(blockDim.x >> 5) ? shs[lane] : 0;
+      x = (uint64_t)warp_sum_i64((int64_t)x);
+      if (lane == 0 && x) atomicAdd((unsigned long long*)a.fw, (unsigned long long)x);
+    }
+  }
+}
+
 template <int G, int U, bool SELF1, bool DYN>
 __global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a_in, int64_t begin, int64_t end) {
   const Sweep32Args a = resolve32(a_in);
@@ -225,6 +248,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a_
   const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   uint32_t dmax = 0, rmax = 0;
+  uint64_t fwsum = 0;
   for (int64_t base = begin + warp * kGroupsPerWarp; base < end; base += nwarps * kGroupsPerWarp) {
     const int64_t i = base + gw;
     bool active = i < end;
@@ -250,12 +274,12 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a_
     }
     if (active && lane == 0) {
       uint32_t db, rb;
-      finish32<DYN>(a, v, acc.value(), yself, pf, db, rb);
+      finish32<DYN>(a, v, acc.value(), yself, pf, db, rb, fwsum);
       dmax = max(dmax, db);
       rmax = max(rmax, rb);
     }
   }
-  block_max2_to(dmax, rmax, a.resid);
+  block_epilogue32<DYN>(a, dmax, rmax, fwsum);
 }
 
 template <int KV, bool DYN>
@@ -267,6 +291,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_warp(const Sweep32Args a_i
   const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   uint32_t dmax = 0, rmax = 0;
+  uint64_t fwsum = 0;
   for (int64_t i = begin + warp; i < end; i += nwarps) {
     const int32_t v = (int32_t)i;
     // the flag is the same for the whole warp; lane 0 alone changes it, after the shuffles below
@@ -283,12 +308,12 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_warp(const Sweep32Args a_i
     for (int o = 16; o > 0; o >>= 1) yself = max(yself, __shfl_xor_sync(0xffffffffu, yself, o));
     if (lane == 0) {
       uint32_t db, rb;
-      finish32<DYN>(a, v, acc.value(), yself, pf, db, rb);
+      finish32<DYN>(a, v, acc.value(), yself, pf, db, rb, fwsum);
       dmax = max(dmax, db);
       rmax = max(rmax, rb);
     }
   }
-  block_max2_to(dmax, rmax, a.resid);
+  block_epilogue32<DYN>(a, dmax, rmax, fwsum);
 }
 
 template <int KV, bool DYN>
@@ -301,6 +326,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_block(const Sweep32Args a_
   __shared__ int s_skip;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t dmax = 0, rmax = 0;
+  uint64_t fwsum = 0;
   for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
     const int32_t v = (int32_t)i;
     if (DYN) {
@@ -331,13 +357,77 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_block(const Sweep32Args a_
         ym = max(ym, s_y[k]);
       }
       uint32_t db, rb;
-      finish32<DYN>(a, v, tot.value(), ym, pf, db, rb);
+      finish32<DYN>(a, v, tot.value(), ym, pf, db, rb, fwsum);
       dmax = max(dmax, db);
       rmax = max(rmax, rb);
     }
     __syncthreads();
   }
-  block_max2_to(dmax, rmax, a.resid);
+  block_epilogue32<DYN>(a, dmax, rmax, fwsum);
+}
+
+// Rows of the highest in-degree class in 1024-edge chunks (the hub chunk
+// table): a warp per chunk stores the chunk's compensated sum (s, e); a warp
+// per hub vertex merges its chunks' sums, lanes striding over the chunks and
+// a fixed shuffle tree after them, so every run gives the same bits. Long
+// rows no longer serialise on one block. DF / DF-P skip unaffected hubs as
+// the FP64 hub kernels do.
+template <bool DYN>
+__global__ void __launch_bounds__(kThreads) k_sweep32_hub_part(const Sweep32Args a_in) {
+  const Sweep32Args a = resolve32(a_in);
+  if (converged32(a)) return;
+  const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  for (int64_t c = warp; c < a.hub.nchunk; c += nwarps) {
+    const int32_t v = (int32_t)(a.hub.begin + a.hub.chunk_hub[c]);
+    if (DYN && !a.dV[v]) continue;  // the same flag on every lane
+    const int64_t jb = a.hub.chunk_j0[c];
+    const int64_t re = a.off[v + 1];
+    const int64_t je = jb + kHubChunk < re ? jb + kHubChunk : re;
+    Kahan acc;
+    uint32_t unused = 0;
+    gather32_vec<32, 2>(a, jb, je, lane, v, acc, unused, pf, pl);
+    acc.template group_reduce<32>();
+    if (lane == 0) a.hub_part[c] = make_float2(acc.s, acc.e);
+  }
+}
+
+template <bool DYN>
+__global__ void __launch_bounds__(kThreads) k_sweep32_hub_finish(const Sweep32Args a_in) {
+  const Sweep32Args a = resolve32(a_in);
+  if (converged32(a)) return;
+  const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  uint32_t dmax = 0, rmax = 0;
+  uint64_t fwsum = 0;
+  for (int64_t h = warp; h < a.hub.nhub; h += nwarps) {
+    const int32_t v = (int32_t)(a.hub.begin + h);
+    if (DYN) {
+      // every lane reads the flag before lane 0 may change it
+      const bool skip = __shfl_sync(0xffffffffu, lane == 0 ? (int)(a.dV[v] == 0) : 0, 0) != 0;
+      if (skip) {
+        if (lane == 0) skip_unaffected32(a, v);
+        continue;
+      }
+    }
+    Kahan tot;
+    for (int64_t c = a.hub.hub_first[h] + lane; c < a.hub.hub_first[h + 1]; c += 32) {
+      const float2 x = a.hub_part[c];
+      tot.merge(x.x, x.y);
+    }
+    tot.template group_reduce<32>();
+    if (lane == 0) {
+      uint32_t db, rb;
+      finish32<DYN>(a, v, tot.value(), ld_gather_b32(a.y + v, pl), pf, db, rb, fwsum);
+      dmax = max(dmax, db);
+      rmax = max(rmax, rb);
+    }
+  }
+  block_epilogue32<DYN>(a, dmax, rmax, fwsum);
 }
 
 enum Kind32 { kT1 = 0, kT4, kG4, kG16, kWarp, kBlock };
@@ -373,7 +463,14 @@ int launch_all32(const Sweep32Args& a, const PartThr& t, const int64_t* cb, cuda
       case kG4: k_sweep32_group<4, 4, false, DYN><<<grid_for(cnt * 4, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kG16: k_sweep32_group<16, 8, false, DYN><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kWarp: k_sweep32_warp<2, DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      default: k_sweep32_block<4, DYN><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e); break;
+      default:
+        if (a.hub.nchunk > 0 && a.hub.begin == b && a.hub.nhub == cnt && a.hub_part) {
+          k_sweep32_hub_part<DYN><<<grid_for(a.hub.nchunk * 32, kThreads, maxg), kThreads, 0, s>>>(a);
+          k_sweep32_hub_finish<DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a);
+        } else {
+          k_sweep32_block<4, DYN><<<grid_for(cnt, 1, maxg), kThreads, 0, s>>>(a, b, e);
+        }
+        break;
     }
   }
   PRDF_LAUNCH_CHECK();

@@ -97,3 +97,27 @@ def test_autotune_tile_is_valid_and_consistent():
     R0, _ = g.pagerank_ppr(S, precision=0, tile=8)
     R1, _ = g.pagerank_ppr(S, precision=0, tile=tile)
     assert float((R1 - R0).abs().max()) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("extra_row", [0, 1])
+def test_ppr_compact_and_dense_teleport(precision, extra_row):
+    """A teleport with non-zero entries on at most n/4 vertices is read through a compact row table (a 4-byte
+    index per vertex instead of its whole row); one vertex more keeps the dense form. Both sides of the
+    switch meet L-inf 1e-8 against the oracle, and every column still sums to 1."""
+    n, g, og, w_out = weighted_case(11, 20000, seed=11)
+    K = 8
+    rows = np.arange(0, n, 4)[: n // 4]
+    if extra_row:
+        rows = np.concatenate([rows, [1]])
+    S = np.zeros((n, K))
+    S[rows, :] = synth.uniform((len(rows), K), seed=21) + 0.01
+    S[:, 3] = 0.0
+    S[rows[:5], 3] = 1.0  # a column on five seeds only
+    S /= S.sum(axis=0, keepdims=True)
+    R, st = g.pagerank_ppr(dev(S), precision=precision)
+    P = oracle.row_normalise(og, w_out)
+    Ro, _ = oracle.ppr(og, P, S, tol=1e-15, max_iter=1000)
+    assert np.max(np.abs(host(R) - Ro)) <= 1e-8
+    assert st.converged
+    assert np.max(np.abs(host(R).sum(axis=0) - 1.0)) <= 1e-8
