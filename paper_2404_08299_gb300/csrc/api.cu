@@ -511,8 +511,10 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
       a.dV = g->dV.p;
       a.dN = g->dN.p;
       a.wrote = g->wrote.p;
-      a.tau_f = p->tau_f;
-      a.tau_p = p->tau_p;
+      // + 0.0 turns a tolerance of -0 into +0: the sweep compares products with
+      // the tolerance by their bit patterns, which order -0 below +0
+      a.tau_f = p->tau_f + 0.0;
+      a.tau_p = p->tau_p + 0.0;
       a.prune = p->prune;
     }
   }

@@ -26,6 +26,12 @@ namespace prdf {
 namespace {
 
 constexpr int kThreads = 256;
+// four blocks of 256 threads per SM (64 registers a thread): the sweeps are
+// bound by the latency of their gathers, so resident warps matter more than
+// registers (at 70 registers a thread the DF-P warp kernel ran 3 blocks per SM
+// and took 1.5x the time of the same work at 64). The block-per-vertex kernel
+// and the 8-indices-per-lane group need more registers and keep three.
+constexpr int kMinBlocks = 4;
 
 // Exact accumulator (4 x 32-bit words, 2^-124 resolution) or plain FP64.
 template <bool EXACT>
@@ -198,12 +204,27 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
   }
 }
 
+// Exact integer value of an out-degree held as a double (an integer below
+// 2^53), decoded from its bit pattern on the integer pipes; 0 for 0.
+__device__ __forceinline__ uint64_t degree_of(double d) {
+  const uint64_t b = dbits(d);
+  const int e = (int)(b >> 52) - 1023;
+  const uint64_t mant = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+  return e >= 0 ? mant >> (52 - e) : 0ull;
+}
+
 // Vertex epilogue: Eq. 1 (Static, DF) or Eq. 2 (DF-P), prune / expand flags,
-// next x, and this vertex's |r - R[v]| as bits. Four FP64 instructions on the
-// Static path.
+// next x, and this vertex's |r - R[v]| as bits. GB300's FP64 pipe is narrow,
+// so FP64 instructions are kept to those that need FP64 rounding: three on the
+// Static path (r, |r - R[v]| as one FMA, next x); on the DF-P path also
+// Eq. 2's two extra steps, R[v] and the threshold tau * max(r, R[v]). The
+// maximum and the comparisons run on the bit patterns of the non-negative
+// doubles (integer instructions, the same order as the FP64 comparison; a
+// negative threshold's pattern is negative as int64, so it orders below every
+// non-negative value, as in FP64).
 template <bool DYN>
 __device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v, double c, uint64_t xself_b,
-                                                  uint64_t pf, uint64_t& fwsum) {
+                                                  uint64_t pf, uint64_t& fwsum, uint8_t dn_old) {
   const double xself = bitsd(xself_b);
   const double d = ld_stream_f64(a.degd + v, pf);
   double r;
@@ -216,15 +237,18 @@ __device__ __forceinline__ uint64_t finish_vertex(const SweepArgs& a, int32_t v,
   // |r - R[v]| with R[v] = x[v] * |out(v)| of the previous iteration, one rounding
   const double dr = fabs(fma(xself, -d, r));
   if (DYN) {
-    const double rold = xself * d;
-    const double m = fmax(r, rold);
-    if (a.prune && dr <= a.tau_p * m) a.dV[v] = 0;
+    const uint64_t rb = dbits(r), ob = dbits(xself * d), drb = dbits(dr);
+    const double m = bitsd(rb > ob ? rb : ob);  // max(r, R[v])
+    const int64_t tp = (int64_t)dbits(a.tau_p * m);
+    const int64_t tf = a.tau_f == a.tau_p ? tp : (int64_t)dbits(a.tau_f * m);
+    if (a.prune && (int64_t)drb <= tp) a.dV[v] = 0;
     // deltaN holds exactly this sweep's expand set: set or cleared for every vertex; the out-edges of
     // the set are counted for the choice of the expansion round's direction
-    if (dr > a.tau_f * m) {
-      a.dN[v] = 1;
-      fwsum += (uint64_t)d;
-    } else if (a.dN[v]) {
+    // (dn_old: the vertex's deltaN flag before this sweep, read ahead; no load on this path)
+    if ((int64_t)drb > tf) {
+      if (!dn_old) a.dN[v] = 1;
+      fwsum += degree_of(d);
+    } else if (dn_old) {
       a.dN[v] = 0;
     }
     a.wrote[v] = 1;
@@ -268,6 +292,29 @@ __device__ __forceinline__ bool skip_unaffected(const SweepArgs& a, int32_t v) {
   return true;
 }
 
+// The three flags of a vertex, read ahead of its turn: a vertex's flags change
+// during a sweep only in its own epilogue or skip, so a read issued earlier in
+// the sweep sees the values of the previous sweep, which is what the skip and
+// the epilogue need, and the loads leave the critical path.
+struct Flags {
+  uint8_t dv = 1, wr = 0, dn = 0;
+};
+__device__ __forceinline__ Flags load_flags(const SweepArgs& a, int32_t v) {
+  Flags f;
+  f.dv = a.dV[v];
+  f.wr = a.wrote[v];
+  f.dn = a.dN[v];
+  return f;
+}
+// skip_unaffected with the flags read ahead
+__device__ __forceinline__ void skip_vertex(const SweepArgs& a, int32_t v, const Flags& f) {
+  if (f.wr) {
+    a.xn[v] = a.x[v];
+    a.wrote[v] = 0;
+  }
+  if (f.dn) a.dN[v] = 0;
+}
+
 __device__ __forceinline__ void block_max_to(uint64_t dmax, uint64_t* out) {
   __shared__ uint64_t sh[32];
   dmax = warp_max_u64(dmax);
@@ -302,24 +349,26 @@ __device__ __forceinline__ void block_epilogue(const SweepArgs& a, uint64_t dmax
 }
 
 // Work item of a group: list entry, vertex, its row of G' and the first
-// G*U indices of the row (this lane's share).
+// G*U indices of the row (this lane's share), and (DF / DF-P) its flags.
 template <int U>
 struct Item {
   int32_t v;
   int64_t b, e;
   int32_t u[U];
+  Flags f;
 };
 
 // G lanes per vertex (G = 1, 4, 16), U indices per lane per round. The loop is
 // uniform across each warp (a warp owns 32/G consecutive list entries per
 // step), so the group shuffles always see all 32 lanes. Software pipeline:
-// the list entry of the item two steps ahead and the offsets and first
-// indices of the next item are loaded while the current item's gathers are
-// in flight, so a step costs about one memory round trip instead of four.
-// With self-loops on every vertex, a row of length 1 is [v] itself and needs
+// the list entry of the item two steps ahead (and its affected flag) and the
+// offsets, first indices and other flags of the next item are loaded while
+// the current item's gathers are in flight, so a step costs about one memory
+// round trip instead of four. With self-loops on every vertex, a row of length 1 is [v] itself and needs
 // no offsets or indices.
 template <int G, int U, bool EXACT, bool DYN, bool SELF1>
-__global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, int64_t begin, int64_t end) {
+__global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_group(const SweepArgs a_in, int64_t begin,
+                                                                                  int64_t end) {
   const SweepArgs a = resolve(a_in);
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
@@ -332,13 +381,19 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, 
   uint64_t dmax = 0, fwsum = 0;
 
   auto load_v = [&](int64_t i) -> int32_t { return i < end ? (int32_t)i : -1; };
-  // DF / DF-P: the row of an unaffected vertex is not read (its flag can
-  // change in this sweep only when the vertex itself is finished)
-  auto load_item = [&](int32_t v, Item<U>& it) {
+  auto load_dv = [&](int32_t v) -> uint8_t { return (DYN && v >= 0) ? a.dV[v] : (uint8_t)1; };
+  // DF / DF-P: the row of an unaffected vertex is not read
+  auto load_item = [&](int32_t v, uint8_t dv, Item<U>& it) {
     it.v = v;
     it.b = 0;
     it.e = 0;
-    const bool live = v >= 0 && (!DYN || a.dV[v]);
+    it.f = Flags();
+    if (DYN && v >= 0) {
+      it.f.dv = dv;
+      it.f.wr = a.wrote[v];
+      it.f.dn = a.dN[v];
+    }
+    const bool live = v >= 0 && dv;
     if (live) {
       if (SELF1) {
         it.b = 0;
@@ -358,17 +413,22 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, 
 
   int64_t base = begin + warp * kGroupsPerWarp;
   Item<U> cur;
-  load_item(load_v(base + gw), cur);
+  {
+    const int32_t v0 = load_v(base + gw);
+    load_item(v0, load_dv(v0), cur);
+  }
   int32_t v_next = load_v(base + step + gw);
+  uint8_t dv_next = load_dv(v_next);
   for (; base < end; base += step) {
     // gathers of the current item
     uint64_t xv[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) xv[k] = cur.u[k] >= 0 ? ld_gather_b64(a.x + cur.u[k], pl) : 0ull;
-    // prefetch: next item's row and first indices, and the list entry after it
+    // prefetch: next item's row, first indices and flags, and the list entry (and flag) after it
     Item<U> nxt;
-    load_item(v_next, nxt);
+    load_item(v_next, dv_next, nxt);
     v_next = load_v(base + 2 * step + gw);
+    dv_next = load_dv(v_next);
 
     // the warp is converged here (uniform loop): one vote picks the
     // three-word add when every gathered term of the step is in the common window
@@ -377,7 +437,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, 
     for (int k = 0; k < U; ++k) w1 = w1 && (cur.u[k] < 0 || Acc<EXACT>::in_w1(xv[k]));
     const bool all_w1 = __all_sync(0xffffffffu, w1);
     bool active = cur.v >= 0;
-    if (DYN && active && skip_unaffected(a, cur.v)) active = false;
+    if (DYN && active && !cur.f.dv) {
+      if (lane == 0) skip_vertex(a, cur.v, cur.f);
+      active = false;
+    }
     Acc<EXACT> acc;
     uint64_t xself = 0;
     if (active) {
@@ -405,7 +468,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, 
       }
     }
     if (active && lane == 0) {
-      const uint64_t db = finish_vertex<DYN>(a, cur.v, acc.value(), xself, pf, fwsum);
+      const uint64_t db = finish_vertex<DYN>(a, cur.v, acc.value(), xself, pf, fwsum, cur.f.dn);
       dmax = db > dmax ? db : dmax;
     }
     cur = nxt;
@@ -413,10 +476,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep_group(const SweepArgs a_in, 
   block_epilogue<DYN>(a, dmax, fwsum);
 }
 
-// one warp per vertex, 16-byte index loads; the next vertex's list entry and
-// row offsets are loaded while the current row is gathered
+// one warp per vertex, 16-byte index loads; the next vertex's list entry, row
+// offsets and (DF / DF-P) flags are loaded while the current row is gathered
 template <int KV, bool EXACT, bool DYN>
-__global__ void __launch_bounds__(kThreads) k_sweep_warp(const SweepArgs a_in, int64_t begin, int64_t end) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_warp(const SweepArgs a_in, int64_t begin, int64_t end) {
   const SweepArgs a = resolve(a_in);
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
@@ -427,31 +490,39 @@ __global__ void __launch_bounds__(kThreads) k_sweep_warp(const SweepArgs a_in, i
   int64_t i = begin + warp;
   int32_t v = i < end ? (int32_t)i : -1;
   int64_t b = v >= 0 ? ld_stream_i64(a.off + v, pf) : 0, e = v >= 0 ? ld_stream_i64(a.off + v + 1, pf) : 0;
+  Flags f;
+  if (DYN && v >= 0) f = load_flags(a, v);
   for (; i < end; i += nwarps) {
     const int64_t inx = i + nwarps;
     const int32_t vn = inx < end ? (int32_t)inx : -1;
     bool active = true;
-    if (DYN && skip_unaffected(a, v)) active = false;
+    if (DYN && !f.dv) {
+      if (lane == 0) skip_vertex(a, v, f);
+      active = false;
+    }
     Acc<EXACT> acc;
     // x[v], for R[v] of the previous iteration = x[v] * |out(v)|, issued ahead of the gathers
     uint64_t xself = (active && lane == 0) ? ld_gather_b64(a.x + v, pl) : 0ull;
     if (active) gather_row_vec<32, KV, EXACT, false>(a, b, e, lane, v, acc, xself, pf, pl);
     const int64_t bn = vn >= 0 ? ld_stream_i64(a.off + vn, pf) : 0, en = vn >= 0 ? ld_stream_i64(a.off + vn + 1, pf) : 0;
+    Flags fn;
+    if (DYN && vn >= 0) fn = load_flags(a, vn);
     acc.template group_reduce<32>();
     if (active && lane == 0) {
-      const uint64_t db = finish_vertex<DYN>(a, v, acc.value(), xself, pf, fwsum);
+      const uint64_t db = finish_vertex<DYN>(a, v, acc.value(), xself, pf, fwsum, f.dn);
       dmax = db > dmax ? db : dmax;
     }
     v = vn;
     b = bn;
     e = en;
+    f = fn;
   }
   block_epilogue<DYN>(a, dmax, fwsum);
 }
 
 // one block per vertex (high in-degree)
 template <int KV, bool EXACT, bool DYN>
-__global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a_in, int64_t begin, int64_t end) {
+__global__ void __launch_bounds__(kThreads, 3) k_sweep_block(const SweepArgs a_in, int64_t begin, int64_t end) {
   const SweepArgs a = resolve(a_in);
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
@@ -479,7 +550,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a_in, 
     if (threadIdx.x == 0) {
       Acc<EXACT> tot;
       for (int k = 0; k < kThreads / 32; ++k) tot.from_shared(s_acc[k]);
-      const uint64_t db = finish_vertex<DYN>(a, v, tot.value(), xb, pf, fwsum);
+      const uint64_t db = finish_vertex<DYN>(a, v, tot.value(), xb, pf, fwsum, DYN ? a.dN[v] : (uint8_t)0);
       dmax = db > dmax ? db : dmax;
     }
     __syncthreads();
@@ -496,7 +567,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_block(const SweepArgs a_in, 
 // an unaffected hub through. A hub's flag changes only in its finishing warp,
 // which runs after every chunk of the sweep has read it.
 template <bool EXACT, bool DYN>
-__global__ void __launch_bounds__(kThreads) k_sweep_hub_part(const SweepArgs a_in) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_hub_part(const SweepArgs a_in) {
   const SweepArgs a = resolve(a_in);
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
@@ -518,7 +589,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_hub_part(const SweepArgs a_i
 }
 
 template <bool EXACT, bool DYN>
-__global__ void __launch_bounds__(kThreads) k_sweep_hub_finish(const SweepArgs a_in) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_hub_finish(const SweepArgs a_in) {
   const SweepArgs a = resolve(a_in);
   if (a.prev && bitsd(*a.prev) <= a.tol) return;
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
@@ -542,7 +613,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep_hub_finish(const SweepArgs a
       tot.from_shared(reinterpret_cast<const uint32_t*>(a.hub_part + c));
     tot.template group_reduce<32>();
     if (lane == 0) {
-      const uint64_t db = finish_vertex<DYN>(a, v, tot.value(), ld_gather_b64(a.x + v, pl), pf, fwsum);
+      const uint64_t db =
+          finish_vertex<DYN>(a, v, tot.value(), ld_gather_b64(a.x + v, pl), pf, fwsum, DYN ? a.dN[v] : (uint8_t)0);
       dmax = db > dmax ? db : dmax;
     }
   }
