@@ -35,15 +35,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__global__ void k_degrees(const int64_t* __restrict__ off, int32_t n, double* __restrict__ deg,
-                          double* __restrict__ inv) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t d = off[v + 1] - off[v];
-    deg[v] = (double)d;
-    inv[v] = d > 0 ? 1.0 / (double)d : 0.0;
-  }
-}
-
 // x[i] = R0[perm[i]] / |out(perm[i])| in the sweep numbering (R0 = NULL: 1/n)
 __global__ void k_init_x(const double* __restrict__ R0, const int32_t* __restrict__ perm, int32_t n,
                          const double* __restrict__ inv, double* __restrict__ xa, double* __restrict__ xb) {
@@ -263,6 +254,52 @@ __global__ void k_effective(const int32_t* __restrict__ s, const int32_t* __rest
   }
 }
 
+// ids of a batch list in the sweep numbering: out[i] = inv[a[i]]
+__global__ void k_map_ids(const int32_t* __restrict__ a, int64_t cnt, const int32_t* __restrict__ inv,
+                          int32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = inv[a[i]];
+}
+
+// position of (u, v) (original ids) in a CSR of the sweep numbering, whose row inv[u] lists renumbered ids in
+// original-id order, or -1
+__device__ __forceinline__ int64_t find_edge_keyed(const int64_t* off, const int32_t* adj, const int32_t* perm,
+                                                   const int32_t* inv, int32_t u, int32_t v) {
+  const int32_t r = inv[u];
+  int64_t lo = off[r], hi = off[r + 1];
+  const int64_t e = hi;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (perm[adj[mid]] < v) lo = mid + 1; else hi = mid;
+  }
+  return (lo < e && perm[adj[lo]] == v) ? lo : -1;
+}
+
+__global__ void k_effective_keyed(const int32_t* __restrict__ s, const int32_t* __restrict__ d, int64_t cnt,
+                                  int deletion, const int32_t* __restrict__ perm, const int32_t* __restrict__ inv,
+                                  const int64_t* __restrict__ o_off, const int32_t* __restrict__ o_adj,
+                                  const int64_t* __restrict__ n_off, const int32_t* __restrict__ n_adj,
+                                  uint8_t* __restrict__ eff) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool in_old = find_edge_keyed(o_off, o_adj, perm, inv, s[i], d[i]) >= 0;
+    const bool in_new = find_edge_keyed(n_off, n_adj, perm, inv, s[i], d[i]) >= 0;
+    eff[i] = deletion ? (in_old && !in_new) : (!in_old && in_new);
+  }
+}
+
+// Vertices of the in-degree <= 1 classes (the sweep numbering's ids [0, end1))
+// that receive an in-edge: their bit of multi is set, and the number of bits
+// newly set is added to *count.
+__global__ void k_mark_multi(const int32_t* __restrict__ ins_dst, int64_t cnt, const int32_t* __restrict__ inv,
+                             int64_t end1, uint32_t* __restrict__ multi, unsigned long long* __restrict__ count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = inv[ins_dst[i]];
+    if (r >= end1) continue;
+    const uint32_t bit = 1u << (r & 31);
+    if (!(atomicOr(multi + (r >> 5), bit) & bit)) atomicAdd(count, 1ull);
+  }
+}
+
 int check_params(const prdf_params* p) {
   if (!p) {
     set_error("params is NULL");
@@ -299,15 +336,8 @@ int check_params(const prdf_params* p) {
   return PRDF_OK;
 }
 
-int ensure_degrees(prdf_graph* g, cudaStream_t s) {
-  PRDF_TRY(g->outdeg.alloc(g->n, s));
-  PRDF_TRY(g->inv_outdeg.alloc(g->n, s));
-  k_degrees<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(g->csr[PRDF_OUT].off.p, g->n, g->outdeg.p, g->inv_outdeg.p);
-  PRDF_LAUNCH_CHECK();
-  return PRDF_OK;
-}
-
 int ensure_partition(prdf_graph* g, int which, cudaStream_t s) {
+  PRDF_TRY(ensure_orig(g, s));
   if (g->pvalid[which]) return PRDF_OK;
   PRDF_TRY(g->P[which].reserve(g->n, s));
   PRDF_TRY(partition_by_degree(g->csr[which].off.p, g->n, g->thr[which], g->P[which].p, g->pcount[which], g->ws, s));
@@ -479,6 +509,7 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
     a.c0 = (float)((1.0 - p->alpha) / (double)n);
     a.self_loops = g->self_loops ? 1 : 0;
     a.tol_rel = L->tol_rel;
+    a.multi = rl.multi_count > 0 ? rl.multi.p : nullptr;
     a.hub = g->hub_in.view();
     a.hub_part = g->sweep_hub_part32.p;
     if (dynamic) {
@@ -505,6 +536,7 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
     a.c0 = (1.0 - p->alpha) / (double)n;
     a.self_loops = g->self_loops ? 1 : 0;
     a.tol = p->tol;
+    a.multi = rl.multi_count > 0 ? rl.multi.p : nullptr;
     a.hub = g->hub_in.view();
     a.hub_part = g->sweep_hub_part.p;
     if (dynamic) {
@@ -673,37 +705,12 @@ int run_host_loop(prdf_graph* g, const Loop& L, const prdf_params* p, IterResult
   return PRDF_OK;
 }
 
-// The same loop as one CUDA graph (see above).
-int run_graph_loop(prdf_graph* g, const Loop& L, IterResult* res, cudaStream_t s) {
-  PRDF_TRY(g->ctl.reserve(2, s));
-  PRDF_CUDA(cudaMemsetAsync(g->ctl.p, 0, 2 * sizeof(int), s));
-  // what the captured kernels hold: their arguments and the buffers of the graph-driven iteration
-  std::vector<uint64_t> key;
-  auto put = [&key](const void* p, size_t nb) {
-    const size_t at = key.size();
-    key.resize(at + (nb + 7) / 8, 0);
-    memcpy(key.data() + at, p, nb);
-  };
-  auto putv = [&put](uint64_t v) { put(&v, sizeof(v)); };
-  putv(((uint64_t)L.fp32 << 3) | ((uint64_t)L.dynamic << 2) | ((uint64_t)L.expand << 1) | (uint64_t)L.exact);
-  putv((uint64_t)L.max_iter);
-  put(&L.tol, sizeof(L.tol));
-  put(&L.tol_rel, sizeof(L.tol_rel));
-  if (L.fp32) put(&L.a32, sizeof(L.a32));
-  else put(&L.a, sizeof(L.a));
-  put(L.cb, sizeof(L.cb));
-  put(L.cbo, sizeof(L.cbo));
-  putv((uint64_t)L.nci | ((uint64_t)L.nco << 32));
-  putv((uint64_t)L.pull_warp_b);
-  putv(L.fthr);
-  const Relabel& rl = g->rl;
-  const void* ptrs[] = {g->ctl.p,     g->xa.p,       g->xb.p,        g->ya.p,       g->yb.p,      g->resid.p,
-                        g->resid32.p, g->fwork.p,    g->dN.p,        g->dV.p,       rl.in.off.p,  rl.in.adj.p,
-                        rl.out.off.p, rl.out.adj.p,  rl.pout.p};
-  put(ptrs, sizeof(ptrs));
-  putv(rl.version);
-  putv((uint64_t)g->n);
-  const int slot = (L.fp32 ? 4 : 0) + (L.dynamic ? 2 : 0) + (L.expand ? 1 : 0);
+// Launch on s the cached while-loop graph of `slot`, first building it when
+// it was made for another key: a conditional while node whose body is
+// recorded by body(capture stream, conditional handle) (the body ends with a
+// one-thread check that sets the condition).
+template <class Body>
+int launch_while_graph(prdf_graph* g, int slot, const std::vector<uint64_t>& key, Body body, cudaStream_t s) {
   if (!g->loop_exec[slot] || g->loop_key[slot] != key) {
     if (g->loop_exec[slot]) {
       cudaGraphExecDestroy(g->loop_exec[slot]);
@@ -723,16 +730,12 @@ int run_graph_loop(prdf_graph* g, const Loop& L, IterResult* res, cudaStream_t s
     np.conditional.size = 1;
     cudaGraphNode_t node;
     if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
-    cudaGraph_t body = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
+    cudaGraph_t bodyg = e == cudaSuccess ? np.conditional.phGraph_out[0] : nullptr;
     if (e == cudaSuccess)
-      e = cudaStreamBeginCaptureToGraph(g->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      e = cudaStreamBeginCaptureToGraph(g->cap_stream, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     int rc = PRDF_OK;
     if (e == cudaSuccess) {
-      rc = launch_loop_sweep(g, L, -1, g->cap_stream);
-      if (rc == PRDF_OK) rc = launch_loop_expansion(g, L, -1, g->cap_stream);
-      if (rc == PRDF_OK)
-        rc = L.fp32 ? launch_iter_check32(g->ctl.p, g->resid32.p, L.tol_rel, L.max_iter, h, g->cap_stream)
-                    : launch_iter_check(g->ctl.p, g->resid.p, L.tol, L.max_iter, h, g->cap_stream);
+      rc = body(g->cap_stream, h);
       cudaGraph_t captured = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &captured);
       if (e == cudaSuccess) e = e2;
@@ -749,6 +752,53 @@ int run_graph_loop(prdf_graph* g, const Loop& L, IterResult* res, cudaStream_t s
     g->loop_key[slot] = key;
   }
   PRDF_CUDA(cudaGraphLaunch(g->loop_exec[slot], s));
+  return PRDF_OK;
+}
+
+// key words of a graph: the raw bytes of the values it was captured with
+struct KeyWriter {
+  std::vector<uint64_t> key;
+  void put(const void* p, size_t nb) {
+    const size_t at = key.size();
+    key.resize(at + (nb + 7) / 8, 0);
+    memcpy(key.data() + at, p, nb);
+  }
+  void putv(uint64_t v) { put(&v, sizeof(v)); }
+};
+
+// The same loop as one CUDA graph (see above).
+int run_graph_loop(prdf_graph* g, const Loop& L, IterResult* res, cudaStream_t s) {
+  PRDF_TRY(g->ctl.reserve(2, s));
+  PRDF_CUDA(cudaMemsetAsync(g->ctl.p, 0, 2 * sizeof(int), s));
+  // what the captured kernels hold: their arguments and the buffers of the graph-driven iteration
+  KeyWriter kw;
+  kw.putv(((uint64_t)L.fp32 << 3) | ((uint64_t)L.dynamic << 2) | ((uint64_t)L.expand << 1) | (uint64_t)L.exact);
+  kw.putv((uint64_t)L.max_iter);
+  kw.put(&L.tol, sizeof(L.tol));
+  kw.put(&L.tol_rel, sizeof(L.tol_rel));
+  if (L.fp32) kw.put(&L.a32, sizeof(L.a32));
+  else kw.put(&L.a, sizeof(L.a));
+  kw.put(L.cb, sizeof(L.cb));
+  kw.put(L.cbo, sizeof(L.cbo));
+  kw.putv((uint64_t)L.nci | ((uint64_t)L.nco << 32));
+  kw.putv((uint64_t)L.pull_warp_b);
+  kw.putv(L.fthr);
+  const Relabel& rl = g->rl;
+  const void* ptrs[] = {g->ctl.p,     g->xa.p,       g->xb.p,        g->ya.p,       g->yb.p,      g->resid.p,
+                        g->resid32.p, g->fwork.p,    g->dN.p,        g->dV.p,       rl.in.off.p,  rl.in.adj.p,
+                        rl.out.off.p, rl.out.adj.p,  rl.pout.p};
+  kw.put(ptrs, sizeof(ptrs));
+  kw.putv(rl.version);
+  kw.putv((uint64_t)g->n);
+  const int slot = (L.fp32 ? 4 : 0) + (L.dynamic ? 2 : 0) + (L.expand ? 1 : 0);
+  PRDF_TRY(launch_while_graph(g, slot, kw.key, [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+    int rc = launch_loop_sweep(g, L, -1, cs);
+    if (rc == PRDF_OK) rc = launch_loop_expansion(g, L, -1, cs);
+    if (rc == PRDF_OK)
+      rc = L.fp32 ? launch_iter_check32(g->ctl.p, g->resid32.p, L.tol_rel, L.max_iter, h, cs)
+                  : launch_iter_check(g->ctl.p, g->resid.p, L.tol, L.max_iter, h, cs);
+    return rc;
+  }, s));
   PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
   int hit = 0;
@@ -794,6 +844,7 @@ struct KOp {
   const PprHubTable* hub;  // chunks of the highest class's rows of this CSR
   const double* S64;  // right-hand side (dense [n, K]), also the start of the iteration
   bool sparse_rhs;    // look for few non-zero rows in S64 (a teleport on a few seed vertices)
+  int slot;           // first of the four graph-cache slots of this operator's loops
 };
 
 int64_t hub_begin(const Relabel& rl) {
@@ -846,6 +897,43 @@ int ppr32_solve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int t
   const int64_t hb = op.hub_begin;
   const int check = p->check_every > 0 ? p->check_every : 8;
   float* buf[2] = {*cur, *other};
+  const int tiles = (K + tile - 1) / tile;
+  if (!p->time_sweeps) {
+    // one CUDA graph: a while node over one sweep (every column tile) and the stop check
+    PRDF_TRY(g->ctl.reserve(2, s));
+    PRDF_CUDA(cudaMemsetAsync(g->ctl.p, 0, 2 * sizeof(int), s));
+    a.ctl = g->ctl.p;
+    a.Ra = buf[0];
+    a.Rb = buf[1];
+    a.resid_base = g->resid32.p;
+    const PprHub hv = op.hub->view();
+    KeyWriter kw;
+    kw.put(&a, sizeof(a));
+    kw.put(&hv, sizeof(hv));
+    kw.putv((uint64_t)tile | ((uint64_t)max_iter << 32));
+    kw.putv((uint64_t)hb);
+    kw.putv((uint64_t)(uintptr_t)g->ppr_part.p);
+    kw.putv((uint64_t)g->n);
+    PRDF_TRY(launch_while_graph(g, op.slot + (srow ? 1 : 0), kw.key, [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+      int rc = launch_ppr32_sweep(a, tile, g->n, hb, hv, g->ppr_part.p, cs);
+      if (rc == PRDF_OK) rc = launch_iter_check32(g->ctl.p, g->resid32.p, a.tol_rel, max_iter, h, cs);
+      return rc;
+    }, s));
+    int hit = 0;
+    PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PRDF_CUDA(cudaStreamSynchronize(s));
+    memcpy(&hit, g->ws.host_i64, sizeof(int));
+    if (hit < 1 || hit > max_iter) {
+      set_error("K-column graph ran %d sweeps", hit);
+      return PRDF_ECUDA;
+    }
+    const int k = hit - 1;
+    *iters = hit;
+    *cur = buf[(k + 1) & 1];
+    *other = buf[k & 1];
+    *kernels += (long long)hit * (tiles * ppr32_kernels(hb, op.hub->begin, g->n) + 1);
+    return PRDF_OK;
+  }
   int launched = 0;
   bool done = false;
   while (launched < max_iter && !done) {
@@ -884,7 +972,6 @@ int ppr32_solve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int t
   *iters = k + 1;
   *cur = buf[(k + 1) & 1];
   *other = buf[k & 1];
-  const int tiles = (K + tile - 1) / tile;
   *kernels += (long long)launched * tiles * ppr32_kernels(hb, op.hub->begin, g->n);
   return PRDF_OK;
 }
@@ -942,6 +1029,60 @@ int ksolve(prdf_graph* g, const KOp& op, const prdf_params* p, int K, int tile, 
     }
     const double* rhs = sp.rows ? sp.Sc64.p : op.S64;
     const int32_t* srow = sp.rows ? sp.srow.p : nullptr;
+    if (!p->time_sweeps) {
+      // one CUDA graph: a while node over one FP64 Jacobi step (every column tile) and the stop check
+      const int max_iter = p->max_iter;
+      PRDF_TRY(g->resid.reserve((size_t)max_iter + 1, s));
+      PRDF_CUDA(cudaMemsetAsync(g->resid.p, 0, sizeof(uint64_t) * ((size_t)max_iter + 1), s));
+      PRDF_TRY(g->ctl.reserve(2, s));
+      PRDF_CUDA(cudaMemsetAsync(g->ctl.p, 0, 2 * sizeof(int), s));
+      PRDF_TRY(g->ppr_part64.reserve((size_t)(op.hub->nchunk > 0 ? op.hub->nchunk : 1) * (size_t)tile, s));
+      Ppr64Args pa;
+      memset(&pa, 0, sizeof(pa));
+      pa.off = op.off;
+      pa.adj = op.adj;
+      pa.P = op.p64;
+      pa.S = rhs;
+      pa.srow = srow;
+      pa.K = K;
+      pa.alpha = p->alpha;
+      pa.beta = 1.0 - p->alpha;
+      pa.inv_beta = 1.0 / (1.0 - p->alpha);
+      pa.ctl = g->ctl.p;
+      pa.Ra = g->R64a.p;
+      pa.Rb = g->R64b.p;
+      pa.dmax_base = g->resid.p;
+      const PprHub hv = op.hub->view();
+      KeyWriter kw;
+      kw.put(&pa, sizeof(pa));
+      kw.put(&hv, sizeof(hv));
+      kw.putv((uint64_t)tile | ((uint64_t)max_iter << 32));
+      kw.put(&p->tol, sizeof(p->tol));
+      kw.putv((uint64_t)op.hub_begin);
+      kw.putv((uint64_t)(uintptr_t)g->ppr_part64.p);
+      kw.putv((uint64_t)g->n);
+      PRDF_TRY(launch_while_graph(g, op.slot + 2, kw.key, [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+        int rc = launch_ppr64_step(pa, tile, g->n, op.hub_begin, hv, g->ppr_part64.p, cs);
+        if (rc == PRDF_OK) rc = launch_iter_check(g->ctl.p, g->resid.p, p->tol, max_iter, h, cs);
+        return rc;
+      }, s));
+      int hit = 0;
+      PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      PRDF_CUDA(cudaStreamSynchronize(s));
+      memcpy(&hit, g->ws.host_i64, sizeof(int));
+      if (hit < 1 || hit > max_iter) {
+        set_error("K-column graph ran %d steps", hit);
+        return PRDF_ECUDA;
+      }
+      PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64, g->resid.p + hit - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+      PRDF_CUDA(cudaStreamSynchronize(s));
+      memcpy(&r->dmax, g->ws.host_i64, sizeof(double));
+      r->steps64 += hit;
+      r->converged = r->dmax <= p->tol ? 1 : 0;
+      r->kernels += (long long)hit * (((K + tile - 1) / tile) * ppr32_kernels(op.hub_begin, op.hub->begin, g->n) + 1);
+      *out = ((hit - 1) & 1) ? g->R64a.p : g->R64b.p;  // step k writes R64b when k is even
+      return PRDF_OK;
+    }
     double* a = g->R64a.p;
     double* b = g->R64b.p;
     for (int it = 0; it < p->max_iter; ++it) {
@@ -1157,7 +1298,7 @@ int prdf_graph_create(int32_t n, const int32_t* src, const int32_t* dst, const f
   g->self_loops = loops;
   if (r == PRDF_OK) r = build_csr(n, m0, src, dst, w, loops, false, g->csr[PRDF_OUT], g->ws, s);
   if (r == PRDF_OK) r = build_csr(n, m0, dst, src, w, loops, false, g->csr[PRDF_IN], g->ws, s);
-  if (r == PRDF_OK) r = ensure_degrees(g, s);
+  g->m = g->csr[PRDF_OUT].m;
   if (r == PRDF_OK) r = build_relabelled(g, s);
   if (r == PRDF_OK && cudaStreamSynchronize(s) != cudaSuccess) {
     set_error("graph build: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1187,7 +1328,7 @@ int prdf_graph_size(const prdf_graph* g, int32_t* n_host, int64_t* m_host) {
     return PRDF_EINVAL;
   }
   if (n_host) *n_host = g->n;
-  if (m_host) *m_host = g->csr[PRDF_OUT].m;
+  if (m_host) *m_host = g->m;
   return PRDF_OK;
 }
 
@@ -1201,6 +1342,7 @@ int prdf_graph_export_csr(const prdf_graph* g, int which, int64_t* off, int32_t*
     return PRDF_ESTATE;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  PRDF_TRY(ensure_orig(const_cast<prdf_graph*>(g), s));
   const Csr& c = g->csr[which];
   if (off) PRDF_CUDA(cudaMemcpyAsync(off, c.off.p, sizeof(int64_t) * ((size_t)g->n + 1), cudaMemcpyDeviceToDevice, s));
   if (adj && c.m) PRDF_CUDA(cudaMemcpyAsync(adj, c.adj.p, sizeof(int32_t) * (size_t)c.m, cudaMemcpyDeviceToDevice, s));
@@ -1223,16 +1365,83 @@ int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t*
   cudaStream_t s = (cudaStream_t)stream;
   PRDF_TRY(check_inputs(g, del_src, del_dst, n_del, ins_src, ins_dst, n_ins, nullptr, nullptr, s));
   const int32_t n = g->n;
+  Relabel& rl = g->rl;
+  if (g->self_loops && rl.valid) {
+    // Every vertex already has its self-loop: each row of G and of G' becomes
+    // (old \ D) u I, merged in order (batch_update.cu), directly on the copies
+    // in the sweep numbering (rows ordered by original id, columns compared
+    // through perm). The numbering, its partitions and the chunk tables are
+    // kept; the original-id CSRs are derived again when asked for.
+    DBuf<int32_t> rows;
+    const int64_t nb = n_del + n_ins;
+    PRDF_TRY(rows.alloc((size_t)(2 * nb > 0 ? 2 * nb : 1), s));
+    int32_t* del_r_out = rows.p;           // inv[del_src]
+    int32_t* del_r_in = rows.p + n_del;    // inv[del_dst]
+    int32_t* ins_r_out = rows.p + 2 * n_del;
+    int32_t* ins_r_in = rows.p + 2 * n_del + n_ins;
+    if (n_del) {
+      k_map_ids<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_src, n_del, rl.inv.p, del_r_out);
+      k_map_ids<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_dst, n_del, rl.inv.p, del_r_in);
+    }
+    if (n_ins) {
+      k_map_ids<<<grid_for(n_ins, kThreads), kThreads, 0, s>>>(ins_src, n_ins, rl.inv.p, ins_r_out);
+      k_map_ids<<<grid_for(n_ins, kThreads), kThreads, 0, s>>>(ins_dst, n_ins, rl.inv.p, ins_r_in);
+    }
+    PRDF_LAUNCH_CHECK();
+    Csr nout, nin;
+    PRDF_TRY(update_csr(n, rl.out, del_r_out, del_dst, n_del, ins_r_out, ins_dst, ins_w, n_ins, nout, g->ws, s,
+                        rl.perm.p, rl.inv.p));
+    PRDF_TRY(update_csr(n, rl.in, del_r_in, del_src, n_del, ins_r_in, ins_src, ins_w, n_ins, nin, g->ws, s,
+                        rl.perm.p, rl.inv.p));
+    if (del_eff && n_del)
+      k_effective_keyed<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_src, del_dst, n_del, 1, rl.perm.p,
+                                                                       rl.inv.p, rl.out.off.p, rl.out.adj.p,
+                                                                       nout.off.p, nout.adj.p, del_eff);
+    if (ins_eff && n_ins)
+      k_effective_keyed<<<grid_for(n_ins, kThreads), kThreads, 0, s>>>(ins_src, ins_dst, n_ins, 0, rl.perm.p,
+                                                                       rl.inv.p, rl.out.off.p, rl.out.adj.p,
+                                                                       nout.off.p, nout.adj.p, ins_eff);
+    PRDF_LAUNCH_CHECK();
+    rl.out = static_cast<Csr&&>(nout);
+    rl.in = static_cast<Csr&&>(nin);
+    g->m = rl.out.m;
+    // vertices of the classes of in-degree <= 1 (ids [0, end1)) that gain an in-edge take the general path
+    // of their kernel
+    int64_t end1 = 0;
+    for (int c = 0; c < rl.thr.n && rl.thr.thr[c] <= 1; ++c) end1 += rl.count[c];
+    const bool self1 = end1 > 0;
+    if (self1 && n_ins) {
+      PRDF_TRY(g->counter.reserve(1, s));
+      PRDF_CUDA(cudaMemsetAsync(g->counter.p, 0, sizeof(unsigned long long), s));
+      k_mark_multi<<<grid_for(n_ins, kThreads), kThreads, 0, s>>>(ins_dst, n_ins, rl.inv.p, end1, rl.multi.p,
+                                                                  g->counter.p);
+      PRDF_LAUNCH_CHECK();
+      PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64 + 1, g->counter.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                s));
+    }
+    PRDF_TRY(update_degrees(g, s));
+    rl.drift += nb;
+    ++rl.version;
+    g->orig_valid = false;
+    g->pvalid[0] = g->pvalid[1] = false;
+    g->ppr_valid = false;
+    PRDF_CUDA(cudaStreamSynchronize(s));
+    if (self1 && n_ins) rl.multi_count += g->ws.host_i64[1];
+    // a fresh numbering once the batches applied since the last one add up to
+    // 1/64 of the edges (degree classes and out-degree tiers drift)
+    if (rl.drift * 64 > g->m) {
+      PRDF_TRY(build_relabelled(g, s));
+      PRDF_CUDA(cudaStreamSynchronize(s));
+    }
+    return PRDF_OK;
+  }
+  // Graphs made without self-loops: rebuild from the edge list (which also
+  // gives every vertex its self-loop) and renumber.
+  PRDF_TRY(ensure_orig(g, s));
   Csr& old = g->csr[PRDF_OUT];
   const int64_t m = old.m;
   Csr nout, nin;
-  if (g->self_loops) {
-    // every vertex already has its self-loop: each row of G and of G' becomes
-    // (old \ D) u I, merged in order (batch_update.cu), no re-sort of the graph
-    PRDF_TRY(update_csr(n, g->csr[PRDF_OUT], del_src, del_dst, n_del, ins_src, ins_dst, ins_w, n_ins, nout, g->ws, s));
-    PRDF_TRY(update_csr(n, g->csr[PRDF_IN], del_dst, del_src, n_del, ins_dst, ins_src, ins_w, n_ins, nin, g->ws, s));
-  } else {
-    // rebuild from the edge list (which also gives every vertex its self-loop)
+  {
     DBuf<uint8_t> deleted;
     PRDF_TRY(deleted.alloc((size_t)m, s));
     PRDF_CUDA(cudaMemsetAsync(deleted.p, 0, (size_t)m, s));
@@ -1264,9 +1473,8 @@ int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t*
   g->self_loops = true;  // the rebuild gives every vertex its self-loop
   g->csr[PRDF_OUT] = static_cast<Csr&&>(nout);
   g->csr[PRDF_IN] = static_cast<Csr&&>(nin);
-  g->csr[PRDF_OUT].m = nout.m;
-  g->csr[PRDF_IN].m = nin.m;
-  PRDF_TRY(ensure_degrees(g, s));
+  g->m = g->csr[PRDF_OUT].m;
+  g->orig_valid = true;
   g->pvalid[0] = g->pvalid[1] = false;
   PRDF_TRY(build_relabelled(g, s));
   PRDF_CUDA(cudaStreamSynchronize(s));
@@ -1393,7 +1601,7 @@ int prdf_pagerank_static(prdf_graph* g, const prdf_params* p, const double* R0, 
     cudaEventElapsedTime(&stats->ms_partition, t.e[0], t.e[1]);
     cudaEventElapsedTime(&stats->ms_iterate, t.e[1], t.e[2]);
     stats->ms_sweep = it.ms_sweep > 0 ? it.ms_sweep : 0.f;
-    stats->edges_processed = (long long)(it.iters + iters32) * g->csr[PRDF_IN].m;
+    stats->edges_processed = (long long)(it.iters + iters32) * g->m;
     // init + sweeps + finalize
     stats->kernel_launches = 1 + kernels32 + it.kernels + 1;
   }
@@ -1613,7 +1821,8 @@ int prdf_pagerank_ppr(prdf_graph* g, const double* S, int K, double* R, const pr
   PRDF_LAUNCH_CHECK();
   PRDF_CUDA(cudaEventRecord(t.e[1], s));
   PRDF_TRY(ensure_hub(g, g->rl.in, g->hub_in, s));
-  const KOp op{g->rl.in.off.p, g->rl.in.adj.p, g->pin32.p, g->pin64.p, hub_begin(g->rl), &g->hub_in, g->S64.p, true};
+  const KOp op{g->rl.in.off.p, g->rl.in.adj.p, g->pin32.p, g->pin64.p, hub_begin(g->rl), &g->hub_in, g->S64.p, true,
+               8};
   KSolve ks;
   ks.kernels = 1;
   double* Rfinal = nullptr;
@@ -1647,6 +1856,7 @@ int prdf_graph_set_weights(prdf_graph* g, const float* w, void* stream) {
     return PRDF_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  PRDF_TRY(ensure_orig(g, s));  // w is given in the original out-CSR's slot order
   Csr& o = g->csr[PRDF_OUT];
   Csr& in = g->csr[PRDF_IN];
   DBuf<float> wo, wi;
@@ -1710,7 +1920,7 @@ int prdf_pagerank_backward(prdf_graph* g, const double* R, const double* G, int 
   PRDF_CUDA(cudaEventRecord(t.e[1], s));
   PRDF_TRY(ensure_hub(g, g->rl.out, g->hub_out, s));
   const KOp op{g->rl.out.off.p, g->rl.out.adj.p, g->pout32.p, g->pout64.p, hub_begin(g->rl), &g->hub_out, g->S64.p,
-               false};
+               false, 12};
   KSolve ks;
   ks.kernels = 1;
   double* lam = nullptr;
@@ -1721,6 +1931,7 @@ int prdf_pagerank_backward(prdf_graph* g, const double* R, const double* G, int 
     ks.kernels += 1;
   }
   if (grad_w) {
+    PRDF_TRY(ensure_orig(g, s));  // grad_w is written in the original out-CSR's slot order
     double* Rr = (lam == g->R64a.p) ? g->R64b.p : g->R64a.p;
     k_rows_gather_scaled<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(R, g->rl.perm.p, g->n, K, 1.0, Rr);
     PRDF_LAUNCH_CHECK();

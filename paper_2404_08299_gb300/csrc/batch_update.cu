@@ -12,6 +12,12 @@
 // Rows without batch entries are copied edge-parallel in contiguous segments
 // between the changed rows, each with one shift. The result equals a rebuild
 // of the whole edge list when every vertex already has its self-loop.
+//
+// Keyed form: the rows of a CSR in the sweep numbering hold renumbered ids in
+// the order of the vertices' original ids. With key (renumbered -> original)
+// every comparison with an old entry uses key[entry], the batch's columns are
+// original ids, and store (original -> renumbered) maps an added column to the
+// value stored; rows stay ordered by original id.
 #include "internal.cuh"
 
 namespace prdf {
@@ -34,6 +40,23 @@ __device__ __forceinline__ bool contains(const int64_t* off, const int32_t* adj,
   return p < e && adj[p] == c;
 }
 
+// the same on an old row compared through key (null: the entries themselves)
+__device__ __forceinline__ int64_t lower_bound_key(const int32_t* a, const int32_t* key, int64_t lo, int64_t hi,
+                                                   int32_t c) {
+  if (!key) return lower_bound_i32(a, lo, hi, c);
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (key[a[mid]] < c) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ bool contains_key(const int64_t* off, const int32_t* adj, const int32_t* key, int32_t u,
+                                             int32_t c) {
+  const int64_t e = off[u + 1];
+  const int64_t p = lower_bound_key(adj, key, off[u], e, c);
+  return p < e && (key ? key[adj[p]] : adj[p]) == c;
+}
+
 // row of CSR entry k: the last u with off[u] <= k
 __device__ __forceinline__ int32_t row_of(const int64_t* off, int32_t n, int64_t k) {
   int32_t lo = 0, hi = n;  // off[lo] <= k < off[hi]
@@ -44,27 +67,29 @@ __device__ __forceinline__ int32_t row_of(const int64_t* off, int32_t n, int64_t
   return lo;
 }
 
-// deletion rows with self-loops masked out (self-loops are never deleted)
+// deletion rows with self-loops masked out (self-loops are never deleted; a
+// row id r is compared through key when the columns are original ids)
 __global__ void k_mask_self(const int32_t* __restrict__ r, const int32_t* __restrict__ c, int64_t cnt,
-                            int32_t* __restrict__ out) {
+                            const int32_t* __restrict__ key, int32_t* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = r[i] == c[i] ? -1 : r[i];
+    out[i] = (key ? key[r[i]] : r[i]) == c[i] ? -1 : r[i];
 }
 
 // dflag[k] = D entry k is in the old row; iflag[k] = I entry k adds an element
 __global__ void k_batch_flags(int32_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                              const int64_t* __restrict__ d_off, const int32_t* __restrict__ d_adj, int64_t nd,
-                              const int64_t* __restrict__ i_off, const int32_t* __restrict__ i_adj, int64_t ni,
-                              uint32_t* __restrict__ dflag, uint32_t* __restrict__ iflag) {
+                              const int32_t* __restrict__ key, const int64_t* __restrict__ d_off,
+                              const int32_t* __restrict__ d_adj, int64_t nd, const int64_t* __restrict__ i_off,
+                              const int32_t* __restrict__ i_adj, int64_t ni, uint32_t* __restrict__ dflag,
+                              uint32_t* __restrict__ iflag) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nd + ni; k += (int64_t)gridDim.x * blockDim.x) {
     if (k < nd) {
       const int32_t u = row_of(d_off, n, k);
-      dflag[k] = contains(off, adj, u, d_adj[k]) ? 1u : 0u;
+      dflag[k] = contains_key(off, adj, key, u, d_adj[k]) ? 1u : 0u;
     } else {
       const int64_t q = k - nd;
       const int32_t u = row_of(i_off, n, q);
       const int32_t c = i_adj[q];
-      const bool surviving = contains(off, adj, u, c) && !contains(d_off, d_adj, u, c);
+      const bool surviving = contains_key(off, adj, key, u, c) && !contains(d_off, d_adj, u, c);
       iflag[q] = surviving ? 0u : 1u;
     }
   }
@@ -141,7 +166,8 @@ __global__ void k_changed_len(const int32_t* __restrict__ changed, int64_t k, co
 // surviving edge keeps the larger weight.
 __global__ void k_move_changed(const int32_t* __restrict__ changed, int64_t k, const int64_t* __restrict__ cpref,
                                int64_t T, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                               const float* __restrict__ w, const int64_t* __restrict__ d_off,
+                               const int32_t* __restrict__ key, const float* __restrict__ w,
+                               const int64_t* __restrict__ d_off,
                                const int32_t* __restrict__ d_adj, const int64_t* __restrict__ dpref,
                                const int64_t* __restrict__ i_off, const int32_t* __restrict__ i_adj,
                                const float* __restrict__ i_w, const int64_t* __restrict__ ipref,
@@ -166,18 +192,20 @@ __global__ void k_move_changed(const int32_t* __restrict__ changed, int64_t k, c
       const int64_t b = off[u], j = b + (x - cpref[r]);
       const int64_t db = d_off[u], de = d_off[u + 1], ib = i_off[u], ie = i_off[u + 1];
       const int32_t c = adj[j];
-      const int64_t p = lower_bound_i32(d_adj, db, de, c);
-      if (p < de && d_adj[p] == c) continue;  // deleted (a re-insertion is placed by k_place_new)
-      const int64_t qq = lower_bound_i32(i_adj, ib, ie, c);
+      const int32_t ck = key ? key[c] : c;  // the batch lists hold keys
+      const int64_t p = lower_bound_i32(d_adj, db, de, ck);
+      if (p < de && d_adj[p] == ck) continue;  // deleted (a re-insertion is placed by k_place_new)
+      const int64_t qq = lower_bound_i32(i_adj, ib, ie, ck);
       const int64_t pos = noff[u] + (j - b) - (dpref[p] - dpref[db]) + (ipref[qq] - ipref[ib]);
       nadj[pos] = c;
-      if (nw) nw[pos] = (qq < ie && i_adj[qq] == c) ? fmaxf(w[j], i_w[qq]) : w[j];
+      if (nw) nw[pos] = (qq < ie && i_adj[qq] == ck) ? fmaxf(w[j], i_w[qq]) : w[j];
     }
   }
 }
 
 // adding I entries (thread per entry)
 __global__ void k_place_new(int32_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                            const int32_t* __restrict__ key, const int32_t* __restrict__ store,
                             const int64_t* __restrict__ d_off, const int32_t* __restrict__ d_adj,
                             const int64_t* __restrict__ dpref, const int64_t* __restrict__ i_off,
                             const int32_t* __restrict__ i_adj, const float* __restrict__ i_w,
@@ -187,11 +215,11 @@ __global__ void k_place_new(int32_t n, const int64_t* __restrict__ off, const in
     if (!iflag[k]) continue;
     const int32_t u = row_of(i_off, n, k);
     const int32_t c = i_adj[k];
-    const int64_t old_before = lower_bound_i32(adj, off[u], off[u + 1], c) - off[u];
+    const int64_t old_before = lower_bound_key(adj, key, off[u], off[u + 1], c) - off[u];
     const int64_t db = d_off[u];
     const int64_t p = lower_bound_i32(d_adj, db, d_off[u + 1], c);
     const int64_t pos = noff[u] + old_before - (dpref[p] - dpref[db]) + (ipref[k] - ipref[i_off[u]]);
-    nadj[pos] = c;
+    nadj[pos] = store ? store[c] : c;
     if (nw) nw[pos] = i_w[k];
   }
 }
@@ -200,7 +228,7 @@ __global__ void k_place_new(int32_t n, const int64_t* __restrict__ off, const in
 
 int update_csr(int32_t n, const Csr& old, const int32_t* del_rows, const int32_t* del_cols, int64_t n_del,
                const int32_t* ins_rows, const int32_t* ins_cols, const float* ins_w, int64_t n_ins, Csr& out,
-               Workspace& ws, cudaStream_t s) {
+               Workspace& ws, cudaStream_t s, const int32_t* key, const int32_t* store) {
   const bool weighted = old.w.p != nullptr;
   // the batch as two small CSRs over the same rows
   Csr D, I;
@@ -208,7 +236,7 @@ int update_csr(int32_t n, const Csr& old, const int32_t* del_rows, const int32_t
     DBuf<int32_t> dr;
     PRDF_TRY(dr.alloc((size_t)(n_del > 0 ? n_del : 1), s));
     if (n_del > 0) {
-      k_mask_self<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_rows, del_cols, n_del, dr.p);
+      k_mask_self<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_rows, del_cols, n_del, key, dr.p);
       PRDF_LAUNCH_CHECK();
     }
     PRDF_TRY(build_csr(n, n_del, dr.p, del_cols, nullptr, false, true, D, ws, s));
@@ -222,8 +250,8 @@ int update_csr(int32_t n, const Csr& old, const int32_t* del_rows, const int32_t
   PRDF_TRY(dpref.alloc((size_t)nd + 1, s));
   PRDF_TRY(ipref.alloc((size_t)ni + 1, s));
   if (nd + ni > 0) {
-    k_batch_flags<<<grid_for(nd + ni, kThreads), kThreads, 0, s>>>(n, old.off.p, old.adj.p, D.off.p, D.adj.p, nd,
-                                                                   I.off.p, I.adj.p, ni, dflag.p, iflag.p);
+    k_batch_flags<<<grid_for(nd + ni, kThreads), kThreads, 0, s>>>(n, old.off.p, old.adj.p, key, D.off.p, D.adj.p,
+                                                                   nd, I.off.p, I.adj.p, ni, dflag.p, iflag.p);
     PRDF_LAUNCH_CHECK();
   }
   PRDF_TRY(exclusive_scan_u32(dflag.p, nd, dpref.p, ws, s));
@@ -274,13 +302,14 @@ int update_csr(int32_t n, const Csr& old, const int32_t* del_rows, const int32_t
     const int64_t T = ws.host_i64[0];
     if (T > 0) {
       k_move_changed<<<grid_for((T + 7) / 8, kThreads), kThreads, 0, s>>>(
-          changed.p, k, cpref.p, T, old.off.p, old.adj.p, old.w.p, D.off.p, D.adj.p, dpref.p, I.off.p, I.adj.p,
+          changed.p, k, cpref.p, T, old.off.p, old.adj.p, key, old.w.p, D.off.p, D.adj.p, dpref.p, I.off.p, I.adj.p,
           weighted ? I.w.p : nullptr, ipref.p, out.off.p, out.adj.p, out.w.p);
       PRDF_LAUNCH_CHECK();
     }
   }
   if (ni > 0) {
-    k_place_new<<<grid_for(ni, kThreads), kThreads, 0, s>>>(n, old.off.p, old.adj.p, D.off.p, D.adj.p, dpref.p,
+    k_place_new<<<grid_for(ni, kThreads), kThreads, 0, s>>>(n, old.off.p, old.adj.p, key, store, D.off.p, D.adj.p,
+                                                            dpref.p,
                                                             I.off.p, I.adj.p, weighted ? I.w.p : nullptr, iflag.p,
                                                             ipref.p, ni, out.off.p, out.adj.p, out.w.p);
     PRDF_LAUNCH_CHECK();

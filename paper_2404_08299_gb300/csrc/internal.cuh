@@ -57,10 +57,13 @@ int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, c
 // D: (del_rows[i], del_cols[i]), self-loops ignored; I: (ins_rows[i],
 // ins_cols[i]) with weights ins_w when old is weighted (duplicates and
 // re-inserted surviving edges keep the maximum). Equal to a rebuild when
-// every row of old holds its own vertex.
+// every row of old holds its own vertex. Keyed form (key, store not null):
+// old's entries are ordered by key[entry], the batch's columns are keys, an
+// added column c is stored as store[c], and a deletion (r, c) is a self-loop
+// when key[r] == c.
 int update_csr(int32_t n, const Csr& old, const int32_t* del_rows, const int32_t* del_cols, int64_t n_del,
                const int32_t* ins_rows, const int32_t* ins_cols, const float* ins_w, int64_t n_ins, Csr& out,
-               Workspace& ws, cudaStream_t s);
+               Workspace& ws, cudaStream_t s, const int32_t* key = nullptr, const int32_t* store = nullptr);
 
 // The graph renumbered so that each in-degree class is a contiguous id range
 // (new id i = vertex perm[i], perm being the in-degree partition).
@@ -77,7 +80,16 @@ struct Relabel {
   DBuf<int32_t> pout;                // out-degree partition of `out` (new ids), for marking
   int64_t pout_count[kMaxThr + 1] = {};
   bool pout_valid = false;
-  uint64_t version = 0;              // bumped on every rebuild
+  uint64_t version = 0;              // bumped on every rebuild and every batch update
+  // Batch updates keep the numbering: in and out are updated in place (rows
+  // stay ordered by original id), so a vertex's degree may leave its class
+  // bounds. Every kernel handles rows of any length; the one exception is the
+  // class of in-degree <= 1, whose kernel reads no row: a vertex of that class
+  // that gains an in-edge gets its bit in multi (one bit per vertex, cleared by
+  // the next renumbering) and takes the general path.
+  DBuf<uint32_t> multi;
+  int64_t multi_count = 0;           // vertices with their bit set
+  int64_t drift = 0;                 // batch entries applied since the numbering was made
 };
 
 // Rows of the highest in-degree class are cut into chunks of kHubChunk edges
@@ -102,6 +114,8 @@ struct SweepArgs {
   const double* kf;        // DF-P: 1 / (1 - alpha / |out(v)|) (Eq. 2's self-loop factor)
   double alpha, c0;        // damping, (1 - alpha) / n
   int self_loops;          // every vertex has exactly one self-loop (graph built with PRDF_ADD_SELF_LOOPS)
+  const uint32_t* multi;   // null, or a bit per vertex: set for the in-degree <= 1 classes' vertices that
+                           // gained in-edges since the numbering was made (they read their row)
   uint64_t* resid;         // L-inf change of this sweep (bits of a non-negative double), atomic max
   const uint64_t* prev;    // L-inf change of the previous sweep, or null on the first sweep
   double tol;              // the sweep exits at once if *prev <= tol (already converged)
@@ -137,6 +151,7 @@ struct Sweep32Args {
   const float* invf;       // 1 / |out(v)| as float
   float alpha, c0;
   int self_loops;
+  const uint32_t* multi;   // as in SweepArgs
   uint32_t* resid;         // [0]: max |r - R[v]|, [1]: max r of this sweep (FP32 bits, atomic max)
   const uint32_t* prev;    // previous sweep's pair, or null
   float tol_rel;           // the sweep exits at once if prev[0] <= tol_rel * prev[1]
@@ -180,6 +195,13 @@ struct Ppr32Args {
   uint32_t* resid;         // [0] max |R_new - R|, [1] max |R_new| (FP32 bits, atomic max)
   const uint32_t* prev;    // previous sweep's pair or null
   float tol_rel;
+  // device-driven iteration (CUDA graph): when ctl is set, iteration it = ctl[0]
+  // reads R from Ra (even it) or Rb (odd it), writes the other, and uses the
+  // pair resid_base + 2 it (previous: resid_base + 2 (it - 1))
+  const int* ctl;
+  const float* Ra;
+  float* Rb;
+  uint32_t* resid_base;
 };
 struct Ppr64Args {
   const int64_t* off;
@@ -193,6 +215,13 @@ struct Ppr64Args {
   int K;
   double alpha, beta, inv_beta;
   uint64_t* dmax;          // max |T(R) - R| (FP64 bits, atomic max)
+  // device-driven iteration (CUDA graph): when ctl is set, step it = ctl[0]
+  // reads R from Ra (even it) or Rb (odd it), writes the other, and puts its
+  // maximum in dmax_base + it
+  const int* ctl;
+  const double* Ra;
+  double* Rb;
+  uint64_t* dmax_base;
 };
 
 // Owner of a chunk table (PprHub above) of one CSR of the sweep numbering.
@@ -285,9 +314,9 @@ struct prdf_graph {
   bool weighted = false;
   bool self_loops = true;           // every vertex has exactly one self-loop
   cudaStream_t stream = nullptr;
-  prdf::Csr csr[2];                  // [PRDF_OUT] = G, [PRDF_IN] = G'
-  prdf::DBuf<double> outdeg;         // |out(v)| as a double
-  prdf::DBuf<double> inv_outdeg;     // 1 / |out(v)|
+  prdf::Csr csr[2];                  // [PRDF_OUT] = G, [PRDF_IN] = G' in original ids (see orig_valid)
+  bool orig_valid = true;            // false after a batch update until ensure_orig()
+  int64_t m = 0;                     // edges of G (self-loops included)
   prdf::PartThr thr[2];              // class thresholds per CSR
   prdf::DBuf<int32_t> P[2];          // partitions
   int64_t pcount[2][prdf::kMaxThr + 1] = {};
@@ -311,15 +340,15 @@ struct prdf_graph {
   prdf::DBuf<unsigned long long> fwork;  // frontier out-edges of each expansion round
   prdf::DBuf<int> ctl;               // device iteration counter of the graph-driven loop
   cudaStream_t cap_stream = nullptr; // private stream used to capture graph bodies
-  // instantiated sweep loops (CUDA graphs), one per kind of loop: FP32 stage,
-  // dynamic, expanding (index fp32 * 4 + dynamic * 2 + expand), each with the
-  // arguments and buffers it was captured for
-  cudaGraphExec_t loop_exec[8] = {};
-  std::vector<uint64_t> loop_key[8];
+  // instantiated loops (CUDA graphs), one per kind of loop, each with the
+  // arguments and buffers it was captured for: sweep loops at fp32 * 4 +
+  // dynamic * 2 + expand; K-column loops from 8 on
+  cudaGraphExec_t loop_exec[16] = {};
+  std::vector<uint64_t> loop_key[16];
   prdf::Relabel rl;                  // class-contiguous copy used by the sweeps
   // weighted graphs: transition probabilities P_uv = w_uv / sum_k w_uk
   bool ppr_valid = false;
-  prdf::DBuf<double> wsum;           // sum of out-weights per vertex (original ids)
+  prdf::DBuf<double> wsum;           // sum of out-weights per vertex (sweep numbering)
   prdf::DBuf<double> pin64;          // P on the in-edge slots of rl.in
   prdf::DBuf<float> pin32;
   prdf::DBuf<double> pout64;         // P on the out-edge slots of rl.out (adjoint)
@@ -333,4 +362,10 @@ struct prdf_graph {
 namespace prdf {
 int build_relabelled(prdf_graph* g, cudaStream_t s);
 int build_ppr_weights(prdf_graph* g, cudaStream_t s);
+// The CSRs of G and G' in original ids, derived from the sweep numbering's
+// copies when a batch update has changed those (rows come out sorted, as the
+// numbering keeps each row in original-id order).
+int ensure_orig(prdf_graph* g, cudaStream_t s);
+// |out(i)| and 1 / |out(i)| of the sweep numbering from its out-CSR (drops the cached Eq. 2 factor)
+int update_degrees(prdf_graph* g, cudaStream_t s);
 }

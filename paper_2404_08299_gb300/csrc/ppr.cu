@@ -78,6 +78,27 @@ __device__ __forceinline__ void block_max2_u32(uint32_t dmax, uint32_t rmax, uin
   }
 }
 
+// per-iteration buffers of the graph-driven loops
+__device__ __forceinline__ Ppr32Args resolve_ppr32(const Ppr32Args& in) {
+  if (!in.ctl) return in;
+  Ppr32Args a = in;
+  const int it = in.ctl[0];
+  a.R = (it & 1) ? in.Rb : in.Ra;
+  a.Rn = (it & 1) ? const_cast<float*>(in.Ra) : in.Rb;
+  a.resid = in.resid_base + 2 * it;
+  a.prev = it > 0 ? in.resid_base + 2 * (it - 1) : nullptr;
+  return a;
+}
+__device__ __forceinline__ Ppr64Args resolve_ppr64(const Ppr64Args& in) {
+  if (!in.ctl) return in;
+  Ppr64Args a = in;
+  const int it = in.ctl[0];
+  a.R = (it & 1) ? in.Rb : in.Ra;
+  a.Rn = (it & 1) ? const_cast<double*>(in.Ra) : in.Rb;
+  a.dmax = in.dmax_base + it;
+  return a;
+}
+
 __device__ __forceinline__ bool ppr32_converged(const Ppr32Args& a) {
   if (!a.prev) return false;
   return __uint_as_float(a.prev[0]) <= a.tol_rel * __uint_as_float(a.prev[1]);
@@ -210,7 +231,8 @@ __device__ __forceinline__ void merge_slots(Dot2* t) {
 
 // One vertex per slot (rows of at most a few hundred edges), U edges in flight.
 template <int LPE, int U>
-__global__ void __launch_bounds__(kThreads) k_ppr32_group(const Ppr32Args a, int64_t begin, int64_t end, int c0) {
+__global__ void __launch_bounds__(kThreads) k_ppr32_group(const Ppr32Args a_in, int64_t begin, int64_t end, int c0) {
+  const Ppr32Args a = resolve_ppr32(a_in);
   if (ppr32_converged(a)) return;
   constexpr int kSlots = 32 / LPE;
   const int sub = threadIdx.x & (LPE - 1);
@@ -239,7 +261,8 @@ __global__ void __launch_bounds__(kThreads) k_ppr32_group(const Ppr32Args a, int
 // One warp per vertex (mid-degree rows): the slots stride over the row, U
 // edges in flight each, and meet by shuffles.
 template <int LPE, int U>
-__global__ void __launch_bounds__(kThreads) k_ppr32_warp(const Ppr32Args a, int64_t begin, int64_t end, int c0) {
+__global__ void __launch_bounds__(kThreads) k_ppr32_warp(const Ppr32Args a_in, int64_t begin, int64_t end, int c0) {
+  const Ppr32Args a = resolve_ppr32(a_in);
   if (ppr32_converged(a)) return;
   constexpr int kSlots = 32 / LPE;
   const int sub = threadIdx.x & (LPE - 1);
@@ -274,8 +297,9 @@ __global__ void __launch_bounds__(kThreads) k_ppr32_warp(const Ppr32Args a, int6
 // handled by different warps; each chunk's compensated partial sums go to
 // part[chunk][column] and a second kernel merges them in chunk order.
 template <int LPE, int U>
-__global__ void __launch_bounds__(kThreads) k_ppr32_hub_part(const Ppr32Args a, PprHub h, int c0, int tile,
+__global__ void __launch_bounds__(kThreads) k_ppr32_hub_part(const Ppr32Args a_in, PprHub h, int c0, int tile,
                                                              float2* __restrict__ part) {
+  const Ppr32Args a = resolve_ppr32(a_in);
   if (ppr32_converged(a)) return;
   constexpr int kSlots = 32 / LPE;
   const int sub = threadIdx.x & (LPE - 1);
@@ -303,8 +327,9 @@ __global__ void __launch_bounds__(kThreads) k_ppr32_hub_part(const Ppr32Args a, 
 }
 
 template <int LPE>
-__global__ void __launch_bounds__(kThreads) k_ppr32_hub_finish(const Ppr32Args a, PprHub h, int c0, int tile,
+__global__ void __launch_bounds__(kThreads) k_ppr32_hub_finish(const Ppr32Args a_in, PprHub h, int c0, int tile,
                                                                const float2* __restrict__ part) {
+  const Ppr32Args a = resolve_ppr32(a_in);
   if (ppr32_converged(a)) return;
   constexpr int kSlots = 32 / LPE;
   const int sub = threadIdx.x & (LPE - 1);
@@ -452,7 +477,8 @@ __device__ __forceinline__ void merge_slots64(double* t) {
 
 // one vertex per slot (in-degree up to the two highest classes)
 template <int LPE, int U>
-__global__ void __launch_bounds__(kThreads) k_ppr64_group(const Ppr64Args a, int64_t begin, int64_t end, int c0) {
+__global__ void __launch_bounds__(kThreads) k_ppr64_group(const Ppr64Args a_in, int64_t begin, int64_t end, int c0) {
+  const Ppr64Args a = resolve_ppr64(a_in);
   constexpr int kSlots = 32 / LPE;
   const int sub = threadIdx.x & (LPE - 1);
   const int slot = (threadIdx.x & 31) / LPE;
@@ -475,7 +501,8 @@ __global__ void __launch_bounds__(kThreads) k_ppr64_group(const Ppr64Args a, int
 
 // a warp per vertex (mid-degree rows), slots meet by shuffles
 template <int LPE, int U>
-__global__ void __launch_bounds__(kThreads) k_ppr64_warp(const Ppr64Args a, int64_t begin, int64_t end, int c0) {
+__global__ void __launch_bounds__(kThreads) k_ppr64_warp(const Ppr64Args a_in, int64_t begin, int64_t end, int c0) {
+  const Ppr64Args a = resolve_ppr64(a_in);
   constexpr int kSlots = 32 / LPE;
   const int sub = threadIdx.x & (LPE - 1);
   const int slot = (threadIdx.x & 31) / LPE;
@@ -497,8 +524,9 @@ __global__ void __launch_bounds__(kThreads) k_ppr64_warp(const Ppr64Args a, int6
 
 // hub rows in 1024-edge chunks: partial sums per chunk, then merged in chunk order
 template <int LPE, int U>
-__global__ void __launch_bounds__(kThreads) k_ppr64_hub_part(const Ppr64Args a, PprHub h, int c0, int tile,
+__global__ void __launch_bounds__(kThreads) k_ppr64_hub_part(const Ppr64Args a_in, PprHub h, int c0, int tile,
                                                              double* __restrict__ part) {
+  const Ppr64Args a = resolve_ppr64(a_in);
   constexpr int kSlots = 32 / LPE;
   const int sub = threadIdx.x & (LPE - 1);
   const int slot = (threadIdx.x & 31) / LPE;
@@ -522,8 +550,9 @@ __global__ void __launch_bounds__(kThreads) k_ppr64_hub_part(const Ppr64Args a, 
 }
 
 template <int LPE>
-__global__ void __launch_bounds__(kThreads) k_ppr64_hub_finish(const Ppr64Args a, PprHub h, int c0, int tile,
+__global__ void __launch_bounds__(kThreads) k_ppr64_hub_finish(const Ppr64Args a_in, PprHub h, int c0, int tile,
                                                                const double* __restrict__ part) {
+  const Ppr64Args a = resolve_ppr64(a_in);
   constexpr int kSlots = 32 / LPE;
   const int sub = threadIdx.x & (LPE - 1);
   const int slot = (threadIdx.x & 31) / LPE;
@@ -564,7 +593,7 @@ __global__ void k_grad_w(const int64_t* __restrict__ off, const int32_t* __restr
     for (int c = lane; c < K; c += 32) b = fma(Ri[c], lam[i * K + c] - g_scale * Gs[i * K + c], b);
     b = warp_sum_f64(b);
     const int32_t u = perm[i];
-    const double invW = 1.0 / W[u];
+    const double invW = 1.0 / W[i];
     const int64_t rb = off[i], re = off[i + 1], ob = orig_off[u];
     for (int64_t j = rb + lane; j < re; j += 32) {
       const double* Lv = lam + (int64_t)adj[j] * K;

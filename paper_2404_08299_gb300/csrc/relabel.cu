@@ -87,7 +87,7 @@ __global__ void k_perm_rows(const int64_t* __restrict__ off, const int32_t* __re
   }
 }
 
-// sum of out-weights per vertex (original ids), one warp per row
+// sum of out-weights per row, one warp per row
 __global__ void k_row_wsum(const int64_t* __restrict__ off, const float* __restrict__ w, int32_t n,
                            double* __restrict__ W) {
   const int lane = threadIdx.x & 31;
@@ -101,25 +101,25 @@ __global__ void k_row_wsum(const int64_t* __restrict__ off, const float* __restr
   }
 }
 
-// P on the in-slots of the renumbered G': slot (u -> v) gets w_uv / W[u];
-// new_src holds renumbered ids, so W is read through perm
-__global__ void k_pin(const int32_t* __restrict__ new_src, const float* __restrict__ w, const int32_t* __restrict__ perm,
-                      const double* __restrict__ W, int64_t m, double* __restrict__ p64, float* __restrict__ p32) {
+// P on the in-slots of the renumbered G': slot (u -> v) gets w_uv / W[u]
+// (new_src and W in the sweep numbering)
+__global__ void k_pin(const int32_t* __restrict__ new_src, const float* __restrict__ w, const double* __restrict__ W,
+                      int64_t m, double* __restrict__ p64, float* __restrict__ p32) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
-    const double p = (double)w[j] / W[perm[new_src[j]]];
+    const double p = (double)w[j] / W[new_src[j]];
     p64[j] = p;
     p32[j] = (float)p;
   }
 }
 
-// P on the out-slots of the renumbered G: row i (vertex perm[i]) divides by its own W
-__global__ void k_pout(const int64_t* __restrict__ off, const float* __restrict__ w, const int32_t* __restrict__ perm,
-                       const double* __restrict__ W, int32_t n, double* __restrict__ p64, float* __restrict__ p32) {
+// P on the out-slots of the renumbered G: row i divides by its own W
+__global__ void k_pout(const int64_t* __restrict__ off, const float* __restrict__ w, const double* __restrict__ W,
+                       int32_t n, double* __restrict__ p64, float* __restrict__ p32) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < n; i += nwarps) {
-    const double Wi = W[perm[i]];
+    const double Wi = W[i];
     for (int64_t j = off[i] + lane; j < off[i + 1]; j += 32) {
       const double p = (double)w[j] / Wi;
       p64[j] = p;
@@ -128,13 +128,13 @@ __global__ void k_pout(const int64_t* __restrict__ off, const float* __restrict_
   }
 }
 
-__global__ void k_perm_degrees(const double* __restrict__ deg, const double* __restrict__ inv_deg,
-                               const int32_t* __restrict__ perm, int32_t n, double* __restrict__ ndeg,
-                               double* __restrict__ ninv) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = perm[i];
-    ndeg[i] = deg[v];
-    ninv[i] = inv_deg[v];
+// |out(i)| and 1 / |out(i)| from the row lengths of a CSR
+__global__ void k_row_degrees(const int64_t* __restrict__ off, int32_t n, double* __restrict__ deg,
+                              double* __restrict__ inv) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = off[v + 1] - off[v];
+    deg[v] = (double)d;
+    inv[v] = d > 0 ? 1.0 / (double)d : 0.0;
   }
 }
 
@@ -159,9 +159,31 @@ int permute_csr(const Csr& src, const int32_t* perm, const int32_t* inv, int32_t
 
 }  // namespace
 
+int ensure_orig(prdf_graph* g, cudaStream_t s) {
+  if (g->orig_valid) return PRDF_OK;
+  Relabel& r = g->rl;
+  // original row u is row inv[u] of the numbering, its entries mapped back through perm
+  PRDF_TRY(permute_csr(r.out, r.inv.p, r.perm.p, g->n, g->csr[PRDF_OUT], g->ws, s));
+  PRDF_TRY(permute_csr(r.in, r.inv.p, r.perm.p, g->n, g->csr[PRDF_IN], g->ws, s));
+  g->orig_valid = true;
+  g->pvalid[0] = g->pvalid[1] = false;
+  return PRDF_OK;
+}
+
+int update_degrees(prdf_graph* g, cudaStream_t s) {
+  Relabel& r = g->rl;
+  PRDF_TRY(r.degd.reserve((size_t)g->n, s));
+  PRDF_TRY(r.inv_deg.reserve((size_t)g->n, s));
+  k_row_degrees<<<grid_for(g->n, kThreads), kThreads, 0, s>>>(r.out.off.p, g->n, r.degd.p, r.inv_deg.p);
+  PRDF_LAUNCH_CHECK();
+  r.kf_alpha = -1;
+  return PRDF_OK;
+}
+
 int build_relabelled(prdf_graph* g, cudaStream_t s) {
   const int32_t n = g->n;
   Relabel& r = g->rl;
+  PRDF_TRY(ensure_orig(g, s));  // the numbering is made from the original-id CSRs
   // out-degree tiers first (highest first), then a stable in-degree partition
   // of that list: classes by in-degree, tiers inside each class
   DBuf<int32_t> hot;
@@ -179,12 +201,11 @@ int build_relabelled(prdf_graph* g, cudaStream_t s) {
   PRDF_LAUNCH_CHECK();
   PRDF_TRY(permute_csr(g->csr[PRDF_IN], r.perm.p, r.inv.p, n, r.in, g->ws, s));
   PRDF_TRY(permute_csr(g->csr[PRDF_OUT], r.perm.p, r.inv.p, n, r.out, g->ws, s));
-  PRDF_TRY(r.degd.alloc((size_t)n, s));
-  PRDF_TRY(r.inv_deg.alloc((size_t)n, s));
-  k_perm_degrees<<<grid_for(n, kThreads), kThreads, 0, s>>>(g->outdeg.p, g->inv_outdeg.p, r.perm.p, n, r.degd.p,
-                                                            r.inv_deg.p);
-  PRDF_LAUNCH_CHECK();
-  r.kf_alpha = -1;
+  PRDF_TRY(update_degrees(g, s));
+  PRDF_TRY(r.multi.reserve((size_t)n / 32 + 1, s));
+  PRDF_CUDA(cudaMemsetAsync(r.multi.p, 0, sizeof(uint32_t) * ((size_t)n / 32 + 1), s));
+  r.multi_count = 0;
+  r.drift = 0;
   r.valid = true;
   // the out-degree partition of the marking kernels (Alg. partition over G) is
   // made with the numbering, so that DF / DF-P / DT find it ready after a batch
@@ -201,14 +222,14 @@ int build_ppr_weights(prdf_graph* g, cudaStream_t s) {
   const Relabel& r = g->rl;
   const int64_t m = r.in.m;
   PRDF_TRY(g->wsum.alloc((size_t)n, s));
-  k_row_wsum<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(g->csr[PRDF_OUT].off.p, g->csr[PRDF_OUT].w.p, n,
-                                                                       g->wsum.p);
+  // each row holds its vertex's entries in original-id order: the same sum as over the original CSR
+  k_row_wsum<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(r.out.off.p, r.out.w.p, n, g->wsum.p);
   PRDF_TRY(g->pin64.alloc((size_t)m, s));
   PRDF_TRY(g->pin32.alloc((size_t)m, s));
   PRDF_TRY(g->pout64.alloc((size_t)m, s));
   PRDF_TRY(g->pout32.alloc((size_t)m, s));
-  k_pin<<<grid_for(m, kThreads), kThreads, 0, s>>>(r.in.adj.p, r.in.w.p, r.perm.p, g->wsum.p, m, g->pin64.p, g->pin32.p);
-  k_pout<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(r.out.off.p, r.out.w.p, r.perm.p, g->wsum.p, n,
+  k_pin<<<grid_for(m, kThreads), kThreads, 0, s>>>(r.in.adj.p, r.in.w.p, g->wsum.p, m, g->pin64.p, g->pin32.p);
+  k_pout<<<grid_for((int64_t)n * 32, kThreads), kThreads, 0, s>>>(r.out.off.p, r.out.w.p, g->wsum.p, n,
                                                                    g->pout64.p, g->pout32.p);
   PRDF_LAUNCH_CHECK();
   g->ppr_valid = true;

@@ -394,8 +394,10 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
       it.f.dn = a.dN[v];
     }
     const bool live = v >= 0 && dv;
+    // the row is [v] unless a batch gave the vertex in-edges (its bit in multi)
+    const bool self_only = SELF1 && !(live && a.multi && ((a.multi[v >> 5] >> (v & 31)) & 1u));
     if (live) {
-      if (SELF1) {
+      if (self_only) {
         it.b = 0;
         it.e = 1;
       } else {
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       const int64_t j = it.b + lane + (int64_t)k * G;
-      if (SELF1) it.u[k] = (live && k == 0 && lane == 0) ? v : -1;
+      if (self_only) it.u[k] = (live && k == 0 && lane == 0) ? v : -1;
       else it.u[k] = (live && j < it.e) ? ld_stream_i32(a.adj + j, pf) : -1;
     }
   };
@@ -455,8 +457,8 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
       }
 #pragma unroll
       for (int k = 0; k < U; ++k) xself = (cur.u[k] == cur.v) ? xv[k] : xself;
-      // rest of a row longer than G*U (not reached with the default classes)
-      if (!SELF1 && cur.e - cur.b > (int64_t)G * U)
+      // rest of a row longer than G*U (rows that grew past their class's bound in a batch update)
+      if (cur.e - cur.b > (int64_t)G * U)
         gather_row<G, U, EXACT>(a, cur.b + (int64_t)G * U, cur.e, lane, cur.v, acc, xself, pf, pl);
     }
     if (G > 1) {

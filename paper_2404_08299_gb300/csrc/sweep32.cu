@@ -259,7 +259,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a_
     Kahan acc;
     uint32_t yself = 0;
     if (active) {
-      if (SELF1) {
+      // the row is [v] unless a batch gave the vertex in-edges (its bit in multi)
+      if (SELF1 && !(a.multi && ((a.multi[v >> 5] >> (v & 31)) & 1u))) {
         yself = lane == 0 ? ld_gather_b32(a.y + v, pl) : 0u;
         if (lane == 0) acc.add(__uint_as_float(yself));
       } else {
