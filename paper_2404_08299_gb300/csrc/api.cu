@@ -1419,7 +1419,9 @@ int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t*
       PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64 + 1, g->counter.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                 s));
     }
-    PRDF_TRY(update_degrees(g, s));
+    // out-degrees change only for the batch's sources: their degrees and Eq. 2 factors are refreshed
+    PRDF_TRY(update_degrees_of(g, del_src, n_del, s));
+    PRDF_TRY(update_degrees_of(g, ins_src, n_ins, s));
     rl.drift += nb;
     ++rl.version;
     g->orig_valid = false;

@@ -368,4 +368,6 @@ int build_ppr_weights(prdf_graph* g, cudaStream_t s);
 int ensure_orig(prdf_graph* g, cudaStream_t s);
 // |out(i)| and 1 / |out(i)| of the sweep numbering from its out-CSR (drops the cached Eq. 2 factor)
 int update_degrees(prdf_graph* g, cudaStream_t s);
+// the same, and the cached Eq. 2 factor, for the rows of the cnt vertices a[] (original ids) only
+int update_degrees_of(prdf_graph* g, const int32_t* a, int64_t cnt, cudaStream_t s);
 }

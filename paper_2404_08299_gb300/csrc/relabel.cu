@@ -157,6 +157,21 @@ int permute_csr(const Csr& src, const int32_t* perm, const int32_t* inv, int32_t
   return PRDF_OK;
 }
 
+// degrees (and the Eq. 2 factor when kf is not null) of the rows of the listed
+// vertices (original ids, mapped through inv); duplicates write equal values
+__global__ void k_row_degrees_of(const int32_t* __restrict__ a, int64_t cnt, const int32_t* __restrict__ inv,
+                                 const int64_t* __restrict__ off, double alpha, double* __restrict__ deg,
+                                 double* __restrict__ inv_deg, double* __restrict__ kf) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < cnt; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = inv[a[k]];
+    const int64_t d = off[i + 1] - off[i];
+    deg[i] = (double)d;
+    inv_deg[i] = d > 0 ? 1.0 / (double)d : 0.0;
+    if (kf) kf[i] = 1.0 / (1.0 - alpha / (double)d);
+  }
+}
+
+
 }  // namespace
 
 int ensure_orig(prdf_graph* g, cudaStream_t s) {
@@ -167,6 +182,16 @@ int ensure_orig(prdf_graph* g, cudaStream_t s) {
   PRDF_TRY(permute_csr(r.in, r.inv.p, r.perm.p, g->n, g->csr[PRDF_IN], g->ws, s));
   g->orig_valid = true;
   g->pvalid[0] = g->pvalid[1] = false;
+  return PRDF_OK;
+}
+
+int update_degrees_of(prdf_graph* g, const int32_t* a, int64_t cnt, cudaStream_t s) {
+  if (cnt <= 0) return PRDF_OK;
+  Relabel& r = g->rl;
+  double* kf = r.kf_alpha >= 0 ? r.kf.p : nullptr;
+  k_row_degrees_of<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(a, cnt, r.inv.p, r.out.off.p, r.kf_alpha, r.degd.p,
+                                                                 r.inv_deg.p, kf);
+  PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }
 

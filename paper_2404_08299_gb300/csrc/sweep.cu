@@ -356,6 +356,7 @@ struct Item {
   int64_t b, e;
   int32_t u[U];
   Flags f;
+  bool self_only;  // the row is [v] (in-degree <= 1 class, no in-edges added since the numbering)
 };
 
 // G lanes per vertex (G = 1, 4, 16), U indices per lane per round. The loop is
@@ -396,6 +397,7 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
     const bool live = v >= 0 && dv;
     // the row is [v] unless a batch gave the vertex in-edges (its bit in multi)
     const bool self_only = SELF1 && !(live && a.multi && ((a.multi[v >> 5] >> (v & 31)) & 1u));
+    it.self_only = self_only;
     if (live) {
       if (self_only) {
         it.b = 0;
@@ -442,6 +444,15 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
     if (DYN && active && !cur.f.dv) {
       if (lane == 0) skip_vertex(a, cur.v, cur.f);
       active = false;
+    }
+    if (SELF1 && cur.self_only) {
+      // row [v] (one lane per item): the in-neighbour sum is the single term x[v], exactly
+      if (active) {
+        const uint64_t db = finish_vertex<DYN>(a, cur.v, bitsd(xv[0]), xv[0], pf, fwsum, cur.f.dn);
+        dmax = db > dmax ? db : dmax;
+      }
+      cur = nxt;
+      continue;
     }
     Acc<EXACT> acc;
     uint64_t xself = 0;
