@@ -35,6 +35,8 @@ WORKLOADS = {
                                        "self-loops; Static FP64, alpha 0.85, tol 1e-10 L-inf"),
     "rmat16": ("rmat", (16, 1 << 20), "R-MAT 2^16 vertices, 2^20 samples seed 1, dedup + self-loops; "
                                       "Static FP64, alpha 0.85, tol 1e-10 L-inf"),
+    "rmat22": ("rmat", (22, 1 << 26), "R-MAT 2^22 vertices, 2^26 samples seed 1, dedup + self-loops; "
+                                      "Static FP64, alpha 0.85, tol 1e-10 L-inf (the size profiles are captured on)"),
 }
 
 
@@ -613,6 +615,7 @@ def main():
     ap.add_argument("--ppr-oracle-cols", type=int, nargs="*", default=[0, 63],
                     help="columns of the K = 64 job checked against the oracle (none: skip)")
     ap.add_argument("--ppr-single", type=int, default=1, help="also solve the 64 columns one per call (K = 1)")
+    ap.add_argument("--no-ppr", action="store_true", help="skip the K-column PPR and adjoint side measurement")
     ap.add_argument("--profile-dfp", type=float, default=0.0,
                     help="build the 2^22 R-MAT, solve Static, apply one random batch of this fraction of |E| and run "
                          "DF-P once (for ncu captures of the build, batch-update, marking and DF-P sweep kernels)")
@@ -798,7 +801,8 @@ def main():
     if not args.no_extras:
         del g
         torch.cuda.empty_cache()
-        extras["ppr_adjoint"] = measure_ppr(args)
+        if not args.no_ppr:
+            extras["ppr_adjoint"] = measure_ppr(args)
         if args.temporal_batches > 0:
             extras["temporal"] = measure_temporal(args)
 

@@ -188,7 +188,7 @@ class Graph:
                                        _ptr(w, torch.float32, m0, "w"), m0,
                                        PRDF_ADD_SELF_LOOPS if self_loops else 0, _stream(), ctypes.byref(h)))
         self._h = h
-        self.weighted = w is not None
+        self.weighted = w is not None and m0 > 0  # an empty tensor passes NULL: an unweighted graph
 
     def __del__(self):
         h = getattr(self, "_h", None)

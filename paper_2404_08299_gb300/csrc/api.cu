@@ -1366,14 +1366,14 @@ int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t*
   PRDF_TRY(check_inputs(g, del_src, del_dst, n_del, ins_src, ins_dst, n_ins, nullptr, nullptr, s));
   const int32_t n = g->n;
   Relabel& rl = g->rl;
-  if (g->self_loops && rl.valid) {
+  const int64_t nb = n_del + n_ins;
+  if (g->self_loops && rl.valid && (rl.drift + nb) * 64 <= g->m) {
     // Every vertex already has its self-loop: each row of G and of G' becomes
     // (old \ D) u I, merged in order (batch_update.cu), directly on the copies
     // in the sweep numbering (rows ordered by original id, columns compared
     // through perm). The numbering, its partitions and the chunk tables are
     // kept; the original-id CSRs are derived again when asked for.
     DBuf<int32_t> rows;
-    const int64_t nb = n_del + n_ins;
     PRDF_TRY(rows.alloc((size_t)(2 * nb > 0 ? 2 * nb : 1), s));
     int32_t* del_r_out = rows.p;           // inv[del_src]
     int32_t* del_r_in = rows.p + n_del;    // inv[del_dst]
@@ -1429,21 +1429,21 @@ int prdf_graph_apply_batch(prdf_graph* g, const int32_t* del_src, const int32_t*
     g->ppr_valid = false;
     PRDF_CUDA(cudaStreamSynchronize(s));
     if (self1 && n_ins) rl.multi_count += g->ws.host_i64[1];
-    // a fresh numbering once the batches applied since the last one add up to
-    // 1/64 of the edges (degree classes and out-degree tiers drift)
-    if (rl.drift * 64 > g->m) {
-      PRDF_TRY(build_relabelled(g, s));
-      PRDF_CUDA(cudaStreamSynchronize(s));
-    }
     return PRDF_OK;
   }
-  // Graphs made without self-loops: rebuild from the edge list (which also
-  // gives every vertex its self-loop) and renumber.
+  // A fresh numbering is due: the batches applied since the last one, this
+  // one included, add up to more than 1/64 of the edges (degree classes and
+  // out-degree tiers drift), or the graph was made without self-loops. The
+  // rows are merged on the original-id CSRs (or rebuilt from the edge list,
+  // which also gives every vertex its self-loop) and then renumbered.
   PRDF_TRY(ensure_orig(g, s));
   Csr& old = g->csr[PRDF_OUT];
   const int64_t m = old.m;
   Csr nout, nin;
-  {
+  if (g->self_loops) {
+    PRDF_TRY(update_csr(n, g->csr[PRDF_OUT], del_src, del_dst, n_del, ins_src, ins_dst, ins_w, n_ins, nout, g->ws, s));
+    PRDF_TRY(update_csr(n, g->csr[PRDF_IN], del_dst, del_src, n_del, ins_dst, ins_src, ins_w, n_ins, nin, g->ws, s));
+  } else {
     DBuf<uint8_t> deleted;
     PRDF_TRY(deleted.alloc((size_t)m, s));
     PRDF_CUDA(cudaMemsetAsync(deleted.p, 0, (size_t)m, s));

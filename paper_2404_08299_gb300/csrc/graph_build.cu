@@ -521,6 +521,8 @@ int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, c
       return PRDF_EINVAL;
     }
   }
+  if (radix_build_applies(n, m0, w, allow_skip, self_loops))
+    return build_csr_radix(n, m0, rows, cols, self_loops, out, ws, s);
   const int64_t N = n;
   DBuf<uint32_t> cnt, fill, ucnt;
   DBuf<int64_t> start;

@@ -51,6 +51,11 @@ struct Csr {
 // (optional) of merged duplicates: maximum; added self-loops: 1.0.
 int build_csr(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, const float* w, bool self_loops,
               bool allow_skip, Csr& out, Workspace& ws, cudaStream_t s);
+// The same CSR by a radix sort of packed (row, column) keys (radix_build.cu):
+// unweighted lists without skipped entries, m0 + n < 2^32; ids already checked.
+bool radix_build_applies(int32_t n, int64_t m0, const float* w, bool allow_skip, bool self_loops);
+int build_csr_radix(int32_t n, int64_t m0, const int32_t* rows, const int32_t* cols, bool self_loops, Csr& out,
+                    Workspace& ws, cudaStream_t s);
 
 // Batch update of one CSR with set semantics (Sec. 3.3): out gets rows
 // (old \ D) u I in column order, merged without re-sorting (batch_update.cu).

@@ -39,15 +39,41 @@ def check_csr(g, og):
     assert np.array_equal(host(adj), og.in_adj)
 
 
+def ones(src, weighted):
+    """Unit weights for the weighted form of a build: unweighted lists take the radix-sort build,
+    weighted ones the per-row sort; both must give the oracle's CSR."""
+    return np.ones(len(src), np.float32) if weighted else None
+
+
+@pytest.mark.parametrize("weighted", [False, True])
 @pytest.mark.parametrize("name,n,src,dst", adversarial_edges())
-def test_csr_build_adversarial(name, n, src, dst):
-    check_csr(gpu_graph(n, src, dst), oracle.graph(n, src, dst))
+def test_csr_build_adversarial(name, n, src, dst, weighted):
+    check_csr(gpu_graph(n, src, dst, ones(src, weighted)), oracle.graph(n, src, dst))
 
 
+@pytest.mark.parametrize("weighted", [False, True])
 @pytest.mark.parametrize("scale,nsamp", [(10, 16000), (16, 1 << 20)])
-def test_csr_build_rmat(scale, nsamp):
+def test_csr_build_rmat(scale, nsamp, weighted):
     n, s, d = synth.rmat(scale, nsamp, seed=1)
+    check_csr(gpu_graph(n, s, d, ones(s, weighted)), oracle.graph(n, s, d))
+
+
+@pytest.mark.parametrize("n,m0", [(3, 1), (1000, 4096 - 1000), (1000, 4097 - 1000), (70001, 500000),
+                                  ((1 << 17) + 3, 1 << 20)])
+def test_csr_build_radix_sizes(n, m0):
+    """Radix-sort build at vertex counts that are not powers of two (key widths of 2 to 18 bits a field,
+    one to five passes) and at key counts of exactly one 4096-key tile and one key more; random ids with many
+    duplicates and runs of empty rows in the no-self-loop form."""
+    rng = np.random.default_rng(n + m0)
+    s = (rng.integers(0, n, m0) if n < 1000 else rng.zipf(1.3, m0) % n).astype(np.int32)
+    d = rng.integers(0, n, m0).astype(np.int32)
     check_csr(gpu_graph(n, s, d), oracle.graph(n, s, d))
+    g = prdf().Graph(n, dev(s), dev(d), self_loops=False)
+    P = prdf()
+    for which, (r, c) in ((P.PRDF_OUT, (s, d)), (P.PRDF_IN, (d, s))):
+        off, adj, _ = g.export_csr(which)
+        want_off, want_adj = oracle.csr_build(n, r, c, self_loops=False)
+        assert np.array_equal(host(off), want_off) and np.array_equal(host(adj), want_adj)
 
 
 def test_builds_after_releasing_the_memory_pool():
@@ -63,14 +89,16 @@ def test_builds_after_releasing_the_memory_pool():
     check_csr(gpu_graph(n, s, d), og)
 
 
-def test_csr_build_grid():
+@pytest.mark.parametrize("weighted", [False, True])
+def test_csr_build_grid(weighted):
     n, s, d = synth.grid(128, 0.05, seed=1)
-    check_csr(gpu_graph(n, s, d), oracle.graph(n, s, d))
+    check_csr(gpu_graph(n, s, d, ones(s, weighted)), oracle.graph(n, s, d))
 
 
-def test_csr_build_bitmap_and_block_rows():
+@pytest.mark.parametrize("weighted", [False, True])
+def test_csr_build_bitmap_and_block_rows(weighted):
     n, s, d = huge_row_edges()
-    g = gpu_graph(n, s, d)
+    g = gpu_graph(n, s, d, ones(s, weighted))
     og = oracle.graph(n, s, d)
     check_csr(g, og)
     assert np.diff(og.out_off).max() > 16384 and np.diff(og.in_off).max() > 16384
