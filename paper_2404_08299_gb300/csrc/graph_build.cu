@@ -2,7 +2,9 @@
 // (Section 4.1, 4.3 of arXiv 2404.08299) from an edge list, with duplicate
 // edges merged and exactly one self-loop per vertex (Section 3.1, 5.1.3).
 //
-// Pipeline (all hand-written kernels):
+// Unweighted lists without skipped entries take the radix-sort build of
+// radix_build.cu. This pipeline serves weighted lists (duplicates keep the
+// largest weight) and lists with skipped entries (all hand-written kernels):
 //   row histogram -> exclusive scan -> atomic scatter into row buckets ->
 //   per-row sort + unique, by row-length class:
 //     <= 8      one thread, 19-comparator sorting network in registers
