@@ -124,35 +124,53 @@ __device__ __forceinline__ void gather_row(const SweepArgs& a, int64_t b, int64_
 }
 
 // Vectorised variant for a row handled by NT lanes: 16-byte index loads for
-// the aligned body (KV of them in flight per lane), scalar head and tail.
-template <int NT, int KV, bool EXACT, bool SELF = true>
-__device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, int64_t e, int lane, int32_t v,
-                                               Acc<EXACT>& acc, uint64_t& xself, uint64_t pf, uint64_t pl) {
+// the aligned body (KV of them in flight per lane), scalar head and tail;
+// row_indices issues a row's first indices, gather_row_from consumes them.
+// (A warp kernel that loaded the next row's first indices a turn ahead needed
+// 76 registers, ran three blocks per SM instead of four and was 4 % slower.)
+template <int KV>
+struct RowIdx {
+  int64_t ba = 0, ea = 0;  // aligned body [ba, ea)
+  int32_t uh = -1;         // this lane's head or tail entry (the unaligned ends), -1: none
+  int4 u4[KV];             // this lane's first body indices
+};
+
+template <int NT, int KV>
+__device__ __forceinline__ void row_indices(const SweepArgs& a, int64_t b, int64_t e, int lane, uint64_t pf,
+                                            RowIdx<KV>& r) {
   int64_t ba = (b + 3) & ~(int64_t)3;
   if (ba > e) ba = e;
   const int64_t ea = ba + ((e - ba) & ~(int64_t)3);
-  {
-    const int64_t nh = ba - b, nt = e - ea;
-    int64_t j = -1;
-    if (lane < nh) j = b + lane;
-    else if (lane >= 4 && lane < 4 + nt) j = ea + (lane - 4);
-    if (j >= 0) {
-      const int32_t u = ld_stream_i32(a.adj + j, pf);
-      const uint64_t xv = ld_gather_b64(a.x + u, pl);
-      acc.add(xv);
-      if (SELF) xself = (u == v) ? xv : xself;
-    }
-  }
-  // body: the next chunk's indices are loaded while this chunk's gathers are
-  // in flight. The loop runs the same trip count on all NT lanes, so each
-  // warp is converged at the vote below.
-  const int64_t step = 4 * (int64_t)NT * KV;
-  int4 u4[KV];
+  r.ba = ba;
+  r.ea = ea;
+  const int64_t nh = ba - b, nt = e - ea;
+  int64_t j = -1;
+  if (lane < nh) j = b + lane;
+  else if (lane >= 4 && lane < 4 + nt) j = ea + (lane - 4);
+  r.uh = j >= 0 ? ld_stream_i32(a.adj + j, pf) : -1;
 #pragma unroll
   for (int k = 0; k < KV; ++k) {
     const int64_t q = ba + 4 * (int64_t)lane + 4 * (int64_t)NT * k;
-    u4[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
+    r.u4[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
   }
+}
+
+// The head / tail term's gather is issued with the body's first gathers and
+// added after them, so the row costs one gather round trip before its first
+// add. The body loads the next chunk's indices while this chunk's gathers are
+// in flight; the loop runs the same trip count on all NT lanes, so each warp
+// is converged at the vote below.
+template <int NT, int KV, bool EXACT, bool SELF = true>
+__device__ __forceinline__ void gather_row_from(const SweepArgs& a, const RowIdx<KV>& r, int lane, int32_t v,
+                                                Acc<EXACT>& acc, uint64_t& xself, uint64_t pf, uint64_t pl) {
+  const int64_t ba = r.ba, ea = r.ea;
+  const int32_t uh = r.uh;
+  const int64_t step = 4 * (int64_t)NT * KV;
+  int4 u4[KV];
+#pragma unroll
+  for (int k = 0; k < KV; ++k) u4[k] = r.u4[k];
+  uint64_t xh = uh >= 0 ? ld_gather_b64(a.x + uh, pl) : 0ull;
+  bool head = uh >= 0;  // the head term is still to be added
   for (int64_t base = ba; base < ea; base += step) {
     const int64_t q0 = base + 4 * (int64_t)lane;
     uint64_t xv[4 * KV];
@@ -168,6 +186,11 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
     for (int k = 0; k < KV; ++k) {
       const int64_t q = q0 + step + 4 * (int64_t)NT * k;
       nx[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
+    }
+    if (head) {
+      acc.add(xh);
+      if (SELF) xself = (uh == v) ? xh : xself;
+      head = false;
     }
     bool w1 = true;
 #pragma unroll
@@ -202,6 +225,18 @@ __device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, in
 #pragma unroll
     for (int k = 0; k < KV; ++k) u4[k] = nx[k];
   }
+  if (head) {  // rows without a body chunk
+    acc.add(xh);
+    if (SELF) xself = (uh == v) ? xh : xself;
+  }
+}
+
+template <int NT, int KV, bool EXACT, bool SELF = true>
+__device__ __forceinline__ void gather_row_vec(const SweepArgs& a, int64_t b, int64_t e, int lane, int32_t v,
+                                               Acc<EXACT>& acc, uint64_t& xself, uint64_t pf, uint64_t pl) {
+  RowIdx<KV> r;
+  row_indices<NT, KV>(a, b, e, lane, pf, r);
+  gather_row_from<NT, KV, EXACT, SELF>(a, r, lane, v, acc, xself, pf, pl);
 }
 
 // Exact integer value of an out-degree held as a double (an integer below
@@ -415,6 +450,26 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
     }
   };
 
+  // Static form: the row offsets run one more step ahead (offsets of the item
+  // two steps ahead, indices of the next), so a step waits for one round trip
+  constexpr bool kOffAhead = !DYN && !SELF1;
+  auto load_off = [&](int32_t v, int64_t& b, int64_t& e) {
+    b = v >= 0 ? ld_stream_i64(a.off + v, pf) : 0;
+    e = v >= 0 ? ld_stream_i64(a.off + v + 1, pf) : 0;
+  };
+  auto load_idx = [&](int32_t v, int64_t b, int64_t e, Item<U>& it) {
+    it.v = v;
+    it.b = b;
+    it.e = e;
+    it.f = Flags();
+    it.self_only = false;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t j = b + lane + (int64_t)k * G;
+      it.u[k] = (v >= 0 && j < e) ? ld_stream_i32(a.adj + j, pf) : -1;
+    }
+  };
+
   int64_t base = begin + warp * kGroupsPerWarp;
   Item<U> cur;
   {
@@ -423,6 +478,8 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
   }
   int32_t v_next = load_v(base + step + gw);
   uint8_t dv_next = load_dv(v_next);
+  int64_t nb = 0, ne = 0;  // kOffAhead: row offsets of v_next
+  if (kOffAhead) load_off(v_next, nb, ne);
   for (; base < end; base += step) {
     // gathers of the current item
     uint64_t xv[U];
@@ -430,9 +487,15 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
     for (int k = 0; k < U; ++k) xv[k] = cur.u[k] >= 0 ? ld_gather_b64(a.x + cur.u[k], pl) : 0ull;
     // prefetch: next item's row, first indices and flags, and the list entry (and flag) after it
     Item<U> nxt;
-    load_item(v_next, dv_next, nxt);
-    v_next = load_v(base + 2 * step + gw);
-    dv_next = load_dv(v_next);
+    if (kOffAhead) {
+      load_idx(v_next, nb, ne, nxt);
+      v_next = load_v(base + 2 * step + gw);
+      load_off(v_next, nb, ne);
+    } else {
+      load_item(v_next, dv_next, nxt);
+      v_next = load_v(base + 2 * step + gw);
+      dv_next = load_dv(v_next);
+    }
 
     // the warp is converged here (uniform loop): one vote picks the
     // three-word add when every gathered term of the step is in the common window
