@@ -74,31 +74,37 @@ __device__ __forceinline__ void gather32(const Sweep32Args& a, int64_t b, int64_
   }
 }
 
+// Row handled by NT lanes: 16-byte index loads for the aligned body (KV of
+// them in flight per lane), scalar head and tail. The head / tail term's
+// index is loaded with the body's first indices and its gather issued with
+// the body's first gathers (added after them), and each chunk's gathers are
+// in flight while the next chunk's indices load, so a row costs one index and
+// one gather round trip before its first add, as in the FP64 sweep.
 template <int NT, int KV>
 __device__ __forceinline__ void gather32_vec(const Sweep32Args& a, int64_t b, int64_t e, int lane, int32_t v,
                                              Kahan& acc, uint32_t& yself, uint64_t pf, uint64_t pl) {
   int64_t ba = (b + 3) & ~(int64_t)3;
   if (ba > e) ba = e;
   const int64_t ea = ba + ((e - ba) & ~(int64_t)3);
+  int32_t uh = -1;
   {
     const int64_t nh = ba - b, nt = e - ea;
     int64_t j = -1;
     if (lane < nh) j = b + lane;
     else if (lane >= 4 && lane < 4 + nt) j = ea + (lane - 4);
-    if (j >= 0) {
-      const int32_t u = ld_stream_i32(a.adj + j, pf);
-      const uint32_t yv = ld_gather_b32(a.y + u, pl);
-      acc.add(__uint_as_float(yv));
-      yself = (u == v) ? yv : yself;
-    }
+    if (j >= 0) uh = ld_stream_i32(a.adj + j, pf);
   }
-  for (int64_t q0 = ba + 4 * (int64_t)lane; q0 < ea; q0 += 4 * (int64_t)NT * KV) {
-    int4 u4[KV];
+  const int64_t step = 4 * (int64_t)NT * KV;
+  int4 u4[KV];
 #pragma unroll
-    for (int k = 0; k < KV; ++k) {
-      const int64_t q = q0 + 4 * (int64_t)NT * k;
-      u4[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
-    }
+  for (int k = 0; k < KV; ++k) {
+    const int64_t q = ba + 4 * (int64_t)lane + 4 * (int64_t)NT * k;
+    u4[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
+  }
+  const uint32_t yh = uh >= 0 ? ld_gather_b32(a.y + uh, pl) : 0u;
+  bool head = uh >= 0;
+  for (int64_t base = ba; base < ea; base += step) {
+    const int64_t q0 = base + 4 * (int64_t)lane;
     uint32_t yv[4 * KV];
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
@@ -107,9 +113,20 @@ __device__ __forceinline__ void gather32_vec(const Sweep32Args& a, int64_t b, in
       yv[4 * k + 2] = u4[k].z >= 0 ? ld_gather_b32(a.y + u4[k].z, pl) : 0u;
       yv[4 * k + 3] = u4[k].w >= 0 ? ld_gather_b32(a.y + u4[k].w, pl) : 0u;
     }
+    int4 nx[KV];
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
-      if (u4[k].x < 0) continue;
+      const int64_t q = q0 + step + 4 * (int64_t)NT * k;
+      nx[k] = q < ea ? ld_stream_i32x4(a.adj + q, pf) : make_int4(-1, -1, -1, -1);
+    }
+    if (head) {
+      acc.add(__uint_as_float(yh));
+      yself = (uh == v) ? yh : yself;
+      head = false;
+    }
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      if (u4[k].x < 0) continue;  // a whole int4 is valid or not
       acc.add(__uint_as_float(yv[4 * k + 0]));
       acc.add(__uint_as_float(yv[4 * k + 1]));
       acc.add(__uint_as_float(yv[4 * k + 2]));
@@ -119,6 +136,12 @@ __device__ __forceinline__ void gather32_vec(const Sweep32Args& a, int64_t b, in
       yself = (u4[k].z == v) ? yv[4 * k + 2] : yself;
       yself = (u4[k].w == v) ? yv[4 * k + 3] : yself;
     }
+#pragma unroll
+    for (int k = 0; k < KV; ++k) u4[k] = nx[k];
+  }
+  if (head) {  // rows without a body chunk
+    acc.add(__uint_as_float(yh));
+    yself = (uh == v) ? yh : yself;
   }
 }
 
@@ -249,38 +272,108 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a_
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   uint32_t dmax = 0, rmax = 0;
   uint64_t fwsum = 0;
-  for (int64_t base = begin + warp * kGroupsPerWarp; base < end; base += nwarps * kGroupsPerWarp) {
-    const int64_t i = base + gw;
-    bool active = i < end;
-    const int32_t v = (int32_t)i;
-    // every lane of the group reads the flag before the group's shuffles, and
-    // only the group's lane 0 changes it (in finish32, after them)
-    if (DYN && active && skip_unaffected32(a, v)) active = false;
-    Kahan acc;
-    uint32_t yself = 0;
-    if (active) {
-      // the row is [v] unless a batch gave the vertex in-edges (its bit in multi)
-      if (SELF1 && !(a.multi && ((a.multi[v >> 5] >> (v & 31)) & 1u))) {
-        yself = lane == 0 ? ld_gather_b32(a.y + v, pl) : 0u;
-        if (lane == 0) acc.add(__uint_as_float(yself));
-      } else {
-        const int64_t b = ld_stream_i64(a.off + v, pf), e = ld_stream_i64(a.off + v + 1, pf);
-        gather32<G, U>(a, b, e, lane, v, acc, yself, pf, pl);
+  if constexpr (!DYN && !SELF1) {
+    // Static form, pipelined as the FP64 group kernel: while an item's first
+    // G*U gathers are in flight, the next item's first indices and the row
+    // offsets of the item after it load, so a step waits for one round trip.
+    // Each lane adds its terms in the same order as gather32.
+    const int64_t step = nwarps * kGroupsPerWarp;
+    auto row_of = [&](int64_t i) -> int32_t { return i < end ? (int32_t)i : -1; };
+    auto load_off = [&](int32_t v, int64_t& b, int64_t& e) {
+      b = v >= 0 ? ld_stream_i64(a.off + v, pf) : 0;
+      e = v >= 0 ? ld_stream_i64(a.off + v + 1, pf) : 0;
+    };
+    auto load_idx = [&](int32_t v, int64_t b, int64_t e, int32_t (&u)[U]) {
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int64_t j = b + lane + (int64_t)k * G;
+        u[k] = (v >= 0 && j < e) ? ld_stream_i32(a.adj + j, pf) : -1;
+      }
+    };
+    int64_t base = begin + warp * kGroupsPerWarp;
+    int32_t v = row_of(base + gw);
+    int64_t b, e;
+    load_off(v, b, e);
+    int32_t u[U];
+    load_idx(v, b, e, u);
+    int32_t vn = row_of(base + step + gw);
+    int64_t bn, en;
+    load_off(vn, bn, en);
+    for (; base < end; base += step) {
+      uint32_t yv[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) yv[k] = u[k] >= 0 ? ld_gather_b32(a.y + u[k], pl) : 0u;
+      int32_t un[U];
+      load_idx(vn, bn, en, un);
+      const int32_t vnn = row_of(base + 2 * step + gw);
+      int64_t bnn, enn;
+      load_off(vnn, bnn, enn);
+      Kahan acc;
+      uint32_t yself = 0;
+      if (v >= 0) {
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          if (u[k] >= 0) acc.add(__uint_as_float(yv[k]));
+          yself = (u[k] == v) ? yv[k] : yself;
+        }
+        // rest of a row longer than G*U (rows that grew past their class's bound in a batch update)
+        if (e - b > (int64_t)G * U) gather32<G, U>(a, b + (int64_t)G * U, e, lane, v, acc, yself, pf, pl);
+      }
+      if (G > 1) {
+        acc.template group_reduce<G>();
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) yself = max(yself, __shfl_xor_sync(0xffffffffu, yself, o));
+      }
+      if (v >= 0 && lane == 0) {
+        uint32_t db, rb;
+        finish32<DYN>(a, v, acc.value(), yself, pf, db, rb, fwsum);
+        dmax = max(dmax, db);
+        rmax = max(rmax, rb);
+      }
+      v = vn;
+      b = bn;
+      e = en;
+#pragma unroll
+      for (int k = 0; k < U; ++k) u[k] = un[k];
+      vn = vnn;
+      bn = bnn;
+      en = enn;
+    }
+    block_epilogue32<DYN>(a, dmax, rmax, fwsum);
+  } else {
+    for (int64_t base = begin + warp * kGroupsPerWarp; base < end; base += nwarps * kGroupsPerWarp) {
+      const int64_t i = base + gw;
+      bool active = i < end;
+      const int32_t v = (int32_t)i;
+      // every lane of the group reads the flag before the group's shuffles, and
+      // only the group's lane 0 changes it (in finish32, after them)
+      if (DYN && active && skip_unaffected32(a, v)) active = false;
+      Kahan acc;
+      uint32_t yself = 0;
+      if (active) {
+        // the row is [v] unless a batch gave the vertex in-edges (its bit in multi)
+        if (SELF1 && !(a.multi && ((a.multi[v >> 5] >> (v & 31)) & 1u))) {
+          yself = lane == 0 ? ld_gather_b32(a.y + v, pl) : 0u;
+          if (lane == 0) acc.add(__uint_as_float(yself));
+        } else {
+          const int64_t b = ld_stream_i64(a.off + v, pf), e = ld_stream_i64(a.off + v + 1, pf);
+          gather32<G, U>(a, b, e, lane, v, acc, yself, pf, pl);
+        }
+      }
+      if (G > 1) {
+        acc.template group_reduce<G>();
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) yself = max(yself, __shfl_xor_sync(0xffffffffu, yself, o));
+      }
+      if (active && lane == 0) {
+        uint32_t db, rb;
+        finish32<DYN>(a, v, acc.value(), yself, pf, db, rb, fwsum);
+        dmax = max(dmax, db);
+        rmax = max(rmax, rb);
       }
     }
-    if (G > 1) {
-      acc.template group_reduce<G>();
-#pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) yself = max(yself, __shfl_xor_sync(0xffffffffu, yself, o));
-    }
-    if (active && lane == 0) {
-      uint32_t db, rb;
-      finish32<DYN>(a, v, acc.value(), yself, pf, db, rb, fwsum);
-      dmax = max(dmax, db);
-      rmax = max(rmax, rb);
-    }
+    block_epilogue32<DYN>(a, dmax, rmax, fwsum);
   }
-  block_epilogue32<DYN>(a, dmax, rmax, fwsum);
 }
 
 template <int KV, bool DYN>
@@ -293,14 +386,21 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_warp(const Sweep32Args a_i
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   uint32_t dmax = 0, rmax = 0;
   uint64_t fwsum = 0;
-  for (int64_t i = begin + warp; i < end; i += nwarps) {
+  // the next row's offsets load while the current row is gathered
+  int64_t i = begin + warp;
+  int64_t b = i < end ? ld_stream_i64(a.off + i, pf) : 0, e = i < end ? ld_stream_i64(a.off + i + 1, pf) : 0;
+  for (; i < end; i += nwarps) {
     const int32_t v = (int32_t)i;
+    const int64_t inx = i + nwarps;
+    const int64_t bn = inx < end ? ld_stream_i64(a.off + inx, pf) : 0;
+    const int64_t en = inx < end ? ld_stream_i64(a.off + inx + 1, pf) : 0;
     // the flag is the same for the whole warp; lane 0 alone changes it, after the shuffles below
     if (DYN && skip_unaffected32(a, v)) {
       __syncwarp();
+      b = bn;
+      e = en;
       continue;
     }
-    const int64_t b = ld_stream_i64(a.off + v, pf), e = ld_stream_i64(a.off + v + 1, pf);
     Kahan acc;
     uint32_t yself = 0;
     gather32_vec<32, KV>(a, b, e, lane, v, acc, yself, pf, pl);
@@ -313,6 +413,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_warp(const Sweep32Args a_i
       dmax = max(dmax, db);
       rmax = max(rmax, rb);
     }
+    b = bn;
+    e = en;
   }
   block_epilogue32<DYN>(a, dmax, rmax, fwsum);
 }
