@@ -242,18 +242,27 @@ __global__ void __launch_bounds__(kThreads) k_ppr32_group(const Ppr32Args a_in, 
   const int col = c0 + 4 * sub;
   const bool colok = col < a.K;
   uint32_t dmax = 0, rmax = 0;
-  for (int64_t base = begin + warp * kSlots; base < end; base += nwarps * kSlots) {
-    const int64_t i = base + slot;
-    if (i >= end) continue;
-    const int32_t v = (int32_t)i;
-    const int64_t b = a.off[v], e = a.off[v + 1];
-    const Own4 w = ppr32_own(a, v, col);
-    BlockSum acc[4];
-    for (int64_t j0 = b; j0 < e; j0 += U) ppr32_edges<U>(a, j0, 1, e, col, colok, acc);
-    float c[4];
+  // The row offsets of the next vertex a slot takes load while the current
+  // vertex's rows are gathered, so a vertex starts with its offsets known.
+  const int64_t step = nwarps * kSlots;
+  int64_t base = begin + warp * kSlots;
+  int64_t i = base + slot;
+  int64_t b = i < end ? a.off[i] : 0, e = i < end ? a.off[i + 1] : 0;
+  for (; base < end; base += step, i += step) {
+    const int64_t in = i + step;
+    const int64_t bn = in < end ? a.off[in] : 0, en = in < end ? a.off[in + 1] : 0;
+    if (i < end) {
+      const int32_t v = (int32_t)i;
+      const Own4 w = ppr32_own(a, v, col);
+      BlockSum acc[4];
+      for (int64_t j0 = b; j0 < e; j0 += U) ppr32_edges<U>(a, j0, 1, e, col, colok, acc);
+      float c[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) c[q] = acc[q].d.value();
-    ppr32_finish4(a, v, col, c, w, dmax, rmax);
+      for (int q = 0; q < 4; ++q) c[q] = acc[q].d.value();
+      ppr32_finish4(a, v, col, c, w, dmax, rmax);
+    }
+    b = bn;
+    e = en;
   }
   block_max2_u32(dmax, rmax, a.resid);
 }
@@ -272,13 +281,19 @@ __global__ void __launch_bounds__(kThreads) k_ppr32_warp(const Ppr32Args a_in, i
   const int col = c0 + 4 * sub;
   const bool colok = col < a.K;
   uint32_t dmax = 0, rmax = 0;
-  for (int64_t i = begin + warp; i < end; i += nwarps) {
+  // the next row's offsets load while the current row is gathered
+  int64_t i = begin + warp;
+  int64_t b = i < end ? a.off[i] : 0, e = i < end ? a.off[i + 1] : 0;
+  for (; i < end; i += nwarps) {
     const int32_t v = (int32_t)i;
-    const int64_t b = a.off[v], e = a.off[v + 1];
+    const int64_t in = i + nwarps;
+    const int64_t bn = in < end ? a.off[in] : 0, en = in < end ? a.off[in + 1] : 0;
     Own4 w;
     if (slot == 0) w = ppr32_own(a, v, col);
     BlockSum acc[4];
     for (int64_t j0 = b + slot; j0 < e; j0 += (int64_t)kSlots * U) ppr32_edges<U>(a, j0, kSlots, e, col, colok, acc);
+    b = bn;
+    e = en;
     Dot2 t[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) t[q] = acc[q].d;
