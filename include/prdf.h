@@ -207,10 +207,9 @@ int prdf_partition(prdf_graph* g, int which, int32_t* P, int64_t* counts_host, v
  * thresholds as in prdf_graph_set_thresholds (n_thr in 1..3, host array);
  * P: int32[n] device output; counts_host: host int64[n_thr+1] output.
  * n must be in [1, 16777216]; larger n returns PRDF_EINVAL with a message.
- * The first call on each device looks the scratch's device address up
- * (make it before any stream capture) and keeps it for the life of the
- * process, so calls after a reset of that device (cudaDeviceReset) are not
- * supported. Calls share the scratch: calls that overlap on the GPU race and
+ * The first call on each device looks the scratch's device address up and
+ * keeps it for the life of the process, so calls after a reset of that
+ * device (cudaDeviceReset) are not supported. Calls share the scratch: calls that overlap on the GPU race and
  * must be serialised by the caller. Returns after the results are complete
  * on `stream`.
  */

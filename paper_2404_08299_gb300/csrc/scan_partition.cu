@@ -252,10 +252,9 @@ int partition_list(const int64_t* off, const int32_t* in, int64_t n, const PartT
 //
 // The array's name means nothing as a device address in host code, so the
 // first call on each device (with that device current) looks its address up
-// with cudaGetSymbolAddress and caches it for the life of the process; make
-// that first call before any stream capture. A reset of the device
-// (cudaDeviceReset) would leave the cached address stale, so calls after one
-// are not supported. All calls share the one array, which keeps the last call's
+// with cudaGetSymbolAddress and caches it for the life of the process. A
+// reset of the device (cudaDeviceReset) would leave the cached address
+// stale, so calls after one are not supported. All calls share the one array, which keeps the last call's
 // contents: each call overwrites every entry it reads before reading it, so
 // nothing needs clearing, but calls that overlap on the GPU (other streams,
 // other threads) race on it and must be serialised by the caller.
