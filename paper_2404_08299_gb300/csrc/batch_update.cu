@@ -67,12 +67,22 @@ __device__ __forceinline__ int32_t row_of(const int64_t* off, int32_t n, int64_t
   return lo;
 }
 
-// deletion rows with self-loops masked out (self-loops are never deleted; a
-// row id r is compared through key when the columns are original ids)
-__global__ void k_mask_self(const int32_t* __restrict__ r, const int32_t* __restrict__ c, int64_t cnt,
-                            const int32_t* __restrict__ key, int32_t* __restrict__ out) {
+// flag[i] = deletion i is not a self-loop (self-loops are never deleted)
+__global__ void k_not_self(const int32_t* __restrict__ r, const int32_t* __restrict__ c, int64_t cnt,
+                           const int32_t* __restrict__ key, uint32_t* __restrict__ flag) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (key ? key[r[i]] : r[i]) == c[i] ? -1 : r[i];
+    flag[i] = (key ? key[r[i]] : r[i]) == c[i] ? 0u : 1u;
+}
+
+// the flagged pairs, in order, at their scanned positions
+__global__ void k_keep_pairs(const int32_t* __restrict__ r, const int32_t* __restrict__ c, int64_t cnt,
+                             const uint32_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                             int32_t* __restrict__ ro, int32_t* __restrict__ co) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+    if (flag[i]) {
+      ro[pos[i]] = r[i];
+      co[pos[i]] = c[i];
+    }
 }
 
 // dflag[k] = D entry k is in the old row; iflag[k] = I entry k adds an element
@@ -132,14 +142,24 @@ __global__ void k_copy_unchanged(int32_t n, int64_t m, const int64_t* __restrict
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t tail_shift = noff[n] - off[n];
-  for (int64_t base = warp * 256; base < m; base += nwarps * 256) {
-    // t = number of changed rows that start at or before base
+  // a warp takes a contiguous run of 256-entry windows: one binary search for
+  // its first window, then the changed-row cursor only moves forward
+  const int64_t nwin = (m + 255) >> 8;
+  const int64_t per = (nwin + nwarps - 1) / nwarps;
+  const int64_t win_end = (warp + 1) * per < nwin ? (warp + 1) * per : nwin;
+  int64_t t = 0;  // number of changed rows that start at or before the window's base
+  if (warp * per < win_end) {
+    const int64_t base0 = (warp * per) << 8;
     int64_t lo = 0, hi = k;
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
-      if (off[changed[mid]] <= base) lo = mid + 1; else hi = mid;
+      if (off[changed[mid]] <= base0) lo = mid + 1; else hi = mid;
     }
-    int64_t t = lo;
+    t = lo;
+  }
+  for (int64_t win = warp * per; win < win_end; ++win) {
+    const int64_t base = win << 8;
+    while (t < k && off[changed[t]] <= base) ++t;
     // the common case: the window [base, base + 256) lies between the end of changed row t - 1 and the start
     // of changed row t, so every entry moves by the same shift (no per-entry tests, all loads in flight)
     const int64_t seg_b = t > 0 ? off[changed[t - 1] + 1] : 0;
@@ -195,14 +215,23 @@ __global__ void k_move_changed(const int32_t* __restrict__ changed, int64_t k, c
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 256; base < T; base += nwarps * 256) {
-    // r = the changed row holding entry base: the last r with cpref[r] <= base
+  // a warp takes a contiguous run of 256-entry windows: one binary search for
+  // its first window, then the row cursor only moves forward
+  const int64_t nwin = (T + 255) >> 8;
+  const int64_t per = (nwin + nwarps - 1) / nwarps;
+  const int64_t win_end = (warp + 1) * per < nwin ? (warp + 1) * per : nwin;
+  int64_t r = 0;  // the changed row holding the entry: the last r with cpref[r] <= entry
+  if (warp * per < win_end) {
+    const int64_t base0 = (warp * per) << 8;
     int64_t lo = 0, hi = k;
     while (hi - lo > 1) {
       const int64_t mid = (lo + hi) >> 1;
-      if (cpref[mid] <= base) lo = mid; else hi = mid;
+      if (cpref[mid] <= base0) lo = mid; else hi = mid;
     }
-    int64_t r = lo;
+    r = lo;
+  }
+  for (int64_t win = warp * per; win < win_end; ++win) {
+    const int64_t base = win << 8;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int64_t x = base + lane + 32 * q;
@@ -637,13 +666,30 @@ int update_csr(int32_t n, const Csr& old, const int32_t* del_rows, const int32_t
   // the batch as two small CSRs over the same rows
   Csr D, I;
   {
-    DBuf<int32_t> dr;
-    PRDF_TRY(dr.alloc((size_t)(n_del > 0 ? n_del : 1), s));
+    // self-loop deletions are dropped first, so that D is built from a plain
+    // list (the radix-sort build)
+    DBuf<uint32_t> keep;
+    DBuf<int64_t> kpos;
+    DBuf<int32_t> dr, dc;
+    int64_t nk = 0;
     if (n_del > 0) {
-      k_mask_self<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_rows, del_cols, n_del, key, dr.p);
+      PRDF_TRY(keep.alloc((size_t)n_del, s));
+      PRDF_TRY(kpos.alloc((size_t)n_del + 1, s));
+      k_not_self<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_rows, del_cols, n_del, key, keep.p);
+      PRDF_LAUNCH_CHECK();
+      PRDF_TRY(exclusive_scan_u32(keep.p, n_del, kpos.p, ws, s));
+      PRDF_CUDA(cudaMemcpyAsync(ws.host_i64, kpos.p + n_del, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      PRDF_CUDA(cudaStreamSynchronize(s));
+      nk = ws.host_i64[0];
+    }
+    PRDF_TRY(dr.alloc((size_t)(nk > 0 ? nk : 1), s));
+    PRDF_TRY(dc.alloc((size_t)(nk > 0 ? nk : 1), s));
+    if (nk > 0) {
+      k_keep_pairs<<<grid_for(n_del, kThreads), kThreads, 0, s>>>(del_rows, del_cols, n_del, keep.p, kpos.p, dr.p,
+                                                                  dc.p);
       PRDF_LAUNCH_CHECK();
     }
-    PRDF_TRY(build_csr(n, n_del, dr.p, del_cols, nullptr, false, true, D, ws, s));
+    PRDF_TRY(build_csr(n, nk, dr.p, dc.p, nullptr, false, false, D, ws, s));
   }
   PRDF_TRY(build_csr(n, n_ins, ins_rows, ins_cols, weighted ? ins_w : nullptr, false, false, I, ws, s));
   const int64_t nd = D.m, ni = I.m;

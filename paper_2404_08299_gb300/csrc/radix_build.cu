@@ -230,10 +230,13 @@ __global__ void __launch_bounds__(kRT) k_uniq_count(const uint64_t* __restrict__
 
 // Columns of the unique keys, and off[r] = position of row r's first unique
 // key (rows without keys take the next row's start; off[n] = total).
-// woff = exclusive scan of the per-warp counts, woff[nw] = total.
+// woff = exclusive scan of the per-warp counts, woff[nw] = total. With urow
+// (lists much shorter than n) the row of each unique key goes to urow instead
+// and k_offsets_from_rows fills off.
 __global__ void __launch_bounds__(kRT) k_uniq_emit(const uint64_t* __restrict__ k, int64_t M, int B, int32_t n,
                                                    const int64_t* __restrict__ woff, int64_t nw,
-                                                   int32_t* __restrict__ adj, int64_t* __restrict__ off) {
+                                                   int32_t* __restrict__ adj, int64_t* __restrict__ off,
+                                                   int32_t* __restrict__ urow) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * kRT + threadIdx.x) >> 5;
   const int64_t base = gw * (32 * kRK);
@@ -259,14 +262,31 @@ __global__ void __launch_bounds__(kRT) k_uniq_emit(const uint64_t* __restrict__ 
       const int64_t p = pos + __popc(bal & lt);
       const int64_t row = (int64_t)(key[r] >> B);
       adj[p] = (int32_t)(key[r] & cmask);
-      const int64_t first = i == 0 ? 0 : (int64_t)(prev >> B) + 1;  // rows after the previous key's
-      for (int64_t q = first; q <= row; ++q) off[q] = p;
+      if (urow) {
+        urow[p] = (int32_t)row;
+      } else {
+        const int64_t first = i == 0 ? 0 : (int64_t)(prev >> B) + 1;  // rows after the previous key's
+        for (int64_t q = first; q <= row; ++q) off[q] = p;
+      }
     }
-    if (i == M - 1) {
+    if (!urow && i == M - 1) {
       const int64_t total = woff[nw];
       for (int64_t q = (int64_t)(key[r] >> B) + 1; q <= n; ++q) off[q] = total;
     }
     pos += __popc(bal);
+  }
+}
+
+// off[r] = first position whose row is >= r (urow ascending, length mu): one
+// binary search per row, for lists much shorter than n
+__global__ void k_offsets_from_rows(const int32_t* __restrict__ urow, int64_t mu, int32_t n, int64_t* __restrict__ off) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= n; r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = mu;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (urow[mid] < r) lo = mid + 1; else hi = mid;
+    }
+    off[r] = lo;
   }
 }
 
@@ -339,7 +359,14 @@ int build_csr_radix(int32_t n, int64_t m0, const int32_t* rows, const int32_t* c
   PRDF_TRY(out.off.alloc((size_t)n + 1, s));
   PRDF_TRY(out.adj.alloc((size_t)(out.m > 0 ? out.m : 1), s));
   out.w.release();
-  k_uniq_emit<<<(unsigned)ntiles, kRT, 0, s>>>(cur, M, B, n, woff.p, nw, out.adj.p, out.off.p);
+  // a list much shorter than n leaves long runs of empty rows: their offsets
+  // are found row-parallel instead of by the lanes that emit the keys
+  const bool sparse = M * 16 < (int64_t)n;
+  DBuf<int32_t> urow;
+  if (sparse) PRDF_TRY(urow.alloc((size_t)(out.m > 0 ? out.m : 1), s));
+  k_uniq_emit<<<(unsigned)ntiles, kRT, 0, s>>>(cur, M, B, n, woff.p, nw, out.adj.p, out.off.p,
+                                               sparse ? urow.p : nullptr);
+  if (sparse) k_offsets_from_rows<<<grid_for((int64_t)n + 1, kRT), kRT, 0, s>>>(urow.p, out.m, n, out.off.p);
   PRDF_LAUNCH_CHECK();
   return PRDF_OK;
 }

@@ -59,11 +59,12 @@ def test_csr_build_rmat(scale, nsamp, weighted):
 
 
 @pytest.mark.parametrize("n,m0", [(3, 1), (1000, 4096 - 1000), (1000, 4097 - 1000), (70001, 500000),
-                                  ((1 << 17) + 3, 1 << 20)])
+                                  ((1 << 17) + 3, 1 << 20), ((1 << 20) + 5, 3000)])
 def test_csr_build_radix_sizes(n, m0):
     """Radix-sort build at vertex counts that are not powers of two (key widths of 2 to 18 bits a field,
     one to five passes) and at key counts of exactly one 4096-key tile and one key more; random ids with many
-    duplicates and runs of empty rows in the no-self-loop form."""
+    duplicates and runs of empty rows in the no-self-loop form (the last case is a list far shorter than n,
+    whose row offsets are found row-parallel)."""
     rng = np.random.default_rng(n + m0)
     s = (rng.integers(0, n, m0) if n < 1000 else rng.zipf(1.3, m0) % n).astype(np.int32)
     d = rng.integers(0, n, m0).astype(np.int32)
@@ -157,9 +158,14 @@ def test_partition_ragged_tiles():
     assert np.array_equal(host(Pg), Po) and cnt[:2] == cnto.tolist() and cnto[1] == 0
 
 
-@pytest.mark.parametrize("seed,size", [(1, 50), (2, 400), (3, 3000)])
-def test_apply_batch_bit_exact(seed, size):
-    n, s, d = synth.rmat(11, 30000, seed=seed)
+@pytest.mark.parametrize("seed,size,scale,nsamp", [(1, 50, 11, 30000), (2, 400, 11, 30000), (3, 3000, 11, 30000),
+                                                   (4, 6000, 15, 1 << 19), (5, 20000, 11, 30000)])
+def test_apply_batch_bit_exact(seed, size, scale, nsamp):
+    """Batches on both merge forms (in place on the numbering's CSRs while the edges changed since the last
+    numbering stay within 1/64 of |E|; on the original-id CSRs with a fresh numbering otherwise) and both batch
+    preparations (one block up to 4096 deletions and 4096 insertions; batch CSRs built by the radix sort above:
+    sizes 6000 and 20000)."""
+    n, s, d = synth.rmat(scale, nsamp, seed=seed)
     g = gpu_graph(n, s, d)
     og = oracle.graph(n, s, d)
     ds, dd, is_, id_ = synth.batch(n, og.out_off, og.out_adj, size, seed=seed, s1=3)
