@@ -618,6 +618,8 @@ def main():
                     help="columns of the K = 64 job checked against the oracle (none: skip)")
     ap.add_argument("--ppr-single", type=int, default=1, help="also solve the 64 columns one per call (K = 1)")
     ap.add_argument("--no-ppr", action="store_true", help="skip the K-column PPR and adjoint side measurement")
+    ap.add_argument("--dfp-workload", default="rmat22", choices=sorted(WORKLOADS),
+                    help="graph of --profile-dfp")
     ap.add_argument("--profile-dfp", type=float, default=0.0,
                     help="build the 2^22 R-MAT, solve Static, apply one random batch of this fraction of |E| and run "
                          "DF-P once (for ncu captures of the build, batch-update, marking and DF-P sweep kernels)")
@@ -654,7 +656,7 @@ def main():
     if args.profile_dfp > 0:
         pbuild.build()
         synth.build()
-        n, s, d = synth.rmat(22, 1 << 26, seed=1)
+        n, s, d = make_edges(args.dfp_workload)
         g = prdf.Graph(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
         n_, m = g.size()
         # host-driven loops (time_sweeps=1): a profiler sees every sweep kernel as its own launch

@@ -450,9 +450,12 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
     }
   };
 
-  // Static form: the row offsets run one more step ahead (offsets of the item
-  // two steps ahead, indices of the next), so a step waits for one round trip
+  // The row offsets run one more step ahead (offsets of the item two steps
+  // ahead, indices of the next), so a step waits for one round trip. In DF /
+  // DF-P the affected flag runs three steps ahead, so that offsets and indices
+  // are loaded only for affected vertices.
   constexpr bool kOffAhead = !DYN && !SELF1;
+  constexpr bool kDynAhead = DYN && !SELF1;
   auto load_off = [&](int32_t v, int64_t& b, int64_t& e) {
     b = v >= 0 ? ld_stream_i64(a.off + v, pf) : 0;
     e = v >= 0 ? ld_stream_i64(a.off + v + 1, pf) : 0;
@@ -478,8 +481,15 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
   }
   int32_t v_next = load_v(base + step + gw);
   uint8_t dv_next = load_dv(v_next);
-  int64_t nb = 0, ne = 0;  // kOffAhead: row offsets of v_next
+  int64_t nb = 0, ne = 0;  // kOffAhead, kDynAhead: row offsets of v_next (when affected)
   if (kOffAhead) load_off(v_next, nb, ne);
+  int32_t v_n2 = -1;  // kDynAhead: the list entry two steps ahead and its affected flag
+  uint8_t dv_n2 = 0;
+  if (kDynAhead) {
+    load_off((v_next >= 0 && dv_next) ? v_next : -1, nb, ne);
+    v_n2 = load_v(base + 2 * step + gw);
+    dv_n2 = load_dv(v_n2);
+  }
   for (; base < end; base += step) {
     // gathers of the current item
     uint64_t xv[U];
@@ -491,6 +501,20 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
       load_idx(v_next, nb, ne, nxt);
       v_next = load_v(base + 2 * step + gw);
       load_off(v_next, nb, ne);
+    } else if (kDynAhead) {
+      const bool live = v_next >= 0 && dv_next;
+      load_idx(live ? v_next : -1, nb, ne, nxt);
+      nxt.v = v_next;
+      if (v_next >= 0) {
+        nxt.f.dv = dv_next;
+        nxt.f.wr = a.wrote[v_next];
+        nxt.f.dn = a.dN[v_next];
+      }
+      v_next = v_n2;
+      dv_next = dv_n2;
+      load_off((v_next >= 0 && dv_next) ? v_next : -1, nb, ne);
+      v_n2 = load_v(base + 3 * step + gw);
+      dv_n2 = load_dv(v_n2);
     } else {
       load_item(v_next, dv_next, nxt);
       v_next = load_v(base + 2 * step + gw);
