@@ -472,8 +472,24 @@ struct Loop {
   int nci = 0, nco = 0;
   int64_t pull_warp_b = 0;
   unsigned long long fthr = ~0ull;
+  FrontList fl;              // listed small frontiers
   int kernels_per_iter = 0;  // kernels of one iteration (without the graph's check)
 };
+
+// An expansion round lists a frontier of at most min(32768, n / 8) vertices
+// (at least 64) and expands it from the list (frontier.cu); larger ones take
+// the partition kernels.
+int front_list(prdf_graph* g, cudaStream_t s, FrontList* fl) {
+  int64_t cap = g->n / 8;
+  if (cap > 32768) cap = 32768;
+  if (cap < 64) cap = 64;
+  PRDF_TRY(g->flist.reserve((size_t)cap, s));
+  PRDF_TRY(g->fcnt.reserve(1, s));
+  fl->list = g->flist.p;
+  fl->cnt = g->fcnt.p;
+  fl->cap = (unsigned int)cap;
+  return PRDF_OK;
+}
 
 int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, bool expand, int max_iter, Loop* L,
                cudaStream_t s) {
@@ -559,8 +575,9 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
     PRDF_CUDA(cudaMemsetAsync(g->fwork.p, 0, sizeof(unsigned long long) * ((size_t)max_iter + 1), s));
     const double lim = p->expand_pull * (double)rl.in.m;
     L->fthr = lim >= 1.8e19 ? ~0ull : (unsigned long long)lim;
+    PRDF_TRY(front_list(g, s, &L->fl));  // allocated here, outside any stream capture
     L->kernels_per_iter += nonempty_classes(L->cbo, L->nco) + (L->pull_warp_b > 0 ? 1 : 0) +
-                           (n > L->pull_warp_b ? 1 : 0);
+                           (n > L->pull_warp_b ? 1 : 0) + 2;
   }
   return PRDF_OK;
 }
@@ -621,7 +638,7 @@ int launch_loop_expansion(prdf_graph* g, const Loop& L, int i, cudaStream_t s) {
   unsigned long long* fw = g->fwork.p + (i >= 0 ? i : 0);
   PRDF_TRY(launch_expand_pull(rl.in.off.p, rl.in.adj.p, g->n, L.pull_warp_b, g->dN.p, g->dV.p, fw, L.fthr, st, s));
   return launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, L.cbo, L.nco, g->dN.p, g->dV.p, nullptr, st, s, fw,
-                       L.fthr);
+                       L.fthr, L.fl);
 }
 
 // stop rule of sweep i from the residual words read back
@@ -786,7 +803,7 @@ int run_graph_loop(prdf_graph* g, const Loop& L, IterResult* res, cudaStream_t s
   const Relabel& rl = g->rl;
   const void* ptrs[] = {g->ctl.p,     g->xa.p,       g->xb.p,        g->ya.p,       g->yb.p,      g->resid.p,
                         g->resid32.p, g->fwork.p,    g->dN.p,        g->dV.p,       rl.in.off.p,  rl.in.adj.p,
-                        rl.out.off.p, rl.out.adj.p,  rl.pout.p};
+                        rl.out.off.p, rl.out.adj.p,  rl.pout.p,     g->flist.p,    g->fcnt.p};
   kw.put(ptrs, sizeof(ptrs));
   kw.putv(rl.version);
   kw.putv((uint64_t)g->n);
@@ -1653,8 +1670,10 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
                                    g->dN.p, s));
   int64_t cbo[kMaxThr + 2];
   begins_from_counts(rl.pout_count, g->thr[PRDF_OUT].n + 1, cbo);
+  FrontList fl;
+  PRDF_TRY(front_list(g, s, &fl));
   PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, g->thr[PRDF_OUT].n + 1, g->dN.p, g->dV.p,
-                         nullptr, Stop(), s));
+                         nullptr, Stop(), s, nullptr, 0, fl));
   PRDF_TRY(count_flags(g->dV.p, n, g->counter.p, s));
   PRDF_CUDA(cudaEventRecord(t.e[2], s));
   PRDF_CUDA(cudaMemcpyAsync(g->ws.host_i64 + 8, g->counter.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -1692,7 +1711,7 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
     stats->affected_initial = aff0;
     // (out-degree partition) + init (+ Eq. 2 factor) + initial marking + expand + count + sweeps/expands + finalize
     stats->kernel_launches = (pout_made ? 5 : 0) + 1 + (kf_made ? 1 : 0) + (n_del + n_ins > 0 ? 1 : 0) +
-                             nonempty_classes(cbo, g->thr[PRDF_OUT].n + 1) + 1 + kernels32 + it.kernels + 1;
+                             nonempty_classes(cbo, g->thr[PRDF_OUT].n + 1) + 2 + 1 + kernels32 + it.kernels + 1;
   }
   return PRDF_OK;
 }
@@ -1730,19 +1749,23 @@ int prdf_pagerank_dt(prdf_graph* g, const int32_t* del_src, const int32_t* del_d
   const int nco = g->thr[PRDF_OUT].n + 1;
   int64_t cbo[kMaxThr + 2];
   begins_from_counts(rl.pout_count, nco, cbo);
-  PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, nullptr, Stop(), s));
+  FrontList fl;
+  PRDF_TRY(front_list(g, s, &fl));
+  PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, nullptr, Stop(), s,
+                         nullptr, 0, fl));
   // reachability closure over G^t: the frontier starts as every affected vertex; each
   // round marks the vertices it reaches that were not yet affected, which form the
   // next frontier, until a round adds none (the affected count stops changing)
-  long long kernels = (pout_made ? 5 : 0) + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, nco);
+  long long kernels = (pout_made ? 5 : 0) + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, nco) + 2;
   PRDF_CUDA(cudaMemcpyAsync(g->dN.p, g->dV.p, (size_t)n, cudaMemcpyDeviceToDevice, s));
   uint8_t* front = g->dN.p;
   uint8_t* next = g->dF.p;
   for (int round = 0; round < n; ++round) {
     PRDF_CUDA(cudaMemsetAsync(next, 0, (size_t)n, s));
-    PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, front, g->dV.p, next, Stop(), s));
+    PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, front, g->dV.p, next, Stop(), s, nullptr,
+                           0, fl));
     PRDF_TRY(count_flags(next, n, g->counter.p, s));
-    kernels += nonempty_classes(cbo, nco) + 1;
+    kernels += nonempty_classes(cbo, nco) + 1 + 2;
     unsigned long long added = 0;
     PRDF_CUDA(cudaMemcpyAsync(&added, g->counter.p, sizeof(added), cudaMemcpyDeviceToHost, s));
     PRDF_CUDA(cudaStreamSynchronize(s));

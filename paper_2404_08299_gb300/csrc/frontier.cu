@@ -129,14 +129,18 @@ __device__ __forceinline__ void mark_targets(const int32_t* __restrict__ adj, in
 
 constexpr int kExpandU = 4;
 
+// the frontier was listed (at most cap vertices) and expanded from the list
+__device__ __forceinline__ bool listed(const unsigned int* cnt, unsigned int cap) { return cnt && *cnt <= cap; }
+
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_expand_group(const int64_t* __restrict__ off,
                                                            const int32_t* __restrict__ adj,
                                                            const int32_t* __restrict__ P, int64_t begin, int64_t end,
                                                            const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
                                                            uint8_t* __restrict__ dF, const Stop st,
-                                                           const unsigned long long* fw, unsigned long long fthr) {
-  if (converged(st) || pull_chosen(round_fw(fw, st), fthr)) return;
+                                                           const unsigned long long* fw, unsigned long long fthr,
+                                                           const unsigned int* lcnt, unsigned int cap) {
+  if (converged(st) || pull_chosen(round_fw(fw, st), fthr) || listed(lcnt, cap)) return;
   const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
   const int64_t gid = (blockIdx.x * (int64_t)kThreads + threadIdx.x) / G;
   const int64_t ng = ((int64_t)gridDim.x * kThreads) / G;
@@ -154,8 +158,9 @@ __global__ void __launch_bounds__(kThreads) k_expand_block(const int64_t* __rest
                                                            const int32_t* __restrict__ P, int64_t begin, int64_t end,
                                                            const uint8_t* __restrict__ dN, uint8_t* __restrict__ dV,
                                                            uint8_t* __restrict__ dF, const Stop st,
-                                                           const unsigned long long* fw, unsigned long long fthr) {
-  if (converged(st) || pull_chosen(round_fw(fw, st), fthr)) return;
+                                                           const unsigned long long* fw, unsigned long long fthr,
+                                                           const unsigned int* lcnt, unsigned int cap) {
+  if (converged(st) || pull_chosen(round_fw(fw, st), fthr) || listed(lcnt, cap)) return;
   const int64_t S = gridDim.y, y = blockIdx.y;
   for (int64_t i = begin + blockIdx.x; i < end; i += gridDim.x) {
     const int32_t u = P[i];
@@ -165,6 +170,72 @@ __global__ void __launch_bounds__(kThreads) k_expand_block(const int64_t* __rest
     const int64_t sb = b + y * span;
     const int64_t se = sb + span < b + len ? sb + span : b + len;
     mark_targets<kExpandU>(adj, sb + threadIdx.x, se, kThreads, dV, dF);
+  }
+}
+
+// Small frontiers. The class kernels above find the frontier by reading dN
+// through the out-degree partition: n scattered byte loads per round however
+// few vertices are in it. k_frontier_list lists the frontier instead (a
+// coalesced read of dN, warp-aggregated appends) while it holds at most cap
+// vertices, and k_expand_list gives each listed vertex a block; the class
+// kernels then return at once. Past cap the list is abandoned (only counted)
+// and the class kernels run as before. The marks are the same either way.
+__global__ void __launch_bounds__(kThreads) k_frontier_list(const uint8_t* __restrict__ dN, int64_t n,
+                                                            int32_t* __restrict__ list, unsigned int* __restrict__ cnt,
+                                                            unsigned int cap, const Stop st,
+                                                            const unsigned long long* fw, unsigned long long fthr) {
+  if (converged(st) || pull_chosen(round_fw(fw, st), fthr)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = n >> 2;  // whole 4-flag words; the tail is read by thread 0
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t base = i0 - lane; base < nw; base += stride) {  // warp-uniform trip count
+    const int64_t i = base + lane;
+    uint32_t word = 0;
+    if (i < nw) word = reinterpret_cast<const uint32_t*>(dN)[i];
+    int c = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c += ((word >> (8 * q)) & 0xFFu) ? 1 : 0;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;
+    unsigned int wbase = 0;
+    if (lane == 31) wbase = atomicAdd(cnt, (unsigned int)total);
+    wbase = __shfl_sync(0xffffffffu, wbase, 31);
+    unsigned int pos = wbase + (unsigned int)(incl - c);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if ((word >> (8 * q)) & 0xFFu) {
+        if (pos < cap) list[pos] = (int32_t)(4 * i + q);
+        ++pos;
+      }
+  }
+  if (i0 == 0)
+    for (int64_t v = nw << 2; v < n; ++v)
+      if (dN[v]) {
+        const unsigned int pos = atomicAdd(cnt, 1u);
+        if (pos < cap) list[pos] = (int32_t)v;
+      }
+}
+
+__global__ void __launch_bounds__(kThreads) k_expand_list(const int64_t* __restrict__ off,
+                                                          const int32_t* __restrict__ adj,
+                                                          const int32_t* __restrict__ list,
+                                                          const unsigned int* __restrict__ cnt, unsigned int cap,
+                                                          uint8_t* __restrict__ dV, uint8_t* __restrict__ dF,
+                                                          const Stop st, const unsigned long long* fw,
+                                                          unsigned long long fthr) {
+  if (converged(st) || pull_chosen(round_fw(fw, st), fthr)) return;
+  const unsigned int c = *cnt;
+  if (c > cap) return;
+  for (unsigned int k = blockIdx.x; k < c; k += gridDim.x) {
+    const int32_t u = list[k];
+    mark_targets<kExpandU>(adj, off[u] + threadIdx.x, off[u + 1], kThreads, dV, dF);
   }
 }
 
@@ -190,20 +261,28 @@ int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, cons
 
 int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, const int64_t* cb, int nclass,
                   const uint8_t* dN, uint8_t* dV, uint8_t* dF, const Stop& st, cudaStream_t s,
-                  const unsigned long long* fw, unsigned long long fthr) {
+                  const unsigned long long* fw, unsigned long long fthr, const FrontList& fl) {
   const int maxg = kSMs * 8;
+  const unsigned int* lcnt = fl.list ? fl.cnt : nullptr;
+  if (fl.list) {
+    const int64_t n = cb[nclass];
+    PRDF_CUDA(cudaMemsetAsync(fl.cnt, 0, sizeof(unsigned int), s));
+    k_frontier_list<<<grid_for(n / 4 + 1, kThreads, kSMs * 4), kThreads, 0, s>>>(dN, n, fl.list, fl.cnt, fl.cap, st,
+                                                                                fw, fthr);
+    k_expand_list<<<kSMs * 8, kThreads, 0, s>>>(off, adj, fl.list, fl.cnt, fl.cap, dV, dF, st, fw, fthr);
+  }
   for (int c = 0; c < nclass; ++c) {
     const int64_t b = cb[c], e = cb[c + 1];
     if (e <= b) continue;
     const int64_t cnt = e - b;
     const int kind = (nclass == 4) ? c : (c == nclass - 1 ? 3 : c);
     switch (kind) {
-      case 0: k_expand_group<1><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr); break;
-      case 1: k_expand_group<8><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr); break;
-      case 2: k_expand_group<32><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr); break;
+      case 0: k_expand_group<1><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr, lcnt, fl.cap); break;
+      case 1: k_expand_group<8><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr, lcnt, fl.cap); break;
+      case 2: k_expand_group<32><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr, lcnt, fl.cap); break;
       default: {
         const dim3 grid(grid_for(cnt, 1, maxg / kExpandSlices), kExpandSlices);
-        k_expand_block<<<grid, kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr);
+        k_expand_block<<<grid, kThreads, 0, s>>>(off, adj, P, b, e, dN, dV, dF, st, fw, fthr, lcnt, fl.cap);
         break;
       }
     }

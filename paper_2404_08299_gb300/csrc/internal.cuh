@@ -300,9 +300,17 @@ int launch_initial_affected(const int32_t* del_src, const int32_t* del_dst, cons
 // st.ctl in the graph-driven loop) is given, also when *fw > fthr (the pull
 // form runs instead). dF (nullable): also mark in dF every vertex that was not
 // yet in dV (one round of Dynamic Traversal's reachability closure).
+// fl (optional scratch): a frontier of at most fl.cap vertices is listed and
+// expanded from the list, without the partition kernels' scan of every vertex.
+struct FrontList {
+  int32_t* list = nullptr;      // cap entries
+  unsigned int* cnt = nullptr;  // one counter
+  unsigned int cap = 0;
+};
 int launch_expand(const int64_t* off, const int32_t* adj, const int32_t* P, const int64_t* cb, int nclass,
                   const uint8_t* dN, uint8_t* dV, uint8_t* dF, const Stop& st, cudaStream_t s,
-                  const unsigned long long* fw = nullptr, unsigned long long fthr = 0);
+                  const unsigned long long* fw = nullptr, unsigned long long fthr = 0,
+                  const FrontList& fl = FrontList());
 // The same round in pull form over G' (in_off/in_adj; rows from warp_begin on
 // take a warp each): marks only if *fw, the frontier's out-edges (counted by
 // the sweep before it), exceeds fthr.
@@ -343,6 +351,8 @@ struct prdf_graph {
   prdf::DBuf<unsigned long long> counter;
   prdf::DBuf<unsigned long long> chk;  // input checks: bad-id flag, bad-rank flag, rank sum (double bits)
   prdf::DBuf<unsigned long long> fwork;  // frontier out-edges of each expansion round
+  prdf::DBuf<int32_t> flist;             // a small frontier listed for its expansion round (frontier.cu)
+  prdf::DBuf<unsigned int> fcnt;         // its size
   prdf::DBuf<int> ctl;               // device iteration counter of the graph-driven loop
   cudaStream_t cap_stream = nullptr; // private stream used to capture graph bodies
   // instantiated loops (CUDA graphs), one per kind of loop, each with the
