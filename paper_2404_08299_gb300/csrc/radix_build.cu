@@ -14,8 +14,9 @@
 // rather than one random store per key. No global atomics, so the result
 // and its timing do not depend on how skewed the rows are. The first pass
 // reads the edge list and makes the keys (and the self-loop keys) on the
-// fly. After the last pass, adjacent equal keys are merged: one tile count,
-// one scan, one emit pass that writes the columns and the row offsets.
+// fly. After the last pass, adjacent equal keys are merged: a count per warp,
+// one scan, one emit pass that writes the columns and the row offsets (found
+// row-parallel instead when the list is much shorter than n).
 #include "internal.cuh"
 
 namespace prdf {

@@ -541,6 +541,13 @@ __global__ void __launch_bounds__(kThreads, U >= 8 ? 3 : kMinBlocks) k_sweep_gro
       cur = nxt;
       continue;
     }
+    // DF / DF-P: a step in which no item of the warp is affected (most steps of
+    // the first sweeps after a small batch) has nothing to reduce. (Every lane
+    // reaches the vote: only the SELF1 form leaves the step early, per lane.)
+    if (DYN && !SELF1 && !__any_sync(0xffffffffu, active)) {
+      cur = nxt;
+      continue;
+    }
     Acc<EXACT> acc;
     uint64_t xself = 0;
     if (active) {
