@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_sweep_warp(const Sweep
     const int64_t bn = vn >= 0 ? ld_stream_i64(a.off + vn, pf) : 0, en = vn >= 0 ? ld_stream_i64(a.off + vn + 1, pf) : 0;
     Flags fn;
     if (DYN && vn >= 0) fn = load_flags(a, vn);
-    acc.template group_reduce<32>();
+    if (active) acc.template group_reduce<32>();  // active is the same on every lane (one row per warp)
     if (active && lane == 0) {
       const uint64_t db = finish_vertex<DYN>(a, v, acc.value(), xself, pf, fwsum, f.dn);
       dmax = db > dmax ? db : dmax;

@@ -360,6 +360,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_group(const Sweep32Args a_
           gather32<G, U>(a, b, e, lane, v, acc, yself, pf, pl);
         }
       }
+      // DF / DF-P: nothing to reduce when no item of the warp's step is affected
+      if (DYN && !__any_sync(0xffffffffu, active)) continue;
       if (G > 1) {
         acc.template group_reduce<G>();
 #pragma unroll
