@@ -91,6 +91,12 @@ typedef struct {
                           frontier's out-edges exceed expand_pull * |E|, else in push form (Alg.
                           affected). Both mark the same set. Default 1/16; >= 1 keeps the push form;
                           must be >= 0. */
+  int64_t expand_list; /* DF / DF-P / DT: a push-form round whose frontier holds at most this many
+                          vertices lists them and expands them from the list, instead of scanning
+                          every vertex's flag through the out-degree partition; the marks are the
+                          same. -1 (default): min(32768, n / 8) on graphs of at least 2^22 vertices,
+                          0 below that (where the scan is cheaper than the list's extra launches);
+                          0: never; must be >= -1. */
   void* stream;        /* cudaStream_t for all work; NULL = legacy default stream */
 } prdf_params;
 

@@ -38,7 +38,7 @@ class _Params(ctypes.Structure):
                 ("tau_p", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("tol_fp32_rel", ctypes.c_double), ("accumulate", ctypes.c_int), ("prune", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("time_sweeps", ctypes.c_int), ("tile", ctypes.c_int),
-                ("expand_pull", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("expand_pull", ctypes.c_double), ("expand_list", ctypes.c_int64), ("stream", ctypes.c_void_p)]
 
 
 class _Stats(ctypes.Structure):

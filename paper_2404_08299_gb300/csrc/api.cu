@@ -325,6 +325,10 @@ int check_params(const prdf_params* p) {
     set_error("expand_pull must be >= 0");
     return PRDF_EINVAL;
   }
+  if (p->expand_list < -1) {
+    set_error("expand_list must be >= -1");
+    return PRDF_EINVAL;
+  }
   if (p->precision != PRDF_FP64 && p->precision != PRDF_FP32_REFINE) {
     set_error("unknown precision %d", p->precision);
     return PRDF_EINVAL;
@@ -476,13 +480,17 @@ struct Loop {
   int kernels_per_iter = 0;  // kernels of one iteration (without the graph's check)
 };
 
-// An expansion round lists a frontier of at most min(32768, n / 8) vertices
-// (at least 64) and expands it from the list (frontier.cu); larger ones take
-// the partition kernels.
-int front_list(prdf_graph* g, cudaStream_t s, FrontList* fl) {
-  int64_t cap = g->n / 8;
-  if (cap > 32768) cap = 32768;
-  if (cap < 64) cap = 64;
+// An expansion round lists a frontier of at most cap vertices and expands it
+// from the list (frontier.cu); larger ones take the partition kernels. The
+// automatic cap is min(32768, n / 8) on graphs of at least 2^22 vertices; on
+// smaller ones the partition kernels' scan costs less than the list's extra
+// launches, so the list is off (cap 0: fl left empty).
+int front_list(prdf_graph* g, const prdf_params* p, cudaStream_t s, FrontList* fl) {
+  int64_t cap = p->expand_list;
+  if (cap < 0) cap = g->n >= (1 << 22) ? (g->n / 8 < 32768 ? g->n / 8 : 32768) : 0;
+  if (cap > g->n) cap = g->n;
+  *fl = FrontList();
+  if (cap == 0) return PRDF_OK;
   PRDF_TRY(g->flist.reserve((size_t)cap, s));
   PRDF_TRY(g->fcnt.reserve(1, s));
   fl->list = g->flist.p;
@@ -575,9 +583,9 @@ int loop_setup(prdf_graph* g, const prdf_params* p, bool fp32, bool dynamic, boo
     PRDF_CUDA(cudaMemsetAsync(g->fwork.p, 0, sizeof(unsigned long long) * ((size_t)max_iter + 1), s));
     const double lim = p->expand_pull * (double)rl.in.m;
     L->fthr = lim >= 1.8e19 ? ~0ull : (unsigned long long)lim;
-    PRDF_TRY(front_list(g, s, &L->fl));  // allocated here, outside any stream capture
+    PRDF_TRY(front_list(g, p, s, &L->fl));  // allocated here, outside any stream capture
     L->kernels_per_iter += nonempty_classes(L->cbo, L->nco) + (L->pull_warp_b > 0 ? 1 : 0) +
-                           (n > L->pull_warp_b ? 1 : 0) + 2;
+                           (n > L->pull_warp_b ? 1 : 0) + (L->fl.list ? 2 : 0);
   }
   return PRDF_OK;
 }
@@ -800,6 +808,7 @@ int run_graph_loop(prdf_graph* g, const Loop& L, IterResult* res, cudaStream_t s
   kw.putv((uint64_t)L.nci | ((uint64_t)L.nco << 32));
   kw.putv((uint64_t)L.pull_warp_b);
   kw.putv(L.fthr);
+  kw.putv((uint64_t)L.fl.cap);
   const Relabel& rl = g->rl;
   const void* ptrs[] = {g->ctl.p,     g->xa.p,       g->xb.p,        g->ya.p,       g->yb.p,      g->resid.p,
                         g->resid32.p, g->fwork.p,    g->dN.p,        g->dV.p,       rl.in.off.p,  rl.in.adj.p,
@@ -1258,6 +1267,7 @@ void prdf_params_default(prdf_params* p) {
   p->time_sweeps = 0;
   p->tile = 0;
   p->expand_pull = 1.0 / 16.0;
+  p->expand_list = -1;
   p->stream = nullptr;
 }
 
@@ -1671,7 +1681,7 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
   int64_t cbo[kMaxThr + 2];
   begins_from_counts(rl.pout_count, g->thr[PRDF_OUT].n + 1, cbo);
   FrontList fl;
-  PRDF_TRY(front_list(g, s, &fl));
+  PRDF_TRY(front_list(g, p, s, &fl));
   PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, g->thr[PRDF_OUT].n + 1, g->dN.p, g->dV.p,
                          nullptr, Stop(), s, nullptr, 0, fl));
   PRDF_TRY(count_flags(g->dV.p, n, g->counter.p, s));
@@ -1711,7 +1721,7 @@ int prdf_pagerank_dfp(prdf_graph* g, const int32_t* del_src, const int32_t* del_
     stats->affected_initial = aff0;
     // (out-degree partition) + init (+ Eq. 2 factor) + initial marking + expand + count + sweeps/expands + finalize
     stats->kernel_launches = (pout_made ? 5 : 0) + 1 + (kf_made ? 1 : 0) + (n_del + n_ins > 0 ? 1 : 0) +
-                             nonempty_classes(cbo, g->thr[PRDF_OUT].n + 1) + 2 + 1 + kernels32 + it.kernels + 1;
+                             nonempty_classes(cbo, g->thr[PRDF_OUT].n + 1) + (fl.list ? 2 : 0) + 1 + kernels32 + it.kernels + 1;
   }
   return PRDF_OK;
 }
@@ -1750,13 +1760,13 @@ int prdf_pagerank_dt(prdf_graph* g, const int32_t* del_src, const int32_t* del_d
   int64_t cbo[kMaxThr + 2];
   begins_from_counts(rl.pout_count, nco, cbo);
   FrontList fl;
-  PRDF_TRY(front_list(g, s, &fl));
+  PRDF_TRY(front_list(g, p, s, &fl));
   PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, g->dN.p, g->dV.p, nullptr, Stop(), s,
                          nullptr, 0, fl));
   // reachability closure over G^t: the frontier starts as every affected vertex; each
   // round marks the vertices it reaches that were not yet affected, which form the
   // next frontier, until a round adds none (the affected count stops changing)
-  long long kernels = (pout_made ? 5 : 0) + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, nco) + 2;
+  long long kernels = (pout_made ? 5 : 0) + 1 + (n_del + n_ins > 0 ? 1 : 0) + nonempty_classes(cbo, nco) + (fl.list ? 2 : 0);
   PRDF_CUDA(cudaMemcpyAsync(g->dN.p, g->dV.p, (size_t)n, cudaMemcpyDeviceToDevice, s));
   uint8_t* front = g->dN.p;
   uint8_t* next = g->dF.p;
@@ -1765,7 +1775,7 @@ int prdf_pagerank_dt(prdf_graph* g, const int32_t* del_src, const int32_t* del_d
     PRDF_TRY(launch_expand(rl.out.off.p, rl.out.adj.p, rl.pout.p, cbo, nco, front, g->dV.p, next, Stop(), s, nullptr,
                            0, fl));
     PRDF_TRY(count_flags(next, n, g->counter.p, s));
-    kernels += nonempty_classes(cbo, nco) + 1 + 2;
+    kernels += nonempty_classes(cbo, nco) + 1 + (fl.list ? 2 : 0);
     unsigned long long added = 0;
     PRDF_CUDA(cudaMemcpyAsync(&added, g->counter.p, sizeof(added), cudaMemcpyDeviceToHost, s));
     PRDF_CUDA(cudaStreamSynchronize(s));

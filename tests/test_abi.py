@@ -50,7 +50,7 @@ def test_params_default_are_the_papers_constants(built_lib):
     built_lib.prdf_params_default(ctypes.byref(p))
     assert (p.alpha, p.tol, p.tau_f, p.tau_p, p.max_iter) == (0.85, 1e-10, 1e-6, 1e-6, 500)
     assert p.precision == prdf.PRDF_FP64 and p.accumulate == prdf.PRDF_ACC_EXACT and p.prune == 1
-    assert p.expand_pull == 1 / 16 and p.stream is None
+    assert p.expand_pull == 1 / 16 and p.expand_list == -1 and p.stream is None
 
 
 def test_graph_create_rejects_bad_sizes_without_touching_the_gpu(built_lib):

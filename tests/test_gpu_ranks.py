@@ -114,7 +114,7 @@ def test_static_rejects_bad_params():
     n, s, d = synth.rmat(6, 300, seed=1)
     g = gpu_graph(n, s, d)
     for kw in ({"alpha": 1.0}, {"alpha": 0.0}, {"tol": 0.0}, {"max_iter": 0}, {"alpha": float("nan")},
-               {"expand_pull": -1.0}, {"expand_pull": float("nan")}):
+               {"expand_pull": -1.0}, {"expand_pull": float("nan")}, {"expand_list": -2}):
         with pytest.raises(prdf().PrdfError) as e:
             g.pagerank_static(**kw)
         assert e.value.code == -1
@@ -127,14 +127,17 @@ def _dynamic_case(seed, scale, nsamp, size, thresholds=None):
 
 
 def _check_dfp_step_by_step(g, og1, R0, batch, prune, expand_pull):
+    """expand_list -1 (automatic: off on graphs this small) and 64 (push rounds with at most 64 frontier vertices
+    expand from a list, larger ones through the partition kernels): both must give the oracle's trace."""
     ds, dd, is_, id_, de, ie, dmo, imo = batch
-    R, st, dV = g.pagerank_dfp(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True, prune=prune,
-                               expand_pull=expand_pull)
     Ro, sto, dVo, trace = oracle.pagerank_dfp(og1, ds, dd, is_, host(R0), del_mask=dmo, ins_mask=imo, prune=bool(prune))
-    assert st.iterations == sto.iterations
-    assert st.affected_initial == trace[0]
-    assert np.array_equal(host(dV), dVo)
-    assert np.max(np.abs(host(R) - Ro) / Ro) <= 1e-12
+    for expand_list in (-1, 64):
+        R, st, dV = g.pagerank_dfp(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True,
+                                   prune=prune, expand_pull=expand_pull, expand_list=expand_list)
+        assert st.iterations == sto.iterations
+        assert st.affected_initial == trace[0]
+        assert np.array_equal(host(dV), dVo)
+        assert np.max(np.abs(host(R) - Ro) / Ro) <= 1e-12
 
 
 @pytest.mark.parametrize("expand_pull", [1 / 16, 0.0, 2.0])  # automatic, always pull, always push
@@ -262,10 +265,13 @@ def test_dfp_all_affected_df_equals_naive_dynamic():
 
 @pytest.mark.parametrize("seed,scale,nsamp,size", [(1, 8, 3000, 20), (5, 12, 3000, 8), (6, 12, 50000, 5),
                                                    (7, 14, 20000, 40)])
-def test_dt_matches_oracle(seed, scale, nsamp, size):
-    """Closure bit-exact (sparse graphs leave unreachable vertices out), same sweep count, ranks to 1e-12."""
+@pytest.mark.parametrize("expand_list", [-1, 64])
+def test_dt_matches_oracle(seed, scale, nsamp, size, expand_list):
+    """Closure bit-exact (sparse graphs leave unreachable vertices out), same sweep count, ranks to 1e-12; with
+    closure rounds of at most 64 frontier vertices expanded from a list or not."""
     g, og1, R0, (ds, dd, is_, id_, de, ie, dmo, imo) = _dynamic_case(seed, scale, nsamp, size)
-    R, st, dV = g.pagerank_dt(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True)
+    R, st, dV = g.pagerank_dt(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True,
+                              expand_list=expand_list)
     Ro, sto, dVo, na, rounds = oracle.pagerank_dt(og1, ds, dd, is_, host(R0), del_mask=dmo, ins_mask=imo)
     assert np.array_equal(host(dV), dVo)
     assert st.affected_initial == na
