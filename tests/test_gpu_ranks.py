@@ -160,6 +160,28 @@ def test_dfp_hub_rows_step_by_step(prune, expand_pull):
     _check_dfp_step_by_step(g, og1, R0, batch, prune, expand_pull)
 
 
+@pytest.mark.parametrize("prune", [1, 0])
+def test_dfp_vertex_count_not_a_multiple_of_four(prune):
+    """n = 4099: the frontier listing reads the flags four at a time and the last three vertices separately;
+    with the listed form forced on and off, DF / DF-P match the oracle step by step, and so does DT."""
+    n = 4099
+    s = synth.randint(40000, n, seed=41)
+    d = synth.randint(40000, n, seed=42)
+    s = np.concatenate([s, np.full(30, n - 1, np.int32), np.full(30, n - 2, np.int32)])
+    d = np.concatenate([d, synth.randint(60, n, seed=43)])
+    extra = (np.array([n - 1], np.int32), np.array([int(d[-1])], np.int32), np.array([n - 3, n - 1], np.int32),
+             np.array([n - 2, 5], np.int32))
+    g, og1, R0, batch = batch_case(n, s, d, 12, 20, extra=extra)
+    _check_dfp_step_by_step(g, og1, R0, batch, prune, 1 / 16)
+    ds, dd, is_, id_, de, ie, dmo, imo = batch
+    Ro, sto, dVo, na, rounds = oracle.pagerank_dt(og1, ds, dd, is_, host(R0), del_mask=dmo, ins_mask=imo)
+    for expand_list in (-1, 64):
+        R, st, dV = g.pagerank_dt(dev(ds), dev(dd), dev(is_), R0, del_mask=de, ins_mask=ie, want_dV=True,
+                                  expand_list=expand_list)
+        assert np.array_equal(host(dV), dVo) and st.iterations == sto.iterations
+        assert np.max(np.abs(host(R) - Ro) / Ro) <= 1e-12
+
+
 @pytest.mark.parametrize("expand_pull", [1 / 16, 0.0, 2.0])
 @pytest.mark.parametrize("prune", [1, 0])
 @pytest.mark.parametrize("thr", [[1, 4, 16, 32, 64], [0, 4]])
