@@ -535,8 +535,9 @@ __global__ void __launch_bounds__(kThreads) k_sweep32_hub_finish(const Sweep32Ar
   block_epilogue32<DYN>(a, dmax, rmax, fwsum);
 }
 
-enum Kind32 { kT1 = 0, kT4, kG4, kG16, kWarp, kBlock };
+enum Kind32 { kT1 = 0, kT4, kG4, kG8, kG16, kG16U8, kWarp, kBlock };
 
+// the FP64 sweep's shapes: lanes x indices per lane sized to the class's rows
 Kind32 class_kind32(const PartThr& t, int c) {
   const int C = t.n + 1;
   if (c == C - 1) return kBlock;
@@ -545,12 +546,39 @@ Kind32 class_kind32(const PartThr& t, int c) {
   if (hi <= 1) return kT1;
   if (hi <= 4) return kT4;
   if (hi <= 16) return kG4;
-  if (hi <= 128) return kG16;
+  if (hi <= 32) return kG8;
+  // 16 lanes; 8 indices per lane only when every row of the class is longer than 64
+  if (hi <= 128) return (c > 0 && t.thr[c - 1] >= 64) ? kG16U8 : kG16;
   return kWarp;
+}
+
+// As in the FP64 sweep: almost no shared memory, so the unified L1 / shared
+// storage goes to L1, which holds the gathered y of the hottest sources.
+template <typename K>
+void prefer_l1_32(K k) {
+  // a preference the driver declines is not an error: clear what this call set
+  if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 0) != cudaSuccess) cudaGetLastError();
+}
+
+template <bool DYN>
+bool prefer_l1_all32() {
+  prefer_l1_32(k_sweep32_group<1, 1, true, DYN>);
+  prefer_l1_32(k_sweep32_group<1, 1, false, DYN>);
+  prefer_l1_32(k_sweep32_group<1, 4, false, DYN>);
+  prefer_l1_32(k_sweep32_group<4, 4, false, DYN>);
+  prefer_l1_32(k_sweep32_group<8, 4, false, DYN>);
+  prefer_l1_32(k_sweep32_group<16, 4, false, DYN>);
+  prefer_l1_32(k_sweep32_group<16, 8, false, DYN>);
+  prefer_l1_32(k_sweep32_warp<2, DYN>);
+  prefer_l1_32(k_sweep32_block<4, DYN>);
+  prefer_l1_32(k_sweep32_hub_part<DYN>);
+  return true;
 }
 
 template <bool DYN>
 int launch_all32(const Sweep32Args& a, const PartThr& t, const int64_t* cb, cudaStream_t s) {
+  static const bool carveout_set = prefer_l1_all32<DYN>();
+  (void)carveout_set;
   const int maxg = kSMs * 8;
   const int C = t.n + 1;
   for (int c = 0; c < C; ++c) {
@@ -566,7 +594,9 @@ int launch_all32(const Sweep32Args& a, const PartThr& t, const int64_t* cb, cuda
         break;
       case kT4: k_sweep32_group<1, 4, false, DYN><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kG4: k_sweep32_group<4, 4, false, DYN><<<grid_for(cnt * 4, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      case kG16: k_sweep32_group<16, 8, false, DYN><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG8: k_sweep32_group<8, 4, false, DYN><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG16: k_sweep32_group<16, 4, false, DYN><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      case kG16U8: k_sweep32_group<16, 8, false, DYN><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kWarp: k_sweep32_warp<2, DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       default:
         if (a.hub.nchunk > 0 && a.hub.begin == b && a.hub.nhub == cnt && a.hub_part) {
