@@ -577,7 +577,10 @@ bool prefer_l1_all32() {
 
 template <bool DYN>
 int launch_all32(const Sweep32Args& a, const PartThr& t, const int64_t* cb, cudaStream_t s) {
-  static const bool carveout_set = prefer_l1_all32<DYN>();
+  // Static form only: the DF / DF-P kernels run at 32-40 registers, eight
+  // blocks per SM, and the smallest shared-memory carve-out leaves room for
+  // fewer of them (measured: mixed DF-P 15 % slower with it)
+  static const bool carveout_set = DYN ? false : prefer_l1_all32<DYN>();
   (void)carveout_set;
   const int maxg = kSMs * 8;
   const int C = t.n + 1;
@@ -594,8 +597,17 @@ int launch_all32(const Sweep32Args& a, const PartThr& t, const int64_t* cb, cuda
         break;
       case kT4: k_sweep32_group<1, 4, false, DYN><<<grid_for(cnt, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kG4: k_sweep32_group<4, 4, false, DYN><<<grid_for(cnt * 4, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      case kG8: k_sweep32_group<8, 4, false, DYN><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
-      case kG16: k_sweep32_group<16, 4, false, DYN><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
+      // The DF / DF-P form is not pipelined: a row longer than its item's G*U
+      // slots costs extra round trips, so it keeps 16 lanes x 8 indices for
+      // in-degree 17..128 (the Static form measured faster with 8 x 4 and 16 x 4)
+      case kG8:
+        if (DYN) k_sweep32_group<16, 8, false, DYN><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
+        else k_sweep32_group<8, 4, false, DYN><<<grid_for(cnt * 8, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
+        break;
+      case kG16:
+        if (DYN) k_sweep32_group<16, 8, false, DYN><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
+        else k_sweep32_group<16, 4, false, DYN><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e);
+        break;
       case kG16U8: k_sweep32_group<16, 8, false, DYN><<<grid_for(cnt * 16, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       case kWarp: k_sweep32_warp<2, DYN><<<grid_for(cnt * 32, kThreads, maxg), kThreads, 0, s>>>(a, b, e); break;
       default:
