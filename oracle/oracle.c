@@ -14,8 +14,7 @@
  * a sequential loop in ascending neighbour order and every max-reduction is
  * exact, so results do not depend on the thread count.
  *
- * Readings where the paper is silent or inconsistent (each is listed in the
- * design notes too):
+ * Readings where the paper is silent or inconsistent:
  *  R1 unaffected vertices are copied through: Rnew[v] = R[v];
  *  R2 updates are synchronous: read R, write Rnew; the prune/expand tests
  *     compare r with R[v] of the previous iteration;
